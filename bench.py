@@ -1,0 +1,366 @@
+"""Throughput benchmark of the DMALA MIMO detector on GB300.
+
+One step = one pass of the whole hot path over one batch: preprocess (Gram / matched filter /
+preconditioner / initial states), `iterations` chain transitions of every chain, and the read-out
+(hard decision + IS-LLR), for the 32x32 64-QAM Rayleigh workload (SNR 20..32 dB step 2,
+4096 channels per SNR point, 64 chains x 200 iterations) with inputs resident in HBM.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead, on a bounded
+sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+WORKLOAD = "rayleigh_32x32_64qam"
+METRIC = "chain-iterations/s and detections/s at BER<=1e-3 vs plain FP32, 1 GB300"
+UNIT = "chain-iterations/s"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_batch(scale: float, rank: int):
+    w = dict(workload.WORKLOADS[WORKLOAD])
+    n = max(1, int(round(w["per_snr"] * scale)))
+    return workload.rayleigh_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["seed"] + 7 * rank), w
+
+
+def ber_of(batch, llr, best_idx):
+    """Uncoded BER of sign(LLR) and of the hard decision, per SNR point."""
+    bits = batch.tx_bits.astype(np.int64)
+    hard = (llr < 0).astype(np.int64)
+    errs_soft = hard != bits
+    # hard decision bits from the complex Gray labels
+    B2 = int(np.log2(batch.qam[0]))
+    lab = best_idx.astype(np.int64) & ((1 << B2) - 1)
+    hb = ((lab[:, None] >> np.arange(B2 - 1, -1, -1)) & 1).reshape(-1)
+    errs_hard = hb != bits
+    per = {}
+    nb = batch.nt.astype(np.int64) * np.log2(batch.qam).astype(np.int64)
+    off = 0
+    for b in range(batch.n_channels):
+        s = float(batch.snr_db[b])
+        e = per.setdefault(s, [0, 0, 0])
+        e[0] += int(errs_soft[off: off + nb[b]].sum())
+        e[1] += int(errs_hard[off: off + nb[b]].sum())
+        e[2] += int(nb[b])
+        off += nb[b]
+    return {f"{k:g}": {"ber_llr": v[0] / v[2], "ber_best": v[1] / v[2], "bits": v[2]}
+            for k, v in sorted(per.items())}
+
+
+def cpu_baseline(batch, w, budget_s: float, rank: int):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload on the host cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    per_snr = max(1, int(budget_s))   # grown below until the sample takes ~budget_s
+    snrs = sorted(set(batch.snr_db.tolist()))
+    by_snr = {s: [i for i in range(batch.n_channels) if batch.snr_db[i] == s] for s in snrs}
+    T, Np = w["iterations"], w["chains"]
+    # calibrate on one channel per SNR point
+    t0 = time.perf_counter()
+    idx = [by_snr[s][0] for s in snrs]
+    oracle.detect_batch(batch, chains=Np, iterations=T, seed=0, channels=idx, threads=cores)
+    dt = time.perf_counter() - t0
+    per_snr = max(1, min(len(by_snr[snrs[0]]), int(budget_s / max(dt, 1e-3))))
+    idx = [i for s in snrs for i in by_snr[s][:per_snr]]
+    t0 = time.perf_counter()
+    oracle.detect_batch(batch, chains=Np, iterations=T, seed=0, channels=idx, threads=cores)
+    dt = time.perf_counter() - t0
+    value = len(idx) * Np * T / dt
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(idx)} channels ({per_snr} per SNR point) x {Np} chains x {T} "
+                      f"iterations, FP64 C oracle, one channel per thread", "seconds": dt,
+            "detections_per_s": len(idx) / dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    batch, w = load_batch(args.scale, 0)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(batch, w, args.cpu_seconds / max(1, args.steps), 0)
+        if i >= args.warmup:
+            vals.append(r)
+    v = float(np.mean([r["value"] for r in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean([r["seconds"] for r in vals])),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "nt": w["nt"], "nr": w["nr"],
+                                            "qam": w["qam"], "chains": w["chains"],
+                                            "iterations": w["iterations"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp32", "fp64"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the channels per SNR")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-fp32", action="store_true", help="also time the plain FP32 sampler")
+    args = ap.parse_args()
+    rank, world, local = _env_rank()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2407_06042_gb300 as pkg
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    batch, w = load_batch(args.scale, rank)
+    T, Np = w["iterations"], w["chains"]
+    B = batch.n_channels
+
+    precision = args.precision
+    if precision == "auto":
+        try:
+            probe = pkg.Detector(max_channels=1, max_nt=32, max_nr=32, chains=Np, precision="mixed")
+            probe.destroy()
+            precision = "mixed"
+        except pkg.McmcError:
+            precision = "fp32"
+
+    stream = torch.cuda.current_stream()
+    Hd = torch.from_numpy(np.ascontiguousarray(batch.H).view(np.float32).copy()).to(dev)
+    yd = torch.from_numpy(np.ascontiguousarray(batch.y).view(np.float32).copy()).to(dev)
+    sd = torch.from_numpy(batch.sigma2.astype(np.float32)).to(dev)
+    n_ant = int(batch.nt.sum())
+    n_bits = int((batch.nt.astype(np.int64) * np.log2(batch.qam).astype(np.int64)).sum())
+    o_idx = torch.empty(n_ant, dtype=torch.int8, device=dev)
+    o_llr = torch.empty(n_bits, dtype=torch.float32, device=dev)
+    o_bf = torch.empty(B, dtype=torch.float64, device=dev)
+
+    def make(prec):
+        return pkg.Detector(max_channels=B, max_nt=int(batch.nt.max()), max_nr=int(batch.nr.max()),
+                            chains=Np, precision=prec, seed=0, stream=stream)
+
+    def step(det):
+        det.preprocess(batch.nt, batch.nr, batch.qam, Hd, batch.H_off, yd, batch.y_off, sd)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        det.run_chains(T)
+        ev1.record(stream)
+        det.estimate(o_idx, o_llr, o_bf, host_io=False)
+        return ev0, ev1
+
+    def timed(det, steps, warmup):
+        for _ in range(warmup):
+            step(det)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = det.kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kev = []
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                kev.append(step(det))
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+        return ms / steps, kms, det.kernel_launches() - l0, clk.summary()
+
+    det = make(precision)
+    ms_step, chain_ms, launches, clocks = timed(det, args.steps, args.warmup)
+    units_rank = B * Np * T
+    value = units_rank * world / (ms_step * 1e-3)
+    det_per_s = B * world / (ms_step * 1e-3)
+    llr = o_llr.cpu().numpy()
+    idx = o_idx.cpu().numpy()
+    ber = ber_of(batch, llr, idx)
+    ber_ok = [k for k, v in ber.items() if v["ber_llr"] <= 1e-3]
+
+    # end to end through the C ABI with host buffers: H2D of the inputs and D2H of the outputs
+    # inside the timed region, every step
+    e2e = None
+    if not args.no_e2e:
+        Hh = torch.from_numpy(np.ascontiguousarray(batch.H).view(np.float32).copy()).pin_memory()
+        yh = torch.from_numpy(np.ascontiguousarray(batch.y).view(np.float32).copy()).pin_memory()
+        sh = torch.from_numpy(batch.sigma2.astype(np.float32)).pin_memory()
+        hi = torch.empty(n_ant, dtype=torch.int8).pin_memory()
+        hl = torch.empty(n_bits, dtype=torch.float32).pin_memory()
+        hb = torch.empty(B, dtype=torch.float64).pin_memory()
+
+        def step_e2e():
+            det.preprocess(batch.nt, batch.nr, batch.qam, Hh, batch.H_off, yh, batch.y_off, sh)
+            det.run_chains(T)
+            det.estimate(hi, hl, hb, host_io=True)
+
+        for _ in range(max(1, args.warmup)):
+            step_e2e()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": units_rank * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(Hh.numel() * 4 + yh.numel() * 4 + sh.numel() * 4),
+               "d2h_bytes_per_step": int(hi.numel() + hl.numel() * 4 + hb.numel() * 8),
+               "detections_per_s": B * world / dt}
+
+    fp32_line = None
+    if args.compare_fp32 and precision != "fp32":
+        d32 = make("fp32")
+        ms32, kms32, _, _ = timed(d32, max(1, args.steps // 2), 1)
+        ber32 = ber_of(batch, o_llr.cpu().numpy(), o_idx.cpu().numpy())
+        fp32_line = {"value": units_rank * world / (ms32 * 1e-3), "ms_per_step": ms32,
+                     "chain_kernel_ms": kms32, "ber": ber32}
+        d32.destroy()
+
+    # roofline of the dominant kernel (the chain loop): algorithmic FP32 work per chain-iteration
+    N = 2 * w["nt"]
+    L = int(np.sqrt(w["qam"]))
+    NO = 2 * N
+    gemm_flops = 2 * N * NO                   # D' = X' [Gt | P~Gt]
+    prop_flops = N * (2 * 4 * L + 12)         # forward + reverse logits, CDF, energy terms
+    flops_per_ci = gemm_flops + prop_flops
+    achieved_tf = flops_per_ci * units_rank / (chain_ms * 1e-3) / 1e12
+    peak_tf = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 CUDA-core peak: SMs x lanes x FMA x max clock
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "traffic": None,
+                "kernel": "chain loop", "per_unit": f"{flops_per_ci} FP32 flop per chain-iteration",
+                "launch_ms": chain_ms}
+
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = cpu_baseline(batch, w, args.cpu_seconds, rank)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"mixed": "bf16x2+f32", "fp32": "f32", "fp64": "f64"}[precision],
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nt": w["nt"], "nr": w["nr"], "qam": w["qam"],
+                           "snr_db": w["snr_db"], "channels": B * world, "chains": Np,
+                           "iterations": T, "precision": precision, "preconditioned": True,
+                           "l2": "inputs larger than L2 (H = %d MB)" % (Hd.numel() * 4 // 2**20),
+                           "parallelism": f"replicas x{world}"},
+                "detections_per_s": det_per_s, "chain_kernel_ms": chain_ms,
+                "ber": ber, "snr_points_at_ber_le_1e-3": ber_ok,
+                "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
+                "e2e": e2e, "cpu_baseline": cb}
+        if fp32_line:
+            line["plain_fp32"] = fp32_line
+        print(json.dumps(line), flush=True)
+    det.destroy()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * mcmcdet.h -- C ABI of the GB300 (sm_103a) DMALA MIMO detector.
+ *
+ * Method: "Near-Optimal MIMO Detection Using Gradient-Based MCMC in Discrete Spaces"
+ * (arXiv 2407.06042). For every received vector y = Hx + n (Sec. II-A, Eq. (1)) the library runs
+ * Np independent DMALA Markov chains (Algorithm 1) on the tempered posterior (Eq. (33)) and reads
+ * out a hard decision (the visited sample with the smallest residual, Sec. III-A) and IS-based
+ * LLRs (Eq. (34), in the form of Eqs. (35)-(36); Algorithm 2).
+ *
+ * Conventions shared by every call (identical to the CPU oracle's, which is written separately):
+ *  - complex channel H of channel b: Nr x Nt, column-major, interleaved (re, im) float pairs;
+ *    element (r, c) at float2 index H_off[b] + c*Nr + r. y: Nr interleaved pairs at y_off[b].
+ *  - real-valued model (stacked): x = [Re x_c ; Im x_c] (N = 2Nt), y = [Re y ; Im y] (M = 2Nr).
+ *  - alphabet per real dimension: L = sqrt(Qc) PAM levels (2 d_min j - (L-1) d_min), j = 0..L-1,
+ *    d_min = sqrt(3 / (2 (Qc - 1))); chain states are these level indices j (int8).
+ *  - bits: antenna i carries log2(Qc) bits, first the Gray label (j ^ (j >> 1)) of its in-phase
+ *    level (real dimension i), then that of its quadrature level (dimension Nt + i), most
+ *    significant bit first; bit 0 <-> b = +1. LLR > 0 favours bit 0. best_idx holds the complex
+ *    Gray label (label_I << log2 L) | label_Q.
+ *  - parameters (Sec. IV-A): alpha = alpha_scale * sigma^2; preconditioned proposal (Remark 1,
+ *    Eqs. (19), (21)) with beta = d_min^2 / sigma^2 and gamma = sigma^2 / (2 d_min^2); plain
+ *    proposal (Eqs. (16)-(17)) otherwise; temperature tau (Eq. (33)) replaces f by f / tau in
+ *    Algorithm 1, gradient included. sigma^2 is the complex noise variance (sigma^2/2 per real
+ *    element).
+ *  - random numbers: Philox4x32-10 keyed by the 64-bit seed (lo, hi words); counter
+ *    (t, n, channel, chain / 4), word chain % 4, for the proposal uniform of dimension n at
+ *    transition t; counter (t, 0xFFFFFFFF, channel, chain / 4) for the acceptance uniform;
+ *    t = 0 draws the initial state (level = word >> (32 - log2 L)). Uniform u = (2 (w >> 9) + 1)
+ *    * 2^-24. Categorical draws take the smallest level j with u * S_{L-1} < S_j (cumulative
+ *    proposal weights, levels ascending). A proposal is accepted iff log u < log A (Eq. (18)).
+ *    "channel" is the channel's index in the batch given to mcmc_detect_preprocess.
+ *  - a run of T iterations performs T Metropolis-Hastings transitions, numbered
+ *    t_offset+1 .. t_offset+T; the hard decision covers every visited state including the
+ *    initial one (ties keep the earliest).
+ *
+ * Errors: every call returns an mcmc_status; no exception crosses the ABI. Arguments are checked
+ * on the host before anything is enqueued (MCMC_EINVAL). Calls out of order return MCMC_ESTATE.
+ * A numeric fault detected on the device (non-finite energy or logit) is reported as
+ * MCMC_ENUMERIC by the next synchronising call. A CUDA runtime failure returns MCMC_ECUDA and the
+ * message is kept in mcmc_detect_last_error(). Device waits are bounded; one that runs out sets
+ * MCMC_ETIMEOUT instead of hanging.
+ *
+ * Threading: a handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef MCMCDET_H
+#define MCMCDET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcmc_detector mcmc_detector;
+
+typedef enum {
+    MCMC_OK = 0,
+    MCMC_EINVAL = 1,        /* bad argument (checked on the host, nothing enqueued) */
+    MCMC_ENOMEM = 2,        /* device or host allocation failed */
+    MCMC_ECUDA = 3,         /* CUDA runtime error, see mcmc_detect_last_error */
+    MCMC_ETIMEOUT = 4,      /* a bounded device wait ran out */
+    MCMC_ENUMERIC = 5,      /* non-finite value met on the device */
+    MCMC_ESTATE = 6,        /* call out of order (e.g. run before preprocess) */
+    MCMC_EUNSUPPORTED = 7   /* valid request the build does not support (e.g. no sm_103a GPU) */
+} mcmc_status;
+
+/* Arithmetic of the chain loop. */
+typedef enum {
+    MCMC_PREC_FP64 = 0,     /* everything FP64 on CUDA cores (parity mode) */
+    MCMC_PREC_FP32 = 1,     /* plain FP32 sampler on CUDA cores */
+    MCMC_PREC_MIXED = 2     /* Gram products on tcgen05 tensor cores from split-BF16 G (FP32
+                               accumulate), states exact in BF16, FP32 proposal and MH ratio */
+} mcmc_prec;
+
+typedef struct {
+    int32_t max_channels;   /* capacity: channels per preprocess call */
+    int32_t max_nt;         /* capacity: transmit antennas (N = 2 max_nt <= 256) */
+    int32_t max_nr;         /* capacity: receive antennas */
+    int32_t chains;         /* Np, a multiple of 4, 4..1024 */
+    int32_t precision;      /* mcmc_prec */
+    int32_t preconditioned; /* 1: Remark 1 proposal (the paper's evaluation setting), 0: plain */
+    int32_t refresh_period; /* R > 0: recompute every chain's energy in FP64 every R transitions
+                               (FP32/MIXED; FP64 mode is exact throughout); 0: never during a run */
+    int32_t split_terms;    /* MIXED: BF16 terms G is split into (2 = hi+lo, 3 = hi+lo+lo2) */
+    int32_t engine;         /* 0: autotuned; otherwise a fixed kernel variant (MCMC_ENGINE_*) */
+    int32_t reserved;       /* must be 0 */
+    uint64_t seed;          /* Philox key */
+    void *stream;           /* cudaStream_t to enqueue on; NULL: the handle creates its own */
+} mcmc_config;
+
+#define MCMC_ENGINE_AUTO 0
+#define MCMC_ENGINE_SIMT 1      /* CUDA-core chain kernel (FP64 / FP32) */
+#define MCMC_ENGINE_TC 2        /* tcgen05 chain kernel (MIXED) */
+
+/* Per-batch statistics (host struct, filled by mcmc_detect_estimate when non-NULL). */
+typedef struct {
+    int64_t transitions;    /* chain transitions performed since preprocess */
+    int64_t accepts;        /* accepted proposals since preprocess */
+    int32_t numeric_faults; /* chains that met a non-finite value */
+    int32_t reserved;
+    double refresh_drift;   /* max |f_tracked - f_fp64| seen at FP64 refreshes (FP32/MIXED) */
+} mcmc_stats;
+
+/* Fills *cfg with defaults: 1 channel, Nt = Nr = 4, 32 chains, FP32, preconditioned, R = 0,
+ * split_terms = 2, autotuned engine, seed 0, own stream. */
+void mcmc_config_default(mcmc_config *cfg);
+
+/* Creates a detector with the given capacity. Allocates its device workspace lazily at the
+ * first preprocess. The config is copied. Returns MCMC_EUNSUPPORTED without an sm_103a device
+ * for MIXED (tensor-core) precision. */
+mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out);
+
+/* Sec. II-A / Remark 1 preparation of a batch of n_channels received vectors (Gram matrix G = H^H H,
+ * matched filter H^H y, ||y||^2, the preconditioner (G + gamma I)^{-1} when enabled, in FP64),
+ * followed by the random initial states (t = 0) and their FP64 energies.
+ *  nt, nr, qam, H_off, y_off: HOST arrays [n_channels]; qam in {4, 16, 64}; 1 <= nt <= max_nt,
+ *    nt <= nr <= max_nr is not required (nr >= 1).
+ *  H, y, noise_var: device pointers when host_io == 0, host pointers when host_io == 1 (copied
+ *    inside, on the handle's stream; the call then returns after the copy was enqueued from a
+ *    pinned staging buffer, so the host arrays may be reused at once).
+ *    noise_var[b] = sigma^2 of channel b (float, > 0, finite).
+ *  alpha_scale > 0 (paper: 1), tau >= 1 (paper: 2).
+ * Inputs may be released once the stream has passed this call. */
+mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels,
+                                   const int32_t *nt, const int32_t *nr, const int32_t *qam,
+                                   const void *H, const int64_t *H_off,
+                                   const void *y, const int64_t *y_off,
+                                   const float *noise_var,
+                                   float alpha_scale, float tau, int32_t host_io);
+
+/* Algorithm 1's loop: `iterations` transitions of every chain of every channel, numbered
+ * t_offset+1 .. t_offset+iterations (t_offset >= 0). Resuming with t_offset = the number of
+ * transitions already done continues the same random stream exactly. */
+mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t t_offset);
+
+/* Read-out (Sec. III-A hard decision, Algorithm 2 / Eq. (34) soft output) from the chains' final
+ * states (S = Np samples per channel, repeats kept). Outputs (any may be NULL):
+ *  best_idx [sum Nt_b]          complex Gray label of the best visited sample per antenna
+ *  llr      [sum Nt_b log2 Qc_b] IS-based LLRs in the bit order above
+ *  best_f   [n_channels]        f(x_best) = -||y - H x_best||^2 / sigma^2 (untempered, FP64)
+ *  stats    host mcmc_stats*
+ * best_idx/llr/best_f are device pointers when host_io == 0, host pointers when host_io == 1.
+ * Synchronises the handle's stream and reports device-side faults. */
+mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr, double *best_f,
+                                 mcmc_stats *stats, int32_t host_io);
+
+/* Chain state export: states [sum over channels Np*N_b] int8 level indices, channel-major, then
+ * chain-major (chain c of channel b at offset Np*sum_{b'<b} N_b' + c*N_b); f [n_channels*Np]
+ * tracked untempered energies of those states (FP64 in FP64 mode, FP64-accumulated FP32
+ * differences otherwise). Host or device pointers per host_io. Synchronises. */
+mcmc_status mcmc_detect_get_chains(mcmc_detector *d, int8_t *states, double *f, int32_t host_io);
+
+/* Chain state import (checkpoint restore, or any start point): same layout as get_chains; every
+ * level must lie in [0, L_b). Energies are recomputed in FP64. */
+mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32_t host_io);
+
+/* Waits for every call enqueued on the handle's stream; reports device faults. */
+mcmc_status mcmc_detect_synchronize(mcmc_detector *d);
+
+/* Releases the handle and its workspace (synchronises first). NULL is a no-op returning MCMC_OK. */
+mcmc_status mcmc_detect_destroy(mcmc_detector *d);
+
+/* Static description of a status code. */
+const char *mcmc_status_string(mcmc_status s);
+
+/* Last error message of the handle ("" when none); the pointer stays valid until the next call. */
+const char *mcmc_detect_last_error(const mcmc_detector *d);
+
+/* Chain kernel launches enqueued on this handle since creation (all kernels of the run loop). */
+int64_t mcmc_detect_kernel_launches(const mcmc_detector *d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCMCDET_H */

@@ -97,6 +97,10 @@ def lib():
             l.oracle_step.restype = ctypes.c_int
             l.oracle_step.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, _ip, ctypes.POINTER(StepInfo)]
+            l.oracle_step_chains.restype = None
+            l.oracle_step_chains.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_int, ctypes.c_uint32, _ip,
+                                             ctypes.POINTER(StepInfo)]
             l.oracle_run_chain.restype = ctypes.c_int
             l.oracle_run_chain.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                            ctypes.c_uint32, ctypes.c_int, _ip, _dp, _ip, _dp]
@@ -235,6 +239,18 @@ class Target:
         lib().oracle_step(self.ptr, int(seed), int(channel), int(chain), int(t), _i(kk),
                           ctypes.byref(info))
         return kk, info
+
+    def step_chains(self, seed, channel, t, states, chain0=0):
+        """Transition t of chains chain0.. from states [chains, N]: (new states, infos dict)."""
+        st = np.ascontiguousarray(states, np.int32).copy()
+        n = st.shape[0]
+        infos = (StepInfo * n)()
+        lib().oracle_step_chains(self.ptr, int(seed), int(channel), int(chain0), n, int(t),
+                                 _i(st), infos)
+        info = dict(log_a=np.array([x.log_a for x in infos]), log_u=np.array([x.log_u for x in infos]),
+                    cat_margin=np.array([x.cat_margin for x in infos]),
+                    accepted=np.array([x.accepted for x in infos], bool))
+        return st, info
 
     def run_chain(self, seed, channel, chain, t_offset, iters, k):
         kk = np.ascontiguousarray(k, np.int32).copy()

@@ -356,6 +356,16 @@ int oracle_run_chain(const oracle_problem *p, uint64_t seed, uint32_t channel, u
     return accepts;
 }
 
+/* One transition numbered t of each of `chains` chains (chain ids chain0 .. chain0+chains-1)
+ * from the states in k (chains x N, row-major), in place; infos may be NULL. */
+void oracle_step_chains(const oracle_problem *p, uint64_t seed, uint32_t channel, uint32_t chain0,
+                        int chains, uint32_t t, int *k, oracle_step_info *infos)
+{
+    for (int c = 0; c < chains; ++c)
+        oracle_step(p, seed, channel, chain0 + (uint32_t)c, t, k + (size_t)c * (size_t)p->N,
+                    infos ? infos + c : NULL);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Soft output (Sec. III-C).                                                                   */
 /* ------------------------------------------------------------------------------------------ */

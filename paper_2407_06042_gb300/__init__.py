@@ -1,0 +1,261 @@
+"""GB300 (sm_103a) DMALA MIMO detector: Python binding of the C-ABI library ``libmcmcdet.so``.
+
+The binding only marshals arguments: every step of the detection (Gram / matched filter,
+preconditioner, chains, read-out) runs in the library's CUDA kernels. The functions below carry
+the C names of ``include/mcmcdet.h``; :class:`Detector` is a convenience wrapper over them that
+accepts torch tensors (device memory, ``host_io = 0``) or numpy / CPU tensors (host memory,
+``host_io = 1``). Importing this package fails loudly when the library cannot be built or
+loaded: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "Detector", "Config", "Stats", "lib", "load", "MCMC_PREC_FP64", "MCMC_PREC_FP32",
+    "MCMC_PREC_MIXED", "MCMC_ENGINE_AUTO", "MCMC_ENGINE_SIMT", "MCMC_ENGINE_TC", "McmcError",
+    "ABI_FUNCTIONS",
+]
+
+MCMC_PREC_FP64, MCMC_PREC_FP32, MCMC_PREC_MIXED = 0, 1, 2
+MCMC_ENGINE_AUTO, MCMC_ENGINE_SIMT, MCMC_ENGINE_TC = 0, 1, 2
+_PREC = {"fp64": MCMC_PREC_FP64, "fp32": MCMC_PREC_FP32, "mixed": MCMC_PREC_MIXED}
+STATUS = {0: "MCMC_OK", 1: "MCMC_EINVAL", 2: "MCMC_ENOMEM", 3: "MCMC_ECUDA", 4: "MCMC_ETIMEOUT",
+          5: "MCMC_ENUMERIC", 6: "MCMC_ESTATE", 7: "MCMC_EUNSUPPORTED"}
+
+# Every entry point of include/mcmcdet.h.
+ABI_FUNCTIONS = [
+    "mcmc_config_default", "mcmc_detect_create", "mcmc_detect_preprocess",
+    "mcmc_detect_run_chains", "mcmc_detect_estimate", "mcmc_detect_get_chains",
+    "mcmc_detect_set_chains", "mcmc_detect_synchronize", "mcmc_detect_destroy",
+    "mcmc_status_string", "mcmc_detect_last_error", "mcmc_detect_kernel_launches",
+]
+
+
+class McmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``mcmc_config``."""
+    _fields_ = [
+        ("max_channels", ctypes.c_int32), ("max_nt", ctypes.c_int32), ("max_nr", ctypes.c_int32),
+        ("chains", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("preconditioned", ctypes.c_int32), ("refresh_period", ctypes.c_int32),
+        ("split_terms", ctypes.c_int32), ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    """Mirror of ``mcmc_stats``."""
+    _fields_ = [("transitions", ctypes.c_int64), ("accepts", ctypes.c_int64),
+                ("numeric_faults", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("refresh_drift", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load (building first if stale) the C-ABI library and declare its signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.build()
+    l = ctypes.CDLL(p)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    l.mcmc_config_default.argtypes = [ctypes.POINTER(Config)]
+    l.mcmc_config_default.restype = None
+    l.mcmc_detect_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    l.mcmc_detect_create.restype = ctypes.c_int
+    l.mcmc_detect_preprocess.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_float,
+                                         ctypes.c_float, i32]
+    l.mcmc_detect_preprocess.restype = ctypes.c_int
+    l.mcmc_detect_run_chains.argtypes = [vp, i32, i64]
+    l.mcmc_detect_run_chains.restype = ctypes.c_int
+    l.mcmc_detect_estimate.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Stats), i32]
+    l.mcmc_detect_estimate.restype = ctypes.c_int
+    l.mcmc_detect_get_chains.argtypes = [vp, vp, vp, i32]
+    l.mcmc_detect_get_chains.restype = ctypes.c_int
+    l.mcmc_detect_set_chains.argtypes = [vp, vp, i32]
+    l.mcmc_detect_set_chains.restype = ctypes.c_int
+    l.mcmc_detect_synchronize.argtypes = [vp]
+    l.mcmc_detect_synchronize.restype = ctypes.c_int
+    l.mcmc_detect_destroy.argtypes = [vp]
+    l.mcmc_detect_destroy.restype = ctypes.c_int
+    l.mcmc_status_string.argtypes = [ctypes.c_int]
+    l.mcmc_status_string.restype = ctypes.c_char_p
+    l.mcmc_detect_last_error.argtypes = [vp]
+    l.mcmc_detect_last_error.restype = ctypes.c_char_p
+    l.mcmc_detect_kernel_launches.argtypes = [vp]
+    l.mcmc_detect_kernel_launches.restype = ctypes.c_int64
+    if path is None:
+        _lib = l
+    return l
+
+
+def lib():
+    return load()
+
+
+def _ptr(x) -> int:
+    """Address of a torch tensor / numpy array / None."""
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return int(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(x.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(x)!r}")
+
+
+def _is_host(x) -> bool:
+    if isinstance(x, np.ndarray):
+        return True
+    return hasattr(x, "device") and x.device.type == "cpu"
+
+
+class Detector:
+    """One ``mcmc_detector`` handle (see include/mcmcdet.h for every argument's meaning)."""
+
+    def __init__(self, *, max_channels: int, max_nt: int, max_nr: int, chains: int,
+                 precision: str = "fp32", preconditioned: bool = True, refresh_period: int = 0,
+                 split_terms: int = 2, engine: int = MCMC_ENGINE_AUTO, seed: int = 0,
+                 stream=None):
+        self._l = lib()
+        cfg = Config()
+        self._l.mcmc_config_default(ctypes.byref(cfg))
+        cfg.max_channels, cfg.max_nt, cfg.max_nr = int(max_channels), int(max_nt), int(max_nr)
+        cfg.chains = int(chains)
+        cfg.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        cfg.preconditioned = int(bool(preconditioned))
+        cfg.refresh_period = int(refresh_period)
+        cfg.split_terms = int(split_terms)
+        cfg.engine = int(engine)
+        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        cfg.stream = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else (stream or None)
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        st = self._l.mcmc_detect_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != 0:
+            raise McmcError(st, self._l.mcmc_status_string(st).decode())
+        self._h = h
+        self.batch_meta = None
+
+    # -- helpers --------------------------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            msg = self._l.mcmc_detect_last_error(self._h).decode()
+            raise McmcError(st, msg or self._l.mcmc_status_string(st).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def kernel_launches(self) -> int:
+        return int(self._l.mcmc_detect_kernel_launches(self._h))
+
+    # -- C ABI ----------------------------------------------------------------------------
+    def preprocess(self, nt, nr, qam, H, H_off, y, y_off, noise_var, *, alpha_scale=1.0,
+                   tau=2.0):
+        nt = np.ascontiguousarray(nt, np.int32)
+        nr = np.ascontiguousarray(nr, np.int32)
+        qam = np.ascontiguousarray(qam, np.int32)
+        H_off = np.ascontiguousarray(H_off, np.int64)
+        y_off = np.ascontiguousarray(y_off, np.int64)
+        host = _is_host(H)
+        if host != _is_host(y) or host != _is_host(noise_var):
+            raise ValueError("H, y and noise_var must all be host or all be device buffers")
+        self._keep = (nt, nr, qam, H_off, y_off, H, y, noise_var)
+        st = self._l.mcmc_detect_preprocess(
+            self._h, int(nt.shape[0]), _ptr(nt), _ptr(nr), _ptr(qam), _ptr(H), _ptr(H_off),
+            _ptr(y), _ptr(y_off), _ptr(noise_var), float(alpha_scale), float(tau), int(host))
+        self._check(st)
+        L = np.round(np.sqrt(qam)).astype(np.int64)
+        nb = np.log2(L).astype(np.int64)
+        self.batch_meta = dict(nt=nt, nr=nr, qam=qam, N=2 * nt.astype(np.int64), L=L, log2L=nb,
+                               n_channels=int(nt.shape[0]))
+
+    def run_chains(self, iterations: int, t_offset: int = 0):
+        self._check(self._l.mcmc_detect_run_chains(self._h, int(iterations), int(t_offset)))
+
+    def sizes(self):
+        m = self.batch_meta
+        n_ant = int(m["nt"].sum())
+        n_bits = int((m["nt"].astype(np.int64) * 2 * m["log2L"]).sum())
+        n_states = int(self.cfg.chains * m["N"].sum())
+        return n_ant, n_bits, n_states
+
+    def estimate(self, best_idx=None, llr=None, best_f=None, *, host_io: Optional[bool] = None,
+                 stats: bool = False):
+        """Fills the given buffers; with no buffers, returns new host numpy arrays."""
+        ret_new = best_idx is None and llr is None and best_f is None
+        if ret_new:
+            n_ant, n_bits, _ = self.sizes()
+            best_idx = np.zeros(n_ant, np.int8)
+            llr = np.zeros(n_bits, np.float32)
+            best_f = np.zeros(self.batch_meta["n_channels"], np.float64)
+        bufs = [b for b in (best_idx, llr, best_f) if b is not None]
+        if host_io is None:
+            host_io = _is_host(bufs[0]) if bufs else True
+        s = Stats()
+        st = self._l.mcmc_detect_estimate(self._h, _ptr(best_idx), _ptr(llr), _ptr(best_f),
+                                          ctypes.byref(s) if stats else None, int(host_io))
+        self._check(st)
+        out = dict(best_idx=best_idx, llr=llr, best_f=best_f)
+        if stats:
+            out["stats"] = dict(transitions=s.transitions, accepts=s.accepts,
+                                refresh_drift=s.refresh_drift)
+        return out
+
+    def get_chains(self, states=None, f=None, *, host_io: Optional[bool] = None):
+        if states is None and f is None:
+            _, _, n_states = self.sizes()
+            states = np.zeros(n_states, np.int8)
+            f = np.zeros(self.batch_meta["n_channels"] * self.cfg.chains, np.float64)
+        if host_io is None:
+            host_io = _is_host(states if states is not None else f)
+        self._check(self._l.mcmc_detect_get_chains(self._h, _ptr(states), _ptr(f), int(host_io)))
+        return states, f
+
+    def set_chains(self, states, *, host_io: Optional[bool] = None):
+        if host_io is None:
+            host_io = _is_host(states)
+        if host_io:
+            states = np.ascontiguousarray(states, np.int8)
+        self._check(self._l.mcmc_detect_set_chains(self._h, _ptr(states), int(host_io)))
+
+    def synchronize(self):
+        self._check(self._l.mcmc_detect_synchronize(self._h))
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._l.mcmc_detect_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    close = destroy
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()

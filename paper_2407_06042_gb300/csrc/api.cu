@@ -1,0 +1,701 @@
+// api.cu -- host side of the C ABI declared in include/mcmcdet.h: handle, argument checks,
+// workspace management, batch planning and kernel launches. No torch types, no exceptions
+// across the ABI.
+#include "../../include/mcmcdet.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_plan.h"
+
+using namespace mcmcdet;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct mcmc_detector {
+    mcmc_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    long long launches = 0;
+
+    // batch state
+    bool prepared = false;
+    int n_channels = 0;
+    std::vector<ChannelDesc> desc;
+    std::vector<WorkItem> items;
+    int max_n = 0, max_nop = 0, max_nt = 0, max_nr = 0;
+    long long tot_states = 0, tot_mat = 0, tot_bt = 0, tot_vec = 0, tot_bits = 0, tot_ant = 0;
+    long long tot_tc = 0;
+    long long transitions = 0;
+    int cg = 0;
+    size_t chain_smem = 0;
+    bool bt_in_smem = false;
+    TcPlan tc{};
+
+    // device workspace
+    DevBuf d_desc, d_items, d_Gc, d_zc, d_Mc, d_gj, d_yy, d_G64, d_GM64, d_z64, d_w64, d_z32,
+        d_w32, d_bt32, d_bt64, d_tc, d_states, d_best_states, d_f, d_best_f, d_accepts,
+        d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf;
+    HostBuf h_stage;
+};
+
+namespace {
+
+mcmc_status fail(mcmc_detector *d, mcmc_status s, const char *fmt, ...)
+    __attribute__((format(printf, 3, 4)));
+
+mcmc_status fail(mcmc_detector *d, mcmc_status s, const char *fmt, ...)
+{
+    if (d) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        d->err = buf;
+    }
+    return s;
+}
+
+mcmc_status cuda_fail(mcmc_detector *d, cudaError_t e, const char *what)
+{
+    return fail(d, e == cudaErrorMemoryAllocation ? MCMC_ENOMEM : MCMC_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(d, e_, what);   \
+    } while (0)
+
+cudaError_t ensure(DevBuf &b, size_t bytes)
+{
+    bytes = std::max<size_t>(bytes, 256);
+    if (b.cap >= bytes) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) b.cap = bytes;
+    return e;
+}
+
+cudaError_t ensure_host(HostBuf &b, size_t bytes)
+{
+    if (b.cap >= bytes) return cudaSuccess;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    cudaError_t e = cudaMallocHost(&b.p, bytes);
+    if (e == cudaSuccess) b.cap = bytes;
+    return e;
+}
+
+template <typename T> T *P(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+int log2_levels(int L) { return L == 2 ? 1 : L == 4 ? 2 : L == 8 ? 3 : -1; }
+
+bool is_pinned_or_device(const void *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice ||
+           at.type == cudaMemoryTypeManaged;
+}
+
+// Host-to-device copy: direct from pinned memory, else through the handle's pinned staging
+// buffer (the call blocks only for the memcpy into the staging buffer).
+cudaError_t h2d(mcmc_detector *d, void *dst, const void *src, size_t bytes, size_t stage_off)
+{
+    if (bytes == 0) return cudaSuccess;
+    if (is_pinned_or_device(src)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, d->stream);
+    std::memcpy(static_cast<char *>(d->h_stage.p) + stage_off, src, bytes);
+    return cudaMemcpyAsync(dst, static_cast<char *>(d->h_stage.p) + stage_off, bytes,
+                           cudaMemcpyHostToDevice, d->stream);
+}
+
+mcmc_status read_status(mcmc_detector *d)
+{
+    unsigned st = 0;
+    CK(cudaMemcpyAsync(&st, P<unsigned>(d->d_misc), sizeof st, cudaMemcpyDeviceToHost, d->stream),
+       "status read");
+    CK(cudaStreamSynchronize(d->stream), "stream synchronize");
+    if (st & kStatusBadState) return fail(d, MCMC_EINVAL, "chain state level out of range");
+    if (st & kStatusTimeout) return fail(d, MCMC_ETIMEOUT, "bounded device wait expired");
+    if (st & kStatusNumeric) return fail(d, MCMC_ENUMERIC, "non-finite value on the device");
+    return MCMC_OK;
+}
+
+// misc block layout: [0] status (unsigned), [8] drift bits (u64), [16] accept total (u64)
+unsigned *status_ptr(mcmc_detector *d) { return P<unsigned>(d->d_misc); }
+unsigned long long *drift_ptr(mcmc_detector *d) { return reinterpret_cast<unsigned long long *>(P<char>(d->d_misc) + 8); }
+
+__global__ void finalize_desc_kernel(ChannelDesc *desc, const float *noise_var, int n,
+                                     double alpha_scale, double tau, int preconditioned,
+                                     unsigned *status)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    ChannelDesc &c = desc[b];
+    const double s2 = noise_var[b];
+    if (!(s2 > 0.0) || !isfinite(s2)) {
+        atomicOr(status, kStatusNumeric);
+        c.sigma2 = 1.0;
+    } else {
+        c.sigma2 = s2;
+    }
+    const double d2 = c.dmin * c.dmin;
+    const double alpha = alpha_scale * c.sigma2;
+    c.tau = tau;
+    c.inv_s2 = 1.0 / c.sigma2;
+    c.cf = 1.0 / (tau * c.sigma2);
+    if (preconditioned) {
+        const double beta = d2 / c.sigma2;
+        c.clin = 2.0 * d2 / (beta * tau * c.sigma2);
+        c.cquad = 2.0 * d2 / (alpha * beta);
+        c.gamma_t = d2 * (c.sigma2 / (2.0 * d2));   // gamma d^2 with gamma = sigma^2 / (2 dmin^2)
+    } else {
+        c.clin = 2.0 / (tau * c.sigma2);
+        c.cquad = 2.0 * d2 / alpha;
+        c.gamma_t = 0.0;
+    }
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+void mcmc_config_default(mcmc_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->max_channels = 1;
+    cfg->max_nt = 4;
+    cfg->max_nr = 4;
+    cfg->chains = 32;
+    cfg->precision = MCMC_PREC_FP32;
+    cfg->preconditioned = 1;
+    cfg->refresh_period = 0;
+    cfg->split_terms = 2;
+    cfg->engine = MCMC_ENGINE_AUTO;
+    cfg->seed = 0;
+    cfg->stream = nullptr;
+}
+
+const char *mcmc_status_string(mcmc_status s)
+{
+    switch (s) {
+    case MCMC_OK: return "ok";
+    case MCMC_EINVAL: return "invalid argument";
+    case MCMC_ENOMEM: return "out of memory";
+    case MCMC_ECUDA: return "CUDA error";
+    case MCMC_ETIMEOUT: return "bounded device wait expired";
+    case MCMC_ENUMERIC: return "non-finite value on the device";
+    case MCMC_ESTATE: return "call out of order";
+    case MCMC_EUNSUPPORTED: return "unsupported on this device or build";
+    }
+    return "unknown status";
+}
+
+const char *mcmc_detect_last_error(const mcmc_detector *d)
+{
+    return d ? d->err.c_str() : "null handle";
+}
+
+int64_t mcmc_detect_kernel_launches(const mcmc_detector *d)
+{
+    return d ? d->launches : 0;
+}
+
+mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out)
+{
+    if (!cfg || !out) return MCMC_EINVAL;
+    *out = nullptr;
+    if (cfg->max_channels < 1 || cfg->max_nt < 1 || 2 * cfg->max_nt > kMaxN || cfg->max_nr < 1 ||
+        cfg->max_nr > 4096 || cfg->chains < 4 || cfg->chains > 1024 || (cfg->chains % 4) != 0 ||
+        cfg->precision < MCMC_PREC_FP64 || cfg->precision > MCMC_PREC_MIXED ||
+        (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < 0 ||
+        cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 || cfg->engine > 2 ||
+        cfg->reserved != 0)
+        return MCMC_EINVAL;
+    if (cfg->precision == MCMC_PREC_MIXED && cfg->engine == MCMC_ENGINE_SIMT) return MCMC_EINVAL;
+    if (cfg->precision != MCMC_PREC_MIXED && cfg->engine == MCMC_ENGINE_TC) return MCMC_EINVAL;
+    mcmc_detector *d = new (std::nothrow) mcmc_detector();
+    if (!d) return MCMC_ENOMEM;
+    d->cfg = *cfg;
+    cudaError_t e = cudaGetDevice(&d->device);
+    if (e != cudaSuccess) { cudaGetLastError(); delete d; return MCMC_EUNSUPPORTED; }
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, d->device) != cudaSuccess) { cudaGetLastError(); delete d; return MCMC_ECUDA; }
+    d->sm_count = prop.multiProcessorCount;
+    d->cc_major = prop.major;
+    d->cc_minor = prop.minor;
+    d->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cfg->precision == MCMC_PREC_MIXED && !(prop.major == 10 && prop.minor == 3)) {
+        delete d;
+        return MCMC_EUNSUPPORTED;
+    }
+    if (cfg->stream) {
+        d->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&d->stream, cudaStreamDefault) != cudaSuccess) {
+            cudaGetLastError();
+            delete d;
+            return MCMC_ECUDA;
+        }
+        d->own_stream = true;
+    }
+    if (ensure(d->d_misc, 256) != cudaSuccess ||
+        cudaMemsetAsync(d->d_misc.p, 0, 256, d->stream) != cudaSuccess) {
+        cudaGetLastError();
+        mcmc_detect_destroy(d);
+        return MCMC_ENOMEM;
+    }
+    *out = d;
+    return MCMC_OK;
+}
+
+mcmc_status mcmc_detect_destroy(mcmc_detector *d)
+{
+    if (!d) return MCMC_OK;
+    if (d->stream) cudaStreamSynchronize(d->stream);
+    DevBuf *bufs[] = {&d->d_desc, &d->d_items, &d->d_Gc, &d->d_zc, &d->d_Mc, &d->d_gj, &d->d_yy,
+                      &d->d_G64, &d->d_GM64, &d->d_z64, &d->d_w64, &d->d_z32, &d->d_w32,
+                      &d->d_bt32, &d->d_bt64, &d->d_tc, &d->d_states, &d->d_best_states, &d->d_f,
+                      &d->d_best_f, &d->d_accepts, &d->d_misc, &d->d_in_H, &d->d_in_y,
+                      &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (d->h_stage.p) cudaFreeHost(d->h_stage.p);
+    if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
+    cudaGetLastError();
+    delete d;
+    return MCMC_OK;
+}
+
+mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const int32_t *nt,
+                                   const int32_t *nr, const int32_t *qam, const void *H,
+                                   const int64_t *H_off, const void *y, const int64_t *y_off,
+                                   const float *noise_var, float alpha_scale, float tau,
+                                   int32_t host_io)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (n_channels < 1 || n_channels > d->cfg.max_channels)
+        return fail(d, MCMC_EINVAL, "n_channels %d outside [1, %d]", n_channels, d->cfg.max_channels);
+    if (!nt || !nr || !qam || !H || !H_off || !y || !y_off || !noise_var)
+        return fail(d, MCMC_EINVAL, "null argument");
+    if (!(alpha_scale > 0.f) || !std::isfinite(alpha_scale) || !(tau >= 1.f) || !std::isfinite(tau))
+        return fail(d, MCMC_EINVAL, "alpha_scale must be > 0 and tau >= 1");
+    if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    const int Np = d->cfg.chains;
+    const bool pre = d->cfg.preconditioned != 0;
+    d->prepared = false;
+    d->desc.assign(n_channels, ChannelDesc{});
+    long long st = 0, mat = 0, bt = 0, vec = 0, bits = 0, ant = 0, hmax = 0, ymax = 0;
+    int maxn = 0, maxnop = 0, maxnt = 0, maxnr = 0;
+    for (int b = 0; b < n_channels; ++b) {
+        const int L = qam[b] == 4 ? 2 : qam[b] == 16 ? 4 : qam[b] == 64 ? 8 : 0;
+        if (!L) return fail(d, MCMC_EINVAL, "channel %d: qam %d not in {4,16,64}", b, qam[b]);
+        if (nt[b] < 1 || nt[b] > d->cfg.max_nt || nr[b] < 1 || nr[b] > d->cfg.max_nr)
+            return fail(d, MCMC_EINVAL, "channel %d: nt=%d nr=%d outside capacity", b, nt[b], nr[b]);
+        if (H_off[b] < 0 || y_off[b] < 0) return fail(d, MCMC_EINVAL, "channel %d: negative offset", b);
+        ChannelDesc &c = d->desc[b];
+        c.N = 2 * nt[b];
+        c.L = L;
+        c.log2L = log2_levels(L);
+        c.Nt = nt[b];
+        c.Nr = nr[b];
+        c.NO = pre ? 2 * c.N : c.N;
+        c.NOp = (c.NO + 7) / 8 * 8;
+        c.state_off = st;
+        c.mat_off = mat;
+        c.bt_off = bt;
+        c.vec_off = vec;
+        c.bit_off = bits;
+        c.ant_off = ant;
+        c.h_off = H_off[b];
+        c.y_off = y_off[b];
+        c.dmin = std::sqrt(3.0 / (2.0 * (qam[b] - 1)));
+        st += (long long)Np * c.N;
+        mat += (long long)c.N * c.N;
+        bt += (long long)c.N * c.NOp;
+        vec += c.N;
+        bits += (long long)c.N * c.log2L;
+        ant += c.Nt;
+        hmax = std::max(hmax, (long long)H_off[b] + (long long)nt[b] * nr[b]);
+        ymax = std::max(ymax, (long long)y_off[b] + nr[b]);
+        maxn = std::max(maxn, c.N);
+        maxnop = std::max(maxnop, c.NOp);
+        maxnt = std::max(maxnt, c.Nt);
+        maxnr = std::max(maxnr, c.Nr);
+    }
+    d->n_channels = n_channels;
+    d->max_n = maxn;
+    d->max_nop = maxnop;
+    d->max_nt = maxnt;
+    d->max_nr = maxnr;
+    d->tot_states = st;
+    d->tot_mat = mat;
+    d->tot_bt = bt;
+    d->tot_vec = vec;
+    d->tot_bits = bits;
+    d->tot_ant = ant;
+
+    // chain-kernel plan
+    const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
+    const bool mixed = d->cfg.precision == MCMC_PREC_MIXED;
+    const int es = fp64 ? 8 : 4;
+    d->items.clear();
+    if (mixed) {
+        if (!tc_make_plan(d->desc, Np, d->cfg.split_terms, d->smem_optin, d->sm_count, &d->tc))
+            return fail(d, MCMC_EUNSUPPORTED, "no tensor-core plan for this batch (N up to %d)", maxn);
+        d->tot_tc = 0;
+        for (auto &c : d->desc) {
+            c.tc_off = d->tot_tc;
+            d->tot_tc += tc_operand_bytes(c, d->tc);
+        }
+        for (int b = 0; b < n_channels; ++b)
+            for (int c0 = 0; c0 < Np; c0 += d->tc.chains_per_cta)
+                d->items.push_back(WorkItem{b, c0, std::min(d->tc.chains_per_cta, Np - c0), 0});
+    } else {
+        const size_t budget = std::min<size_t>(d->smem_optin, 110 * 1024);
+        bool bt_smem = true;
+        int cg = std::min(64, (Np + 7) / 8 * 8);
+        for (;;) {
+            size_t need = chain_smem_bytes_simt(es, cg, maxn, maxnop, bt_smem);
+            if (need <= budget) break;
+            if (bt_smem && (size_t)maxn * maxnop * es > budget / 2) { bt_smem = false; continue; }
+            if (cg > 8) { cg -= 8; continue; }
+            if (bt_smem) { bt_smem = false; continue; }
+            return fail(d, MCMC_EUNSUPPORTED, "batch does not fit the CUDA-core kernel");
+        }
+        d->cg = cg;
+        d->bt_in_smem = bt_smem;
+        d->chain_smem = chain_smem_bytes_simt(es, cg, maxn, maxnop, bt_smem);
+        for (int b = 0; b < n_channels; ++b)
+            for (int c0 = 0; c0 < Np; c0 += cg)
+                d->items.push_back(WorkItem{b, c0, std::min(cg, Np - c0), 0});
+    }
+
+    // workspace
+    const long long ntc = mat / 4;   // complex Nt^2 elements over the batch
+    CK(ensure(d->d_desc, sizeof(ChannelDesc) * n_channels), "alloc desc");
+    CK(ensure(d->d_items, sizeof(WorkItem) * d->items.size()), "alloc items");
+    CK(ensure(d->d_Gc, 16 * ntc), "alloc Gc");
+    CK(ensure(d->d_zc, 8 * vec), "alloc zc");
+    CK(ensure(d->d_yy, 8 * n_channels), "alloc yy");
+    CK(ensure(d->d_G64, 8 * mat), "alloc G64");
+    CK(ensure(d->d_z64, 8 * vec), "alloc z64");
+    CK(ensure(d->d_w64, 8 * vec), "alloc w64");
+    CK(ensure(d->d_z32, 4 * vec), "alloc z32");
+    CK(ensure(d->d_w32, 4 * vec), "alloc w32");
+    if (pre) {
+        CK(ensure(d->d_Mc, 16 * ntc), "alloc Mc");
+        CK(ensure(d->d_GM64, 8 * mat), "alloc GM64");
+    }
+    const size_t gj_stage = (size_t)(maxnt + 2 * maxnt * maxnt) * 16;
+    const bool stage_gj = pre && gj_stage <= std::min<size_t>(d->smem_optin, 160 * 1024);
+    if (pre && !stage_gj) CK(ensure(d->d_gj, 16 * 2 * ntc), "alloc gj");
+    if (fp64) CK(ensure(d->d_bt64, 8 * bt), "alloc bt64");
+    else CK(ensure(d->d_bt32, 4 * bt), "alloc bt32");   // FP32 chains; FP32 read-out of every non-FP64 mode
+    if (mixed) CK(ensure(d->d_tc, (size_t)d->tot_tc), "alloc tc operands");
+    CK(ensure(d->d_states, st), "alloc states");
+    CK(ensure(d->d_best_states, st), "alloc best states");
+    CK(ensure(d->d_f, 8 * (size_t)n_channels * Np), "alloc f");
+    CK(ensure(d->d_best_f, 8 * (size_t)n_channels * Np), "alloc best f");
+    CK(ensure(d->d_accepts, 8 * (size_t)n_channels * Np), "alloc accepts");
+
+    // inputs
+    const float2 *Hd = static_cast<const float2 *>(H);
+    const float2 *yd = static_cast<const float2 *>(y);
+    const float *sd = noise_var;
+    if (host_io) {
+        const size_t hb = 8 * (size_t)hmax, yb = 8 * (size_t)ymax, sb = 4 * (size_t)n_channels;
+        CK(ensure(d->d_in_H, hb), "alloc H");
+        CK(ensure(d->d_in_y, yb), "alloc y");
+        CK(ensure(d->d_in_s2, sb), "alloc noise_var");
+        const bool all_pinned = is_pinned_or_device(H) && is_pinned_or_device(y) && is_pinned_or_device(noise_var);
+        if (!all_pinned) {
+            CK(cudaStreamSynchronize(d->stream), "stream synchronize");
+            CK(ensure_host(d->h_stage, hb + yb + sb), "alloc pinned staging");
+        }
+        CK(h2d(d, d->d_in_H.p, H, hb, 0), "copy H");
+        CK(h2d(d, d->d_in_y.p, y, yb, hb), "copy y");
+        CK(h2d(d, d->d_in_s2.p, noise_var, sb, hb + yb), "copy noise_var");
+        Hd = P<float2>(d->d_in_H);
+        yd = P<float2>(d->d_in_y);
+        sd = P<float>(d->d_in_s2);
+    }
+    CK(cudaMemcpyAsync(d->d_desc.p, d->desc.data(), sizeof(ChannelDesc) * n_channels,
+                       cudaMemcpyHostToDevice, d->stream), "copy desc");
+    CK(cudaMemcpyAsync(d->d_items.p, d->items.data(), sizeof(WorkItem) * d->items.size(),
+                       cudaMemcpyHostToDevice, d->stream), "copy items");
+    CK(cudaMemsetAsync(d->d_misc.p, 0, 256, d->stream), "reset status");
+    CK(cudaMemsetAsync(d->d_accepts.p, 0, 8 * (size_t)n_channels * Np, d->stream), "reset accepts");
+    finalize_desc_kernel<<<(n_channels + 127) / 128, 128, 0, d->stream>>>(
+        P<ChannelDesc>(d->d_desc), sd, n_channels, alpha_scale, tau, pre, status_ptr(d));
+    CK(cudaGetLastError(), "finalize desc");
+    d->launches++;
+
+    PrepArgs pa{};
+    pa.desc = P<ChannelDesc>(d->d_desc);
+    pa.H = Hd;
+    pa.y = yd;
+    pa.Gc = P<double>(d->d_Gc);
+    pa.zc = P<double>(d->d_zc);
+    pa.Mc = P<double>(d->d_Mc);
+    pa.gj = P<double>(d->d_gj);
+    pa.yy = P<double>(d->d_yy);
+    pa.G64 = P<double>(d->d_G64);
+    pa.GM64 = P<double>(d->d_GM64);
+    pa.z64 = P<double>(d->d_z64);
+    pa.w64 = P<double>(d->d_w64);
+    pa.z32 = P<float>(d->d_z32);
+    pa.w32 = P<float>(d->d_w32);
+    pa.bt32 = fp64 ? nullptr : P<float>(d->d_bt32);
+    pa.bt64 = fp64 ? P<double>(d->d_bt64) : nullptr;
+    pa.status = status_ptr(d);
+    const size_t h_stage = 8 * (size_t)(maxnt * maxnr + maxnr);
+    pa.stage_h = h_stage <= std::min<size_t>(d->smem_optin, 128 * 1024);
+    pa.stage_gj = stage_gj;
+    CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : (size_t)maxnt * 16, pre, d->stream),
+       "prep kernels");
+    d->launches += pre ? 3 : 2;
+    if (mixed) {
+        CK(tc_launch_pack(d->tc, P<ChannelDesc>(d->d_desc), n_channels, P<double>(d->d_G64),
+                          P<double>(d->d_GM64), P<uint8_t>(d->d_tc), d->stream), "pack operands");
+        d->launches++;
+    }
+
+    InitArgs ia{};
+    ia.desc = P<ChannelDesc>(d->d_desc);
+    ia.states = P<int8_t>(d->d_states);
+    ia.n_channels = n_channels;
+    ia.chains = Np;
+    ia.items_per_channel = (long long)(Np / 4) * maxn;
+    ia.key0 = (uint32_t)(d->cfg.seed & 0xFFFFFFFFu);
+    ia.key1 = (uint32_t)(d->cfg.seed >> 32);
+    CK(launch_init_states(ia, d->stream), "init states");
+    d->launches++;
+
+    RefreshArgs ra{};
+    ra.desc = P<ChannelDesc>(d->d_desc);
+    ra.states = P<int8_t>(d->d_states);
+    ra.G64 = P<double>(d->d_G64);
+    ra.z64 = P<double>(d->d_z64);
+    ra.yy = P<double>(d->d_yy);
+    ra.f = P<double>(d->d_f);
+    ra.best_f = P<double>(d->d_best_f);
+    ra.best_states = P<int8_t>(d->d_best_states);
+    ra.status = status_ptr(d);
+    ra.n_channels = n_channels;
+    ra.chains = Np;
+    ra.reset_best = 1;
+    CK(launch_refresh(ra, d->stream), "initial energies");
+    d->launches++;
+    d->transitions = 0;
+    d->prepared = true;
+    return MCMC_OK;
+}
+
+mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t t_offset)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "run_chains before preprocess");
+    if (iterations < 0 || t_offset < 0 || t_offset + (int64_t)iterations > 0xFFFFFFFFll)
+        return fail(d, MCMC_EINVAL, "iterations/t_offset out of range");
+    if (iterations == 0) return MCMC_OK;
+    const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
+    const bool mixed = d->cfg.precision == MCMC_PREC_MIXED;
+    ChainArgs ca{};
+    ca.desc = P<ChannelDesc>(d->d_desc);
+    ca.items = P<WorkItem>(d->d_items);
+    ca.n_items = (int)d->items.size();
+    ca.chains = d->cfg.chains;
+    ca.cg = d->cg;
+    ca.max_n = d->max_n;
+    ca.max_nop = d->max_nop;
+    ca.bt_in_smem = d->bt_in_smem;
+    ca.iterations = iterations;
+    ca.t_offset = t_offset;
+    ca.refresh_period = d->cfg.refresh_period;
+    ca.key0 = (uint32_t)(d->cfg.seed & 0xFFFFFFFFu);
+    ca.key1 = (uint32_t)(d->cfg.seed >> 32);
+    ca.bt = fp64 ? (const void *)P<double>(d->d_bt64) : (const void *)P<float>(d->d_bt32);
+    ca.z = fp64 ? (const void *)P<double>(d->d_z64) : (const void *)P<float>(d->d_z32);
+    ca.w = fp64 ? (const void *)P<double>(d->d_w64) : (const void *)P<float>(d->d_w32);
+    ca.G64 = P<double>(d->d_G64);
+    ca.z64 = P<double>(d->d_z64);
+    ca.yy = P<double>(d->d_yy);
+    ca.states = P<int8_t>(d->d_states);
+    ca.best_states = P<int8_t>(d->d_best_states);
+    ca.f = P<double>(d->d_f);
+    ca.best_f = P<double>(d->d_best_f);
+    ca.accepts = P<unsigned long long>(d->d_accepts);
+    ca.drift_bits = drift_ptr(d);
+    ca.status = status_ptr(d);
+    ca.tc_ops = P<uint8_t>(d->d_tc);
+    ca.split_terms = d->cfg.split_terms;
+    if (mixed) {
+        ca.z = P<float>(d->d_z32);
+        ca.w = P<float>(d->d_w32);
+        CK(tc_launch_chains(ca, d->tc, d->stream), "tensor-core chain kernel");
+    } else {
+        CK(launch_chains_simt(ca, fp64, d->chain_smem, d->stream), "chain kernel");
+    }
+    d->launches++;
+    d->transitions += (long long)iterations * d->n_channels * d->cfg.chains;
+    return MCMC_OK;
+}
+
+mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr, double *best_f,
+                                 mcmc_stats *stats, int32_t host_io)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "estimate before preprocess");
+    if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
+    int8_t *o_idx = best_idx;
+    float *o_llr = llr;
+    double *o_bf = best_f;
+    if (host_io) {
+        if (best_idx) { CK(ensure(d->d_out_idx, d->tot_ant), "alloc out"); o_idx = P<int8_t>(d->d_out_idx); }
+        if (llr) { CK(ensure(d->d_out_llr, 4 * d->tot_bits), "alloc out"); o_llr = P<float>(d->d_out_llr); }
+        if (best_f) { CK(ensure(d->d_out_bf, 8 * (size_t)d->n_channels), "alloc out"); o_bf = P<double>(d->d_out_bf); }
+    }
+    EstimateArgs ea{};
+    ea.desc = P<ChannelDesc>(d->d_desc);
+    ea.states = P<int8_t>(d->d_states);
+    ea.best_states = P<int8_t>(d->d_best_states);
+    ea.f = P<double>(d->d_f);
+    ea.best_f = P<double>(d->d_best_f);
+    ea.G = fp64 ? (const void *)P<double>(d->d_G64) : (const void *)P<float>(d->d_bt32);
+    ea.g_is_bt = fp64 ? 0 : 1;
+    ea.z = fp64 ? (const void *)P<double>(d->d_z64) : (const void *)P<float>(d->d_z32);
+    ea.G64 = P<double>(d->d_G64);
+    ea.z64 = P<double>(d->d_z64);
+    ea.yy = P<double>(d->d_yy);
+    ea.n_channels = d->n_channels;
+    ea.chains = d->cfg.chains;
+    ea.best_idx = o_idx;
+    ea.llr = o_llr;
+    ea.best_f_out = o_bf;
+    ea.status = status_ptr(d);
+    CK(launch_estimate(ea, fp64, d->stream), "estimate kernel");
+    d->launches++;
+    if (host_io) {
+        if (best_idx) CK(cudaMemcpyAsync(best_idx, o_idx, d->tot_ant, cudaMemcpyDeviceToHost, d->stream), "copy out");
+        if (llr) CK(cudaMemcpyAsync(llr, o_llr, 4 * d->tot_bits, cudaMemcpyDeviceToHost, d->stream), "copy out");
+        if (best_f) CK(cudaMemcpyAsync(best_f, o_bf, 8 * (size_t)d->n_channels, cudaMemcpyDeviceToHost, d->stream), "copy out");
+    }
+    mcmc_status s = read_status(d);
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->transitions = d->transitions;
+        std::vector<unsigned long long> acc((size_t)d->n_channels * d->cfg.chains);
+        CK(cudaMemcpy(acc.data(), d->d_accepts.p, 8 * acc.size(), cudaMemcpyDeviceToHost), "copy accepts");
+        unsigned long long tot = 0;
+        for (auto v : acc) tot += v;
+        stats->accepts = (int64_t)tot;
+        unsigned long long db = 0;
+        CK(cudaMemcpy(&db, drift_ptr(d), 8, cudaMemcpyDeviceToHost), "copy drift");
+        double dr;
+        std::memcpy(&dr, &db, 8);
+        stats->refresh_drift = dr;
+    }
+    return s;
+}
+
+mcmc_status mcmc_detect_get_chains(mcmc_detector *d, int8_t *states, double *f, int32_t host_io)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "get_chains before preprocess");
+    if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    const cudaMemcpyKind k = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (states) CK(cudaMemcpyAsync(states, d->d_states.p, d->tot_states, k, d->stream), "copy states");
+    if (f) CK(cudaMemcpyAsync(f, d->d_f.p, 8 * (size_t)d->n_channels * d->cfg.chains, k, d->stream), "copy f");
+    return read_status(d);
+}
+
+mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32_t host_io)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "set_chains before preprocess");
+    if (!states) return fail(d, MCMC_EINVAL, "null states");
+    if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    if (host_io) {
+        const int Np = d->cfg.chains;
+        for (int b = 0; b < d->n_channels; ++b) {
+            const ChannelDesc &c = d->desc[b];
+            for (long long i = 0; i < (long long)Np * c.N; ++i) {
+                const int v = states[c.state_off + i];
+                if (v < 0 || v >= c.L) return fail(d, MCMC_EINVAL, "channel %d: level %d out of range", b, v);
+            }
+        }
+        CK(cudaMemcpyAsync(d->d_states.p, states, d->tot_states, cudaMemcpyHostToDevice, d->stream), "copy states");
+        CK(cudaStreamSynchronize(d->stream), "stream synchronize");
+    } else {
+        CK(cudaMemcpyAsync(d->d_states.p, states, d->tot_states, cudaMemcpyDeviceToDevice, d->stream), "copy states");
+    }
+    RefreshArgs ra{};
+    ra.desc = P<ChannelDesc>(d->d_desc);
+    ra.states = P<int8_t>(d->d_states);
+    ra.G64 = P<double>(d->d_G64);
+    ra.z64 = P<double>(d->d_z64);
+    ra.yy = P<double>(d->d_yy);
+    ra.f = P<double>(d->d_f);
+    ra.best_f = P<double>(d->d_best_f);
+    ra.best_states = P<int8_t>(d->d_best_states);
+    ra.status = status_ptr(d);
+    ra.n_channels = d->n_channels;
+    ra.chains = d->cfg.chains;
+    ra.reset_best = 1;
+    CK(launch_refresh(ra, d->stream), "refresh energies");
+    d->launches++;
+    return read_status(d);
+}
+
+mcmc_status mcmc_detect_synchronize(mcmc_detector *d)
+{
+    if (!d) return MCMC_EINVAL;
+    return read_status(d);
+}
+
+}  // extern "C"

@@ -1,0 +1,372 @@
+// chains_simt.cu -- DMALA chain kernel on CUDA cores (FP64 parity mode and the plain FP32
+// sampler): Algorithm 1's loop for a group of chains of one channel per CTA.
+//
+// Per transition t (Algorithm 1, loop body, in order):
+//   1. x'_n ~ q_n(. | x_n) for every (chain, n) from the cached drift slope of the current
+//      state (Eqs. (15)-(17) / (21)); log q(x'|x) accumulated;
+//   2. one small GEMM  D' = X' [Gt | P~ Gt]  gives Gt x' (energy) and the drift at x' (Eq. (10));
+//   3. the reverse factors q_n(x_n | x'_n) and the energy difference (Eqs. (3), (18));
+//   4. per chain: log A = min(0, df/tau + log q(x|x') - log q(x'|x)); accept iff log u < log A;
+//   5. accepted chains take x', Gt x' and the drift slope of x' (the proposal cache of
+//      Algorithm 1's accept branch).
+// The drift slope and Gt x of a state are pure functions of that state, so a run split into
+// several launches (resume) makes exactly the same decisions as one launch.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mcmcdet {
+
+namespace {
+
+template <typename T> struct M;
+template <> struct M<float> {
+    static __device__ __forceinline__ float ex(float x) { return __expf(x); }
+    static __device__ __forceinline__ float lg(float x) { return __logf(x); }
+    static __device__ __forceinline__ float uni(uint32_t w) { return uniform_f(w); }
+};
+template <> struct M<double> {
+    static __device__ __forceinline__ double ex(double x) { return exp(x); }
+    static __device__ __forceinline__ double lg(double x) { return log(x); }
+    static __device__ __forceinline__ double uni(uint32_t w) { return uniform_d(w); }
+};
+
+__host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Shared-memory layout (byte offsets), identical for every work item of a launch.
+struct Layout {
+    size_t bt, zt, wt, a, D, Dp, xsT, term, dterm, fcur, fbest, acc, impr, cnt, k, kp, kb, total;
+};
+
+__host__ __device__ inline Layout make_layout(int es, int cg, int N, int NOp, bool bt_smem)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 16); return r; };
+    L.bt = take(bt_smem ? (size_t)N * NOp * es : 0);
+    L.zt = take((size_t)N * es);
+    L.wt = take((size_t)N * es);
+    L.a = take((size_t)cg * N * es);
+    L.D = take((size_t)cg * N * es);
+    L.Dp = take((size_t)cg * NOp * es);
+    L.xsT = take((size_t)N * cg * es);
+    L.term = take((size_t)cg * N * es);
+    L.dterm = take((size_t)cg * N * es);
+    L.fcur = take((size_t)cg * 8);
+    L.fbest = take((size_t)cg * 8);
+    L.acc = take((size_t)cg * 4);
+    L.impr = take((size_t)cg * 4);
+    L.cnt = take((size_t)cg * 4);
+    L.k = take((size_t)cg * N);
+    L.kp = take((size_t)cg * N);
+    L.kb = take((size_t)cg * N);
+    L.total = o;
+    return L;
+}
+
+template <typename T, int NV> struct Vec;
+template <> struct Vec<float, 4> { using type = float4; };
+template <> struct Vec<double, 2> { using type = double2; };
+
+template <typename T, int CNT>
+__device__ __forceinline__ void load_row(const T *p, T (&v)[CNT])
+{
+    constexpr int NV = sizeof(T) == 4 ? 4 : 2;
+    using V = typename Vec<T, NV>::type;
+#pragma unroll
+    for (int i = 0; i < CNT / NV; ++i) {
+        const V q = reinterpret_cast<const V *>(p)[i];
+        if constexpr (NV == 4) { v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w; }
+        else { v[2 * i] = q.x; v[2 * i + 1] = q.y; }
+    }
+}
+
+template <typename T, int CNT>
+__device__ __forceinline__ void store_row(T *p, const T (&v)[CNT])
+{
+    constexpr int NV = sizeof(T) == 4 ? 4 : 2;
+    using V = typename Vec<T, NV>::type;
+#pragma unroll
+    for (int i = 0; i < CNT / NV; ++i) {
+        V q;
+        if constexpr (NV == 4) { q.x = v[4 * i]; q.y = v[4 * i + 1]; q.z = v[4 * i + 2]; q.w = v[4 * i + 3]; }
+        else { q.x = v[2 * i]; q.y = v[2 * i + 1]; }
+        reinterpret_cast<V *>(p)[i] = q;
+    }
+}
+
+// D'[c][o] = sum_m bt[m][o] xsT[m][c] for the active chains; register tile TCH x TO.
+template <typename T, int TCH, int TO>
+__device__ __forceinline__ void gemm(const T *__restrict__ bt, int NOp, const T *xsT, int cg, int N,
+                                     T *Dp, int nC)
+{
+    const int nOT = NOp / TO, nCT = (nC + TCH - 1) / TCH;
+    for (int tile = threadIdx.x; tile < nOT * nCT; tile += blockDim.x) {
+        const int o0 = (tile % nOT) * TO, c0 = (tile / nOT) * TCH;
+        T acc[TCH][TO];
+#pragma unroll
+        for (int i = 0; i < TCH; ++i)
+#pragma unroll
+            for (int j = 0; j < TO; ++j) acc[i][j] = T(0);
+#pragma unroll 2
+        for (int m = 0; m < N; ++m) {
+            T xv[TCH], bv[TO];
+            load_row<T, TCH>(xsT + (size_t)m * cg + c0, xv);
+            load_row<T, TO>(bt + (size_t)m * NOp + o0, bv);
+#pragma unroll
+            for (int i = 0; i < TCH; ++i)
+#pragma unroll
+                for (int j = 0; j < TO; ++j) acc[i][j] = fma(xv[i], bv[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < TCH; ++i) store_row<T, TO>(Dp + (size_t)(c0 + i) * NOp + o0, acc[i]);
+    }
+}
+
+// Proposal factor of one dimension: logits a (j - k) - cq (j - k)^2 for j < L, their maximum,
+// the cumulative weights S_j = sum_{i<=j} exp(logit_i - max) and their total S_{L-1}.
+template <typename T>
+struct Factor {
+    T mx;
+    T total;
+    T S[kMaxL];
+};
+
+template <typename T>
+__device__ __forceinline__ T logit_of(T a, T cq, int j, int k)
+{
+    const T dj = T(j - k);
+    return a * dj - cq * dj * dj;
+}
+
+template <typename T>
+__device__ __forceinline__ void factor(T a, T cq, int k, int L, Factor<T> &F)
+{
+    T lg[kMaxL];
+    T mx = -T(1e30);
+#pragma unroll
+    for (int j = 0; j < kMaxL; ++j) {
+        lg[j] = logit_of(a, cq, j, k);
+        if (j < L) mx = lg[j] > mx ? lg[j] : mx;
+    }
+    F.mx = mx;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < kMaxL; ++j) {
+        if (j < L) acc += M<T>::ex(lg[j] - mx);
+        F.S[j] = acc;
+    }
+    F.total = acc;
+}
+
+template <typename T, int TCH, int TO>
+__global__ void __launch_bounds__(256) chains_simt_kernel(const ChainArgs A)
+{
+    const WorkItem it = A.items[blockIdx.x];
+    const ChannelDesc d = A.desc[it.b];
+    const int N = d.N, L = d.L, NOp = d.NOp, cg = A.cg, nC = it.nc;
+    const bool pre = d.NO > N;
+    const T clin = (T)d.clin, cq = (T)d.cquad, cf = (T)d.cf;
+    const Layout lay = make_layout(sizeof(T), cg, A.max_n, A.max_nop, A.bt_in_smem);
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *zt = reinterpret_cast<T *>(smem + lay.zt);
+    T *wt = reinterpret_cast<T *>(smem + lay.wt);
+    T *sa = reinterpret_cast<T *>(smem + lay.a);
+    T *sD = reinterpret_cast<T *>(smem + lay.D);
+    T *Dp = reinterpret_cast<T *>(smem + lay.Dp);
+    T *xsT = reinterpret_cast<T *>(smem + lay.xsT);
+    T *term = reinterpret_cast<T *>(smem + lay.term);
+    T *dterm = reinterpret_cast<T *>(smem + lay.dterm);
+    double *fcur = reinterpret_cast<double *>(smem + lay.fcur);
+    double *fbest = reinterpret_cast<double *>(smem + lay.fbest);
+    int *acc = reinterpret_cast<int *>(smem + lay.acc);
+    int *impr = reinterpret_cast<int *>(smem + lay.impr);
+    unsigned *cnt = reinterpret_cast<unsigned *>(smem + lay.cnt);
+    int8_t *sk = reinterpret_cast<int8_t *>(smem + lay.k);
+    int8_t *skp = reinterpret_cast<int8_t *>(smem + lay.kp);
+    int8_t *skb = reinterpret_cast<int8_t *>(smem + lay.kb);
+
+    const T *gbt = reinterpret_cast<const T *>(A.bt) + d.bt_off;
+    const T *bt = gbt;
+    if (A.bt_in_smem) {
+        T *sbt = reinterpret_cast<T *>(smem + lay.bt);
+        for (int e = threadIdx.x; e < N * NOp; e += blockDim.x) sbt[e] = gbt[e];
+        bt = sbt;
+    }
+    const T *gz = reinterpret_cast<const T *>(A.z) + d.vec_off;
+    const T *gw = reinterpret_cast<const T *>(A.w) + d.vec_off;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) { zt[n] = gz[n]; wt[n] = gw[n]; }
+    const long long sbase = d.state_off + (long long)it.c0 * N;
+    for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {
+        const int c = e / N, n = e % N;
+        const int8_t kv = A.states[sbase + e];
+        sk[c * N + n] = kv;
+        skb[c * N + n] = A.best_states[sbase + e];
+        xsT[n * cg + c] = (T)odd_of(kv, L);
+    }
+    for (int c = threadIdx.x; c < cg; c += blockDim.x) {
+        const long long ci = (long long)it.b * A.chains + it.c0 + c;
+        fcur[c] = c < nC ? A.f[ci] : 0.0;
+        fbest[c] = c < nC ? A.best_f[ci] : 0.0;
+        cnt[c] = 0;
+    }
+    __syncthreads();
+    // Gt x and the drift slope of the current states
+    gemm<T, TCH, TO>(bt, NOp, xsT, cg, N, Dp, nC);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {
+        const int c = e / N, n = e % N;
+        const T dg = Dp[c * NOp + n];
+        sD[e] = dg;
+        sa[e] = clin * (pre ? (wt[n] - Dp[c * NOp + N + n]) : (zt[n] - dg));
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int i = 0; i < A.iterations; ++i) {
+        const uint32_t t = (uint32_t)(A.t_offset + 1 + i);
+        // 1. proposal draw, four chains per Philox block
+        for (int q = threadIdx.x; q < (nC / 4) * N; q += blockDim.x) {
+            const int cq4 = q / N, n = q % N;
+            const U4 w = philox4x32_10(t, (uint32_t)n, (uint32_t)it.b,
+                                       (uint32_t)((it.c0 >> 2) + cq4), A.key0, A.key1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = 4 * cq4 + j;
+                const int e = c * N + n;
+                const int kn = sk[e];
+                Factor<T> F;
+                factor<T>(sa[e], cq, kn, L, F);
+                const T target = M<T>::uni(word_of(w, j)) * F.total;
+                int sel = L - 1;
+#pragma unroll
+                for (int l = kMaxL - 1; l >= 0; --l)
+                    if (l < L && target < F.S[l]) sel = l;
+                skp[e] = (int8_t)sel;
+                term[e] = -(logit_of(sa[e], cq, sel, kn) - F.mx - M<T>::lg(F.total));
+                xsT[n * cg + c] = (T)odd_of(sel, L);
+            }
+        }
+        __syncthreads();
+        // 2. D' = X' [Gt | P~ Gt]
+        gemm<T, TCH, TO>(bt, NOp, xsT, cg, N, Dp, nC);
+        __syncthreads();
+        // 3. reverse factor and energy difference per (chain, n)
+        for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {
+            const int c = e / N, n = e % N;
+            const int kn = sk[e], kpn = skp[e];
+            const T dgp = Dp[c * NOp + n];
+            const T ap = clin * (pre ? (wt[n] - Dp[c * NOp + N + n]) : (zt[n] - dgp));
+            Factor<T> F;
+            factor<T>(ap, cq, kpn, L, F);
+            term[e] += logit_of(ap, cq, kn, kpn) - F.mx - M<T>::lg(F.total);
+            dterm[e] = T(2 * (kpn - kn)) * (T(2) * zt[n] - sD[e] - dgp);
+        }
+        __syncthreads();
+        // 4. Metropolis-Hastings decision, one warp per chain
+        for (int c = warp; c < nC; c += nwarps) {
+            T s = T(0), sd = T(0);
+            for (int n = lane; n < N; n += 32) { s += term[c * N + n]; sd += dterm[c * N + n]; }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                sd += __shfl_xor_sync(0xffffffffu, sd, o);
+            }
+            if (lane == 0) {
+                const int cc = it.c0 + c;
+                const U4 w = philox4x32_10(t, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
+                                           A.key0, A.key1);
+                const T logr = s + cf * sd;
+                const T loga = logr < T(0) ? logr : T(0);
+                const T logu = M<T>::lg(M<T>::uni(word_of(w, cc & 3)));
+                int ok = logu < loga;
+                if (!isfinite((double)logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
+                acc[c] = ok;
+                int im = 0;
+                if (ok) {
+                    const double fn = fcur[c] + d.inv_s2 * (double)sd;
+                    fcur[c] = fn;
+                    cnt[c] += 1;
+                    if (fn > fbest[c]) { fbest[c] = fn; im = 1; }
+                }
+                impr[c] = im;
+            }
+        }
+        __syncthreads();
+        // 5. accepted chains take x' and its caches
+        for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {
+            const int c = e / N, n = e % N;
+            if (acc[c]) {
+                const int8_t kv = skp[e];
+                sk[e] = kv;
+                const T dgp = Dp[c * NOp + n];
+                sD[e] = dgp;
+                sa[e] = clin * (pre ? (wt[n] - Dp[c * NOp + N + n]) : (zt[n] - dgp));
+                if (impr[c]) skb[e] = kv;
+            }
+        }
+        __syncthreads();
+        // periodic FP64 refresh of the tracked energies (decisions never read them)
+        if (sizeof(T) == 4 && A.refresh_period > 0 && (t % (uint32_t)A.refresh_period) == 0u) {
+            const double *G = A.G64 + d.mat_off;
+            const double *z = A.z64 + d.vec_off;
+            for (int c = warp; c < nC; c += nwarps) {
+                double quad = 0.0, lin = 0.0;
+                for (int n = lane; n < N; n += 32) {
+                    const double xn = odd_of(sk[c * N + n], L);
+                    double s = 0.0;
+                    for (int m = 0; m < N; ++m) s = fma(G[(size_t)n * N + m], (double)odd_of(sk[c * N + m], L), s);
+                    quad = fma(xn, s, quad);
+                    lin = fma(xn, z[n], lin);
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    quad += __shfl_xor_sync(0xffffffffu, quad, o);
+                    lin += __shfl_xor_sync(0xffffffffu, lin, o);
+                }
+                if (lane == 0) {
+                    const double f64 = -(A.yy[it.b] - 2.0 * lin + quad) * d.inv_s2;
+                    const double dr = fabs(f64 - fcur[c]);
+                    atomicMax(A.drift_bits, (unsigned long long)__double_as_longlong(dr));
+                    fcur[c] = f64;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // write back
+    for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {
+        A.states[sbase + e] = sk[e];
+        A.best_states[sbase + e] = skb[e];
+    }
+    for (int c = threadIdx.x; c < nC; c += blockDim.x) {
+        const long long ci = (long long)it.b * A.chains + it.c0 + c;
+        A.f[ci] = fcur[c];
+        A.best_f[ci] = fbest[c];
+        A.accepts[ci] += cnt[c];
+    }
+}
+
+}  // namespace
+
+size_t chain_smem_bytes_simt(int elem_size, int cg, int max_n, int max_nop, bool bt_in_smem)
+{
+    return make_layout(elem_size, cg, max_n, max_nop, bt_in_smem).total;
+}
+
+cudaError_t launch_chains_simt(const ChainArgs &a, bool fp64, size_t smem, cudaStream_t s)
+{
+    if (a.n_items <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (fp64) {
+        auto k = chains_simt_kernel<double, 4, 4>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        k<<<a.n_items, 256, smem, s>>>(a);
+    } else {
+        auto k = chains_simt_kernel<float, 8, 4>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        k<<<a.n_items, 256, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mcmcdet

@@ -1,0 +1,114 @@
+// common.cuh -- shared device definitions of the DMALA detector kernels (sm_103a).
+//
+// Scaled units used by every kernel: with d = d_min, the state x = d * xt where xt = 2k - (L-1)
+// is an odd integer (k the PAM level index), Gt = d^2 H^T H (real-valued, stacked, N x N),
+// zt = d H^T y. Then (Sec. II-A, Eq. (3))
+//     f(x) = -(||y||^2 - 2 xt^T zt + xt^T Gt xt) / sigma^2,
+// and the tempered energy difference of a move x -> x' (Algorithm 2 with Eq. (18)) is
+//     df_tau = (1 / (tau sigma^2)) sum_n (xt'_n - xt_n)(2 zt_n - (Gt xt)_n - (Gt xt')_n),
+// which needs only the cached Gt xt of both states (no ||y||^2 cancellation).
+// The proposal factor of dimension n (Eq. (16), or Eq. (21) with Remark 1's preconditioner) is,
+// in level units j (target level) and k (current level),
+//     logit(j) = a_n (j - k) - c_quad (j - k)^2,   a_n = c_lin g_n,
+// with g = P~ (zt - Gt xt): P~ = I for the plain proposal (c_lin = 2 / (tau sigma^2),
+// c_quad = 2 d^2 / alpha), P~ = (Gt + gamma d^2 I)^{-1} for the preconditioned one
+// (c_lin = 2 d^2 / (beta tau sigma^2), c_quad = 2 d^2 / (alpha beta)). For the preconditioned
+// drift the kernels use g = wt - (P~ Gt) xt with wt = P~ zt, so one GEMM against [Gt | P~ Gt]
+// yields both the energy terms and the drift.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcmcdet {
+
+constexpr int kMaxN = 256;     // real unknowns per channel (Nt <= 128)
+constexpr int kMaxL = 8;       // PAM levels per real dimension (64-QAM)
+
+// Per-channel description, built on the host at preprocess time.
+struct ChannelDesc {
+    int N;             // real unknowns 2 Nt
+    int L;             // PAM levels
+    int log2L;
+    int Nt;
+    int Nr;
+    int NO;            // GEMM outputs per chain: N (plain) or 2N (preconditioned)
+    int NOp;           // NO rounded up to a multiple of 8
+    int pad0;
+    long long state_off;   // int8 offset of chain 0's state: Np * sum_{b'<b} N_b'
+    long long mat_off;     // offset of this channel's N x N matrices (elements)
+    long long bt_off;      // offset of this channel's N x NOp GEMM operand (elements)
+    long long tc_off;      // offset of this channel's tcgen05 operand block (bytes)
+    long long vec_off;     // offset of this channel's N-vectors
+    long long bit_off;     // offset of this channel's LLRs
+    long long ant_off;     // offset of this channel's antennas (best_idx)
+    long long h_off;       // input offset of H (complex elements)
+    long long y_off;       // input offset of y (complex elements)
+    double sigma2;
+    double dmin;
+    double cf;         // 1 / (tau sigma^2)
+    double clin;       // logit slope per drift unit (level units)
+    double cquad;      // logit curvature (level units)
+    double inv_s2;     // 1 / sigma^2
+    double gamma_t;    // gamma d^2 (preconditioner damping in scaled units)
+    double tau;
+};
+
+// Device status word bits (OR-ed by kernels, read by the host at synchronising calls).
+constexpr unsigned kStatusNumeric = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+constexpr unsigned kStatusBadState = 4u;
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64-bit products
+// with a Weyl-sequence key schedule.
+// ------------------------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t word_of(const U4 &v, int i)
+{
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// Uniform in (0,1): (2 (w >> 9) + 1) * 2^-24, exactly representable in FP32 and FP64.
+__device__ __forceinline__ float uniform_f(uint32_t w)
+{
+    return (float)(2u * (w >> 9) + 1u) * 5.9604644775390625e-8f;
+}
+__device__ __forceinline__ double uniform_d(uint32_t w)
+{
+    return (double)(2u * (w >> 9) + 1u) * 5.9604644775390625e-8;
+}
+
+constexpr uint32_t kMhStream = 0xFFFFFFFFu;   // counter word 1 of the acceptance uniforms
+
+// Level index -> odd integer 2k - (L-1).
+__device__ __forceinline__ int odd_of(int k, int L) { return 2 * k - (L - 1); }
+
+__device__ __forceinline__ int gray_of(int k) { return k ^ (k >> 1); }
+__device__ __forceinline__ int level_of_gray(int g) { int k = g; k ^= k >> 1; k ^= k >> 2; return k; }
+
+__device__ __forceinline__ void set_status(unsigned *status, unsigned bit)
+{
+    atomicOr(status, bit);
+}
+
+}  // namespace mcmcdet

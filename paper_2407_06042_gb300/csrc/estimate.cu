@@ -1,0 +1,166 @@
+// estimate.cu -- read-out of the chains (Sec. III-A hard decision; Sec. III-C, Algorithm 2).
+//
+// One CTA per channel:
+//  * hard decision: the visited state with the largest f (smallest residual), ties to the lowest
+//    chain; its f is recomputed in FP64 and its levels are mapped to complex Gray labels;
+//  * soft output: IS-based LLR of Eq. (34) in the log-sum-exp form of Eqs. (35)-(36) with exact
+//    F(a) = log(1 + e^a), over the S = Np final states. For bit k on dimension n, x+ and x-
+//    differ from the sample in dimension n only (Sec. III-D), so
+//        f(x with level k') - f(x) = (1/sigma^2) (2 D (zt_n - (Gt xt)_n) - D^2 Gt_nn),
+//    D = 2 (k' - k), needs (Gt xt)_n of the sample only.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mcmcdet {
+
+namespace {
+
+template <typename T> struct E;
+template <> struct E<float> {
+    static __device__ __forceinline__ float softplus(float a)
+    {
+        return a > 0.f ? a + log1pf(__expf(-a)) : log1pf(__expf(a));
+    }
+};
+template <> struct E<double> {
+    static __device__ __forceinline__ double softplus(double a)
+    {
+        return a > 0.0 ? a + log1p(exp(-a)) : log1p(exp(a));
+    }
+};
+
+// running log-sum-exp, Eq. (36)
+template <typename T>
+__device__ __forceinline__ T lse_push(T v, T a)
+{
+    if (v == -INFINITY) return a;
+    if (a == -INFINITY) return v;
+    const T m = v > a ? v : a;
+    const T dlt = v > a ? a - v : v - a;
+    return m + E<T>::softplus(dlt);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
+{
+    const int b = blockIdx.x;
+    const ChannelDesc d = A.desc[b];
+    const int N = d.N, L = d.L, B = d.log2L, Np = A.chains, nt = d.Nt;
+    const int8_t *S = A.states + d.state_off;
+    const double *f = A.f + (long long)b * Np;
+    const T *G = reinterpret_cast<const T *>(A.G) + (A.g_is_bt ? d.bt_off : d.mat_off);
+    const int gstride = A.g_is_bt ? d.NOp : N;
+    const T *z = reinterpret_cast<const T *>(A.z) + d.vec_off;
+    const T inv_s2 = (T)d.inv_s2;
+    const T tau = (T)d.tau;
+    const T w = (tau - T(1)) / tau;
+    __shared__ int s_best;
+    __shared__ double s_fref;
+    __shared__ T s_part[2 * 3 * kMaxN];      // partial LSEs (split 0 stored, others merged)
+
+    // hard decision and the reference energy of the soft output
+    if (threadIdx.x < 32) {
+        double bv = -INFINITY, fm = -INFINITY;
+        int bi = 0x7fffffff;
+        for (int c = threadIdx.x; c < Np; c += 32) {
+            const double v = A.best_f[(long long)b * Np + c];
+            if (v > bv || (v == bv && c < bi)) { bv = v; bi = c; }
+            fm = f[c] > fm ? f[c] : fm;
+        }
+        for (int o = 16; o; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            const double of = __shfl_xor_sync(0xffffffffu, fm, o);
+            fm = of > fm ? of : fm;
+        }
+        if (threadIdx.x == 0) { s_best = bi; s_fref = fm; }
+    }
+    __syncthreads();
+    const int8_t *kb = A.best_states + d.state_off + (long long)s_best * N;
+    if (threadIdx.x < 32) {
+        const double *G64 = A.G64 + d.mat_off;
+        const double *z64 = A.z64 + d.vec_off;
+        double quad = 0.0, lin = 0.0;
+        for (int n = threadIdx.x; n < N; n += 32) {
+            const double xn = odd_of(kb[n], L);
+            double s = 0.0;
+            for (int m = 0; m < N; ++m) s = fma(G64[(long long)n * N + m], (double)odd_of(kb[m], L), s);
+            quad = fma(xn, s, quad);
+            lin = fma(xn, z64[n], lin);
+        }
+        for (int o = 16; o; o >>= 1) {
+            quad += __shfl_xor_sync(0xffffffffu, quad, o);
+            lin += __shfl_xor_sync(0xffffffffu, lin, o);
+        }
+        if (threadIdx.x == 0 && A.best_f_out) A.best_f_out[b] = -(A.yy[b] - 2.0 * lin + quad) * d.inv_s2;
+    }
+    if (A.best_idx) {
+        for (int i = threadIdx.x; i < nt; i += blockDim.x)
+            A.best_idx[d.ant_off + i] = (int8_t)((gray_of(kb[i]) << B) | gray_of(kb[nt + i]));
+    }
+    if (!A.llr) return;
+
+    // soft output: thread (n, sp) handles samples s = sp, sp + split, ...
+    const int split = max(1, (int)blockDim.x / N);
+    const int n = threadIdx.x % N, sp = threadIdx.x / N;
+    const bool active = sp < split && (int)threadIdx.x < split * N;
+    T vp[3] = {-INFINITY, -INFINITY, -INFINITY}, vm[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (active) {
+        const T gnn = G[(long long)n * gstride + n];
+        const double fref = s_fref;
+        for (int s = sp; s < Np; s += split) {
+            const int8_t *ks = S + (long long)s * N;
+            T Dn = T(0);
+            for (int m = 0; m < N; ++m) Dn = fma(G[(long long)n * gstride + m], (T)odd_of(ks[m], L), Dn);
+            const int k = ks[n];
+            const T r = z[n] - Dn;
+            const T fs = (T)(f[s] - fref);
+            const int g = gray_of(k);
+            for (int p = 0; p < B; ++p) {
+                const int mask = 1 << (B - 1 - p);
+                const int kpl = level_of_gray(g & ~mask), kmi = level_of_gray(g | mask);
+                const T dp = T(2 * (kpl - k)), dm = T(2 * (kmi - k));
+                const T dfp = inv_s2 * (T(2) * dp * r - dp * dp * gnn);
+                const T dfm = inv_s2 * (T(2) * dm * r - dm * dm * gnn);
+                const T gam = (dfp - dfm) / tau;
+                const T ap = w * (fs + dfp) - E<T>::softplus(-gam);
+                const T am = w * (fs + dfm) - E<T>::softplus(gam);
+                vp[p] = lse_push(vp[p], ap);
+                vm[p] = lse_push(vm[p], am);
+            }
+        }
+    }
+    // merge the partial sums of the split threads of each dimension
+    for (int r = 0; r < split; ++r) {
+        __syncthreads();
+        if (active && sp == r) {
+            for (int p = 0; p < B; ++p) {
+                T *slot = s_part + 2 * (p * kMaxN + n);
+                if (r == 0) { slot[0] = vp[p]; slot[1] = vm[p]; }
+                else { slot[0] = lse_push(slot[0], vp[p]); slot[1] = lse_push(slot[1], vm[p]); }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * B; e += blockDim.x) {
+        const int nn = e / B, p = e % B;
+        const T *slot = s_part + 2 * (p * kMaxN + nn);
+        const T llr = slot[0] - slot[1];
+        if (!isfinite((double)llr)) set_status(A.status, kStatusNumeric);
+        const int ant = nn % nt, part = nn / nt;
+        A.llr[d.bit_off + (long long)ant * 2 * B + part * B + p] = (float)llr;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_estimate(const EstimateArgs &a, bool fp64, cudaStream_t s)
+{
+    if (a.n_channels <= 0) return cudaSuccess;
+    if (fp64) estimate_kernel<double><<<a.n_channels, 256, 0, s>>>(a);
+    else estimate_kernel<float><<<a.n_channels, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mcmcdet

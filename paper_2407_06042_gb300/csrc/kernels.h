@@ -1,0 +1,124 @@
+// kernels.h -- argument blocks and host launchers shared by the CUDA translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mcmcdet {
+
+struct PrepArgs {
+    const ChannelDesc *desc;
+    const float2 *H;        // packed complex channels (FP32)
+    const float2 *y;        // packed received vectors (FP32)
+    double *Gc;             // complex Gram matrices, Nt^2 complex per channel (scratch)
+    double *zc;             // complex matched filters, Nt complex per channel (scratch)
+    double *Mc;             // complex (G + gamma I)^{-1}, Nt^2 complex per channel (scratch)
+    double *gj;             // Gauss-Jordan block in global memory when not staged (scratch)
+    double *yy;             // ||y||^2 per channel
+    double *G64;            // Gt, N x N per channel
+    double *GM64;           // P~ Gt, N x N per channel (preconditioned)
+    double *z64, *w64;      // zt, wt (FP64)
+    float *z32, *w32;       // zt, wt (FP32)
+    float *bt32;            // CUDA-core GEMM operand (FP32), N x NOp per channel, or null
+    double *bt64;           // CUDA-core GEMM operand (FP64), or null
+    unsigned *status;
+    int stage_h;            // stage H and y in shared memory
+    int stage_gj;           // run Gauss-Jordan in shared memory
+};
+
+struct InitArgs {
+    const ChannelDesc *desc;
+    int8_t *states;
+    int n_channels;
+    int chains;
+    long long items_per_channel;   // (chains / 4) * max N
+    uint32_t key0, key1;
+};
+
+struct RefreshArgs {
+    const ChannelDesc *desc;
+    const int8_t *states;
+    const double *G64;
+    const double *z64;
+    const double *yy;
+    double *f;
+    double *best_f;
+    int8_t *best_states;
+    unsigned *status;
+    int n_channels;
+    int chains;
+    int reset_best;
+};
+
+// One chain-kernel work item: chains [c0, c0 + nc) of channel b.
+struct WorkItem {
+    int b;
+    int c0;
+    int nc;
+    int pad;
+};
+
+struct ChainArgs {
+    const ChannelDesc *desc;
+    const WorkItem *items;
+    int n_items;
+    int chains;             // Np
+    int cg;                 // chains per work item (capacity of the shared-memory arrays)
+    int max_n;              // largest N in the batch
+    int max_nop;            // largest NOp in the batch
+    int bt_in_smem;         // copy the GEMM operand to shared memory
+    int iterations;
+    long long t_offset;
+    int refresh_period;
+    uint32_t key0, key1;
+    const void *bt;         // float* or double* operand (N x NOp per channel)
+    const void *z;          // float* or double* zt
+    const void *w;          // float* or double* wt
+    const double *G64;      // FP64 Gt for the periodic refresh
+    const double *z64;
+    const double *yy;
+    int8_t *states;
+    int8_t *best_states;
+    double *f;
+    double *best_f;
+    unsigned long long *accepts;
+    unsigned long long *drift_bits;   // max |f_tracked - f_fp64| as ordered bits
+    unsigned *status;
+    // tcgen05 engine only
+    const uint8_t *tc_ops;  // per-channel packed BF16 operand blocks
+    int split_terms;
+    int tc_ctas_per_sm;
+};
+
+struct EstimateArgs {
+    const ChannelDesc *desc;
+    const int8_t *states;
+    const int8_t *best_states;
+    const double *f;
+    const double *best_f;
+    const void *G;          // float* or double* Gt (N x N per channel), or the Bt operand
+    int g_is_bt;            // G points at the N x NOp operand (row stride NOp)
+    const void *z;          // float* or double* zt
+    const double *G64;
+    const double *z64;
+    const double *yy;
+    int n_channels;
+    int chains;
+    int8_t *best_idx;       // out
+    float *llr;             // out
+    double *best_f_out;     // out
+    unsigned *status;
+};
+
+size_t chain_smem_bytes_simt(int elem_size, int cg, int max_n, int max_nop, bool bt_in_smem);
+
+cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
+                        size_t gj_stage_bytes, bool preconditioned, cudaStream_t s);
+cudaError_t launch_init_states(const InitArgs &a, cudaStream_t s);
+cudaError_t launch_refresh(const RefreshArgs &a, cudaStream_t s);
+cudaError_t launch_chains_simt(const ChainArgs &a, bool fp64, size_t smem, cudaStream_t s);
+cudaError_t launch_estimate(const EstimateArgs &a, bool fp64, cudaStream_t s);
+
+}  // namespace mcmcdet
