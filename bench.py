@@ -207,12 +207,20 @@ def main():
 
     precision = args.precision
     if precision == "auto":
+        precision = "fp32"
         try:
-            probe = pkg.Detector(max_channels=1, max_nt=32, max_nr=32, chains=Np, precision="mixed")
+            probe = pkg.Detector(max_channels=1, max_nt=w["nt"], max_nr=w["nr"], chains=Np,
+                                 precision="mixed")
+            one = batch.subset([0])
+            hp = torch.from_numpy(np.ascontiguousarray(one.H).view(np.float32).copy()).to(dev)
+            yp = torch.from_numpy(np.ascontiguousarray(one.y).view(np.float32).copy()).to(dev)
+            sp = torch.from_numpy(one.sigma2.astype(np.float32)).to(dev)
+            torch.cuda.synchronize()
+            probe.preprocess(one.nt, one.nr, one.qam, hp, one.H_off, yp, one.y_off, sp)
             probe.destroy()
             precision = "mixed"
         except pkg.McmcError:
-            precision = "fp32"
+            pass
 
     stream = torch.cuda.current_stream()
     Hd = torch.from_numpy(np.ascontiguousarray(batch.H).view(np.float32).copy()).to(dev)

@@ -1,25 +1,651 @@
-// chains_tc.cu -- tcgen05 chain kernel (MIXED precision). Placeholder plan: not yet available.
+// chains_tc.cu -- DMALA chain kernel with the Gram products on tcgen05 tensor cores (MIXED).
+//
+// Each CTA owns a group of C chains of one channel (persistent over work items). Per transition
+// (Algorithm 1's loop body):
+//   1. every thread draws x'_n for its (dimension, 8 chains) from the cached drift slope of the
+//      current state (Eqs. (15)-(17) / (21)) and writes x' as BF16 (exact odd integers) into the
+//      shared-memory B operand [C chains x K];
+//   2. one thread issues D = A * X'^T on the tensor core: A = [Gt | P~ Gt] rows (split into
+//      `split_terms` BF16 terms, FP32 accumulation in TMEM), staged once per work item by a TMA
+//      bulk copy; completion is signalled through an mbarrier;
+//   3. every thread reads its TMEM lane (one row of A = one dimension of Gt or P~Gt) for its
+//      16 columns (chains), swaps halves with its partner lane, and evaluates the reverse factor
+//      and the energy difference (Eqs. (3), (18));
+//   4. per chain the log acceptance ratio is reduced over dimensions (warp shuffles, then the
+//      four TMEM lane quadrants through shared memory) and the MH test is taken;
+//   5. accepted chains keep x', Gt x' and the drift slope of x'.
+// A-operand row layout (128 rows per tile t): row 32q + l holds dimension 64t + 16q + (l & 15) of
+// Gt (l < 16) or of P~ Gt (l >= 16), so each warp's TMEM quadrant carries both quantities of
+// 16 dimensions. Both operands are K-major, no swizzle, in 8 x 16-byte core matrices: K-adjacent
+// core matrices 128 B apart (LBO), 8-row groups (K/8)*128 B apart (SBO).
+// Every wait is bounded: a wait that runs out sets the timeout status bit, the CTA stops issuing
+// work, frees its TMEM and returns.
 #include "tc_plan.h"
+
+#include <cuda_bf16.h>
 
 namespace mcmcdet {
 
-bool tc_make_plan(const std::vector<ChannelDesc> &, int, int, size_t, int, TcPlan *plan)
+namespace {
+
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    *plan = TcPlan{};
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
     return false;
 }
 
-long long tc_operand_bytes(const ChannelDesc &, const TcPlan &) { return 0; }
-
-cudaError_t tc_launch_pack(const TcPlan &, const ChannelDesc *, int, const double *, const double *,
-                           uint8_t *, cudaStream_t)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    return cudaErrorNotSupported;
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-cudaError_t tc_launch_chains(const ChainArgs &, const TcPlan &, cudaStream_t)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate)
 {
-    return cudaErrorNotSupported;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Proposal factor (same arithmetic as the CUDA-core FP32 kernel): logits a (j - k) - cq (j - k)^2.
+struct Fac {
+    float mx;
+    float total;
+    float S[kMaxL];
+};
+
+__device__ __forceinline__ float logit_of(float a, float cq, int j, int k)
+{
+    const float dj = (float)(j - k);
+    return a * dj - cq * dj * dj;
+}
+
+__device__ __forceinline__ void factor(float a, float cq, int k, int L, Fac &F)
+{
+    float lg[kMaxL];
+    float mx = -1e30f;
+#pragma unroll
+    for (int j = 0; j < kMaxL; ++j) {
+        lg[j] = logit_of(a, cq, j, k);
+        if (j < L) mx = lg[j] > mx ? lg[j] : mx;
+    }
+    F.mx = mx;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxL; ++j) {
+        if (j < L) acc += __expf(lg[j] - mx);
+        F.S[j] = acc;
+    }
+    F.total = acc;
+}
+
+// 8 values per lane, summed over the 16 lanes of a half warp and scattered: afterwards lanes
+// 2j and 2j+1 of the half hold the sum of value j.
+__device__ __forceinline__ float reduce_scatter16(const float (&v)[8], int dl)
+{
+    float a[4], b2[2];
+    const bool hi8 = dl & 8, hi4 = dl & 4, hi2 = dl & 2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = hi8 ? v[i] : v[4 + i];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 8);
+        a[i] = (hi8 ? v[4 + i] : v[i]) + recv;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = hi4 ? a[i] : a[2 + i];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 4);
+        b2[i] = (hi4 ? a[2 + i] : a[i]) + recv;
+    }
+    const float send = hi2 ? b2[0] : b2[1];
+    const float recv = __shfl_xor_sync(0xffffffffu, send, 2);
+    float c = (hi2 ? b2[1] : b2[0]) + recv;
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+// Shared-memory layout of the kernel (bytes).
+struct TcLayout {
+    uint32_t a, b, red, dred, acc, impr, ref, fref, bar, tmem, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
+{
+    TcLayout L{};
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes, uint32_t al) {
+        o = (o + al - 1) / al * al;
+        const uint32_t r = o;
+        o += bytes;
+        return r;
+    };
+    L.a = take((uint32_t)S * MT * 128 * Kp * 2, 1024);
+    L.b = take((uint32_t)C * Kp * 2, 1024);
+    L.red = take(4u * C * 4, 16);
+    L.dred = take(4u * C * 4, 16);
+    L.acc = take((uint32_t)C * 4, 16);
+    L.impr = take((uint32_t)C * 4, 16);
+    L.ref = take((uint32_t)C * 8, 16);       // FP64 refresh results per chain
+    L.fref = take((uint32_t)C * kMaxN, 16);  // states for the FP64 refresh
+    L.bar = take(16, 8);
+    L.tmem = take(4, 4);
+    L.total = (o + 127) / 128 * 128;
+    return L;
+}
+
+template <int MT>
+__global__ void __launch_bounds__(512, 1) chains_tc_kernel(const ChainArgs A, const int C,
+                                                           const int S, const int Kp)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const TcLayout lay = tc_layout(S, MT, Kp, C);
+    unsigned char *sA = smem + lay.a;
+    unsigned char *sB = smem + lay.b;
+    float *red = reinterpret_cast<float *>(smem + lay.red);
+    float *dred = reinterpret_cast<float *>(smem + lay.dred);
+    int *sacc = reinterpret_cast<int *>(smem + lay.acc);
+    int *simpr = reinterpret_cast<int *>(smem + lay.impr);
+    double *sref = reinterpret_cast<double *>(smem + lay.ref);
+    int8_t *sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.tmem);
+    const uint32_t bar_tma = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, cgi = warp >> 2, h = lane >> 4, dl = lane & 15;
+    const int ncols_alloc = A.tc_tmem_cols;   // TMEM columns to allocate (power of 2, >= 32)
+    const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+
+    if (tid == 0) {
+        mbar_init(bar_tma, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(ncols_alloc));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    uint32_t tma_phase = 0, mma_phase = 0;
+    bool alive = true;
+
+    // Issue the MMAs of one transition (thread 0) and wait for them (everyone).
+    auto gemm = [&]() -> bool {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (int t = 0; t < MT; ++t) {
+                uint32_t first = 1;
+                for (int s = 0; s < S; ++s) {
+                    const uint32_t ab = a0 + (uint32_t)((s * MT + t) * 128 * Kp * 2);
+                    for (int ks = 0; ks < Kp / 16; ++ks) {
+                        const uint64_t da = smem_desc(ab + ks * 256u, 128u, sbo);
+                        const uint64_t db = smem_desc(b0 + ks * 256u, 128u, sbo);
+                        mma_bf16(tmem + (uint32_t)(t * C), da, db, idesc, first ? 0u : 1u);
+                        first = 0;
+                    }
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    bar_mma)
+                : "memory");
+        }
+        const bool ok = mbar_wait(bar_mma, mma_phase);
+        mma_phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return !__syncthreads_or(!ok);   // every thread takes the same branch
+    };
+
+    for (int item = blockIdx.x; item < A.n_items && alive; item += gridDim.x) {
+        const WorkItem it = A.items[item];
+        const ChannelDesc d = A.desc[it.b];
+        const int N = d.N, L = d.L, nC = it.nc;
+        const bool pre = d.NO > N;
+        const float clin = (float)d.clin, cq = (float)d.cquad, cf = (float)d.cf;
+
+        // stage this channel's A operand (TMA bulk copy, mbarrier completion)
+        const uint32_t abytes = (uint32_t)S * MT * 128u * (uint32_t)Kp * 2u;
+        if (tid == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_tma),
+                         "r"(abytes)
+                         : "memory");
+            const unsigned char *src = A.tc_ops + d.tc_off;
+            const uint32_t chunk = 1u << 16;
+            for (uint32_t off = 0; off < abytes; off += chunk) {
+                const uint32_t n = abytes - off < chunk ? abytes - off : chunk;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
+                    "%2, [%3];" ::"r"(smem_u32(sA) + off),
+                    "l"(src + off), "r"(n), "r"(bar_tma)
+                    : "memory");
+            }
+        }
+        // per-thread constants and state
+        float zt[MT], wt[MT];
+        int nd[MT];
+        int8_t k[MT][8], kb[MT][8];
+        float Dg[MT][8], sl[MT][8];
+        const int cbase = 16 * cgi + 8 * h;   // first of this thread's 8 chains (CTA-local)
+        const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
+        const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const int n = 64 * t + 16 * q + dl;
+            nd[t] = n;
+            const bool v = n < N;
+            zt[t] = v ? gz[n] : 0.f;
+            wt[t] = v ? gw[n] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = cbase + j;
+                int8_t kv = 0, kbv = 0;
+                if (v && c < nC) {
+                    const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
+                    kv = A.states[e];
+                    kbv = A.best_states[e];
+                }
+                k[t][j] = kv;
+                kb[t][j] = kbv;
+            }
+        }
+        double fcur = 0.0, fbest = 0.0;
+        unsigned cnt = 0;
+        if (tid < nC) {
+            const long long ci = (long long)it.b * A.chains + it.c0 + tid;
+            fcur = A.f[ci];
+            fbest = A.best_f[ci];
+        }
+        // write x (current states) as the B operand; zero the padding
+        auto write_b = [&](int8_t (&kk)[MT][8]) {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                const int n = nd[t];
+                if (n >= Kp) continue;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = cbase + j;
+                    if (c >= C) continue;
+                    const float xv = (n < N && c < nC) ? (float)odd_of(kk[t][j], L) : 0.f;
+                    const uint32_t off = (uint32_t)(c >> 3) * sbo + (uint32_t)(n >> 3) * 128u +
+                                         (uint32_t)(c & 7) * 16u + (uint32_t)(n & 7) * 2u;
+                    *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16_rn(xv);
+                }
+            }
+        };
+        // zero the whole B operand once (covers K padding rows not owned by any thread)
+        for (int e = tid; e < C * Kp * 2 / 16; e += blockDim.x)
+            reinterpret_cast<uint4 *>(sB)[e] = make_uint4(0, 0, 0, 0);
+        __syncthreads();
+        write_b(k);
+        if (__syncthreads_or(!mbar_wait(bar_tma, tma_phase))) {
+            alive = false;
+            set_status(A.status, kStatusTimeout);
+        }
+        tma_phase ^= 1u;
+        if (alive && !gemm()) { alive = false; set_status(A.status, kStatusTimeout); }
+        // read D for the current states -> Gt x and the drift slope
+        auto read_d = [&](float (&g)[MT][8], float (&m)[MT][8]) {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * C + 16 * cgi), v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float send = h ? v[j] : v[8 + j];
+                    const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
+                    g[t][j] = h ? recv : v[j];
+                    m[t][j] = h ? v[8 + j] : recv;
+                }
+            }
+        };
+        {
+            float g[MT][8], m[MT][8];
+            if (alive) read_d(g, m);
+#pragma unroll
+            for (int t = 0; t < MT; ++t)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    Dg[t][j] = alive ? g[t][j] : 0.f;
+                    sl[t][j] = alive ? clin * (pre ? (wt[t] - m[t][j]) : (zt[t] - g[t][j])) : 0.f;
+                }
+        }
+
+        for (int i = 0; i < A.iterations && alive; ++i) {
+            const uint32_t t_it = (uint32_t)(A.t_offset + 1 + i);
+            float part[8], dpart[8];
+            int8_t kp[MT][8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { part[j] = 0.f; dpart[j] = 0.f; }
+            // 1. proposal draw
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                const int n = nd[t];
+                const bool v = n < N;
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq) {
+                    const int cq0 = cbase + 4 * qq;
+                    U4 w = {0, 0, 0, 0};
+                    if (v && cq0 < nC)
+                        w = philox4x32_10(t_it, (uint32_t)n, (uint32_t)it.b,
+                                          (uint32_t)((it.c0 + cq0) >> 2), A.key0, A.key1);
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * qq + jj;
+                        int sel = k[t][j];
+                        if (v && cq0 + jj < nC) {
+                            Fac F;
+                            factor(sl[t][j], cq, k[t][j], L, F);
+                            const float target = uniform_f(word_of(w, jj)) * F.total;
+                            sel = L - 1;
+#pragma unroll
+                            for (int l = kMaxL - 1; l >= 0; --l)
+                                if (l < L && target < F.S[l]) sel = l;
+                            part[j] -= logit_of(sl[t][j], cq, sel, k[t][j]) - F.mx - __logf(F.total);
+                        }
+                        kp[t][j] = (int8_t)sel;
+                    }
+                }
+            }
+            write_b(kp);
+            // 2. D' = A X'^T on the tensor core
+            if (!gemm()) { alive = false; set_status(A.status, kStatusTimeout); break; }
+            // 3. reverse factor and energy difference
+            float gp[MT][8], mp[MT][8];
+            read_d(gp, mp);
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                const bool v = nd[t] < N;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float ap = clin * (pre ? (wt[t] - mp[t][j]) : (zt[t] - gp[t][j]));
+                    mp[t][j] = ap;   // keep the slope of x' for the update
+                    if (v && cbase + j < nC) {
+                        Fac F;
+                        factor(ap, cq, kp[t][j], L, F);
+                        part[j] += logit_of(ap, cq, k[t][j], kp[t][j]) - F.mx - __logf(F.total);
+                        dpart[j] += (float)(2 * (kp[t][j] - k[t][j])) *
+                                    (2.f * zt[t] - Dg[t][j] - gp[t][j]);
+                    }
+                }
+            }
+            // 4. per-chain reduction and the MH decision
+            const float rs = reduce_scatter16(part, dl);
+            const float rd = reduce_scatter16(dpart, dl);
+            if ((dl & 1) == 0) {
+                const int c = cbase + (dl >> 1);
+                red[q * C + c] = rs;
+                dred[q * C + c] = rd;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid < nC) {
+                const int c = tid;
+                const float s = red[c] + red[C + c] + red[2 * C + c] + red[3 * C + c];
+                const float sd = dred[c] + dred[C + c] + dred[2 * C + c] + dred[3 * C + c];
+                const int cc = it.c0 + c;
+                const U4 w = philox4x32_10(t_it, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
+                                           A.key0, A.key1);
+                const float logr = s + cf * sd;
+                const float loga = logr < 0.f ? logr : 0.f;
+                const float logu = __logf(uniform_f(word_of(w, cc & 3)));
+                int ok = logu < loga;
+                if (!isfinite(logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
+                int im = 0;
+                if (ok) {
+                    fcur += d.inv_s2 * (double)sd;
+                    cnt += 1;
+                    if (fcur > fbest) { fbest = fcur; im = 1; }
+                }
+                sacc[c] = ok;
+                simpr[c] = im;
+            }
+            __syncthreads();
+            // 5. accepted chains take x' and its caches
+            bool any_ref = false;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = cbase + j;
+                const int ok = c < nC ? sacc[c] : 0;
+                const int im = c < nC ? simpr[c] : 0;
+#pragma unroll
+                for (int t = 0; t < MT; ++t) {
+                    if (ok) {
+                        k[t][j] = kp[t][j];
+                        Dg[t][j] = gp[t][j];
+                        sl[t][j] = mp[t][j];
+                    }
+                    if (im) kb[t][j] = kp[t][j];
+                }
+            }
+            // periodic FP64 refresh of the tracked energies (decisions never read them)
+            if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
+                any_ref = true;
+#pragma unroll
+                for (int t = 0; t < MT; ++t) {
+                    if (nd[t] >= N) continue;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (cbase + j < nC) sfs[(cbase + j) * kMaxN + nd[t]] = k[t][j];
+                }
+            }
+            if (any_ref) {
+                __syncthreads();
+                const double *G = A.G64 + d.mat_off;
+                const double *z = A.z64 + d.vec_off;
+                for (int c = warp; c < nC; c += blockDim.x >> 5) {
+                    double quad = 0.0, lin = 0.0;
+                    for (int n = lane; n < N; n += 32) {
+                        const double xn = odd_of(sfs[c * kMaxN + n], L);
+                        double s = 0.0;
+                        for (int m = 0; m < N; ++m)
+                            s = fma(G[(size_t)n * N + m], (double)odd_of(sfs[c * kMaxN + m], L), s);
+                        quad = fma(xn, s, quad);
+                        lin = fma(xn, z[n], lin);
+                    }
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) {
+                        quad += __shfl_xor_sync(0xffffffffu, quad, o);
+                        lin += __shfl_xor_sync(0xffffffffu, lin, o);
+                    }
+                    if (lane == 0) sref[c] = -(A.yy[it.b] - 2.0 * lin + quad) * d.inv_s2;
+                }
+                __syncthreads();
+                if (tid < nC) {
+                    const double dr = fabs(sref[tid] - fcur);
+                    atomicMax(A.drift_bits, (unsigned long long)__double_as_longlong(dr));
+                    fcur = sref[tid];
+                }
+            }
+        }
+        // write back this work item
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const int n = nd[t];
+            if (n >= N) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = cbase + j;
+                if (c >= nC) continue;
+                const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
+                A.states[e] = k[t][j];
+                A.best_states[e] = kb[t][j];
+            }
+        }
+        if (tid < nC) {
+            const long long ci = (long long)it.b * A.chains + it.c0 + tid;
+            A.f[ci] = fcur;
+            A.best_f[ci] = fbest;
+            A.accepts[ci] += cnt;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(ncols_alloc));
+}
+
+// ------------------------------------------------------------------------------------------
+// Operand packing: Gt / P~Gt (FP64) -> `S` BF16 split terms in the core-matrix image.
+// ------------------------------------------------------------------------------------------
+__global__ void pack_kernel(const ChannelDesc *desc, const double *G64, const double *GM64,
+                            uint8_t *ops, int S, int MT, int Kp)
+{
+    const ChannelDesc d = desc[blockIdx.x];
+    const int N = d.N;
+    const bool pre = d.NO > N;
+    __nv_bfloat16 *base = reinterpret_cast<__nv_bfloat16 *>(ops + d.tc_off);
+    const int per_term = MT * 128 * Kp;
+    for (int e = threadIdx.x; e < per_term; e += blockDim.x) {
+        const int t = e / (128 * Kp), rem = e % (128 * Kp);
+        const int r = rem / Kp, kk = rem % Kp;
+        const int q = r >> 5, l = r & 31;
+        const int n = 64 * t + 16 * q + (l & 15), part = l >> 4;
+        double v = 0.0;
+        if (n < N && kk < N) {
+            if (part == 0) v = G64[d.mat_off + (long long)n * N + kk];
+            else if (pre) v = GM64[d.mat_off + (long long)n * N + kk];
+        }
+        // core-matrix position of (r, kk) within the tile
+        const int off = (r >> 3) * (Kp / 8) * 64 + (kk >> 3) * 64 + (r & 7) * 8 + (kk & 7);
+        double rem_v = v;
+        for (int s = 0; s < S; ++s) {
+            const __nv_bfloat16 bv = __float2bfloat16_rn((float)rem_v);
+            rem_v -= (double)__bfloat162float(bv);
+            base[(size_t)(s * MT + t) * 128 * Kp + off] = bv;
+        }
+    }
+}
+
+int pow2_at_least(int v)
+{
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+bool tc_make_plan(const std::vector<ChannelDesc> &desc, int chains, int split_terms,
+                  size_t smem_optin, int sm_count, TcPlan *plan)
+{
+    *plan = TcPlan{};
+    int maxn = 0;
+    for (const auto &c : desc) maxn = std::max(maxn, c.N);
+    if (maxn < 1 || maxn > 128) return false;
+    const int MT = (maxn + 63) / 64;
+    const int Kp = (maxn + 15) / 16 * 16;
+    // 32 chains per CTA: 256 threads at <= 128 registers, two CTAs per SM overlap one CTA's
+    // tensor-core wait with the other's proposal arithmetic
+    int C = std::min(32, (chains + 15) / 16 * 16);
+    const int S = split_terms;
+    TcLayout L = tc_layout(S, MT, Kp, C);
+    while (L.total > smem_optin && C > 16) {
+        C -= 16;
+        L = tc_layout(S, MT, Kp, C);
+    }
+    if (L.total > smem_optin) return false;
+    plan->valid = 1;
+    plan->chains_per_cta = C;
+    plan->m_tiles = MT;
+    plan->kdim = Kp;
+    plan->max_n = maxn;
+    plan->split_terms = S;
+    plan->threads = 8 * C;                    // 4 TMEM quadrants x C/16 column groups x 32
+    plan->tmem_cols = pow2_at_least(MT * C);
+    const int by_smem = (int)(228 * 1024 / (L.total + 1024));
+    const int by_thr = std::min(2048 / plan->threads, 65536 / (plan->threads * 128));
+    const int by_tmem = 512 / plan->tmem_cols;
+    plan->ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_thr), by_tmem));
+    plan->smem = L.total;
+    (void)sm_count;
+    return true;
+}
+
+long long tc_operand_bytes(const ChannelDesc &, const TcPlan &plan)
+{
+    return (long long)plan.split_terms * plan.m_tiles * 128 * plan.kdim * 2;
+}
+
+cudaError_t tc_launch_pack(const TcPlan &plan, const ChannelDesc *desc, int n_channels,
+                           const double *G64, const double *GM64, uint8_t *tc_ops, cudaStream_t s)
+{
+    if (n_channels <= 0) return cudaSuccess;
+    pack_kernel<<<n_channels, 256, 0, s>>>(desc, G64, GM64, tc_ops, plan.split_terms,
+                                           plan.m_tiles, plan.kdim);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStream_t s)
+{
+    if (a_in.n_items <= 0) return cudaSuccess;
+    ChainArgs a = a_in;
+    a.tc_tmem_cols = plan.tmem_cols;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(a.n_items, std::max(1, sms * plan.ctas_per_sm));
+    cudaError_t e;
+    if (plan.m_tiles == 1) {
+        auto k = chains_tc_kernel<1>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem)) != cudaSuccess) return e;
+        k<<<grid, plan.threads, plan.smem, s>>>(a, plan.chains_per_cta, plan.split_terms, plan.kdim);
+    } else {
+        auto k = chains_tc_kernel<2>;
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem)) != cudaSuccess) return e;
+        k<<<grid, plan.threads, plan.smem, s>>>(a, plan.chains_per_cta, plan.split_terms, plan.kdim);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace mcmcdet

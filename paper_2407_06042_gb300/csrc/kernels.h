@@ -89,7 +89,7 @@ struct ChainArgs {
     // tcgen05 engine only
     const uint8_t *tc_ops;  // per-channel packed BF16 operand blocks
     int split_terms;
-    int tc_ctas_per_sm;
+    int tc_tmem_cols;       // TMEM columns each CTA allocates
 };
 
 struct EstimateArgs {

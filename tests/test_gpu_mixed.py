@@ -1,0 +1,95 @@
+"""GPU parity of the tensor-core (MIXED precision) chain kernel against the FP64 oracle.
+
+The Gram products run on tcgen05 from BF16 split terms of Gt and P~Gt with FP32 accumulation;
+everything else is FP32. With three split terms the products carry ~24 significant bits, as in
+FP32, and the FP32 windows apply (2e-3 on |log A - log u|, 2e-4 on the CDF margin). With two
+terms (~16 bits) the same protocol runs with windows 32x wider: the split error 2^-17 relative
+per product replaces FP32's 2^-24 in the error of Gt x' and of the drift slope.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(n=16, snr=12.0, seed=1001):
+    return workload.rayleigh_batch(4, 4, 16, [snr], n, seed)
+
+
+@pytest.mark.parametrize("terms,w_cat,w_acc", [(3, 2e-4, 2e-3), (2, 6.4e-3, 6.4e-2)])
+def test_mixed_step_parity(terms, w_cat, w_acc):
+    b = _small(16)
+    det = H.make_detector(b, chains=32, precision="mixed", split_terms=terms, seed=0)
+    r = H.step_parity(det, b, H.targets(b), seed=0, steps=25, w_cat=w_cat, w_acc=w_acc)
+    assert r["bad"] == 0, r
+    assert r["mism"] <= max(4, r["steps"] // 1000), r
+    det.destroy()
+
+
+def test_mixed_one_launch_equals_single_step_launches():
+    b = _small(6)
+    d1 = H.make_detector(b, chains=32, precision="mixed")
+    d1.run_chains(20)
+    s1, _ = d1.get_chains()
+    d2 = H.make_detector(b, chains=32, precision="mixed")
+    for t in range(20):
+        d2.run_chains(1, t)
+    s2, _ = d2.get_chains()
+    np.testing.assert_array_equal(s1, s2)
+    d1.destroy()
+    d2.destroy()
+
+
+@pytest.mark.parametrize("shapes", [
+    [(36, 40, 16, 18.0), (33, 33, 64, 26.0)],          # N = 72, 66: ragged K and dimensions
+    [(64, 64, 16, 20.0), (64, 128, 4, 8.0)],           # N = 128: two A-operand tiles
+    [(1, 2, 4, 6.0), (3, 3, 64, 20.0), (8, 16, 16, 14.0)],
+])
+def test_mixed_step_parity_shapes(shapes):
+    b = workload.generate(shapes, 91)
+    det = H.make_detector(b, chains=36, precision="mixed", split_terms=3, seed=2)
+    r = H.step_parity(det, b, H.targets(b), seed=2, steps=6, w_cat=2e-4, w_acc=2e-3)
+    assert r["bad"] == 0, r
+    assert r["mism"] <= max(4, r["steps"] // 500), r
+    det.destroy()
+
+
+def test_mixed_ber_within_binomial_interval_of_oracle():
+    """4x4 16-QAM at 12 dB, 1000 channels, 32 chains x 100 iterations: the GPU's uncoded BER of
+    sign(LLR) lies inside the 95% Clopper-Pearson interval of the oracle's."""
+    from scipy.stats import beta
+    b = workload.workload("rayleigh_4x4_16qam")
+    det = H.make_detector(b, chains=32, precision="mixed", seed=0)
+    det.run_chains(100)
+    out = det.estimate()
+    det.destroy()
+    ref = oracle.detect_batch(b, chains=32, iterations=100, seed=0)
+    bits = b.tx_bits.astype(int)
+    e_gpu = int(((out["llr"] < 0).astype(int) != bits).sum())
+    e_ref = int(((np.concatenate([r["llr"] for r in ref]) < 0).astype(int) != bits).sum())
+    n = bits.size
+    lo = beta.ppf(0.025, e_ref, n - e_ref + 1) if e_ref else 0.0
+    hi = beta.ppf(0.975, e_ref + 1, n - e_ref)
+    assert lo <= e_gpu / n <= hi, (e_gpu, e_ref, n)
+
+
+def test_mixed_energies_refresh():
+    """FP64 refresh every R transitions: the tracked energies equal FP64 evaluations of the
+    states right after a refresh point, and the reported drift is small."""
+    b = _small(4, snr=20.0)
+    det = H.make_detector(b, chains=32, precision="mixed", refresh_period=10)
+    det.run_chains(30)
+    out = det.estimate(stats=True)
+    flat, f = det.get_chains()
+    st = H.split_states(det, b, flat)
+    tg = H.targets(b)
+    for ch in range(b.n_channels):
+        for c in range(32):
+            fx = oracle.f_value(tg[ch].Hr, tg[ch].yr, tg[ch].sigma2, tg[ch].values(st[ch][c]))
+            assert abs(f[ch * 32 + c] - fx) <= 1e-9 * abs(fx)
+    assert out["stats"]["refresh_drift"] < 1e-2
+    det.destroy()
