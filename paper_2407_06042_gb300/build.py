@@ -42,7 +42,7 @@ def sources():
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or os.environ.get("MCMCDET_NVCC_EXTRA"):
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
@@ -60,6 +60,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
     if verbose:
         flags += ["-Xptxas", "-v"]
+    extra = os.environ.get("MCMCDET_NVCC_EXTRA", "").split()
+    flags += extra
     objs = []
 
     def compile_one(src):

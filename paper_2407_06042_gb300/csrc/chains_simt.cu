@@ -13,6 +13,7 @@
 // several launches (resume) makes exactly the same decisions as one launch.
 #include "common.cuh"
 #include "kernels.h"
+#include "proposal.cuh"
 
 namespace mcmcdet {
 
@@ -138,34 +139,71 @@ __device__ __forceinline__ T logit_of(T a, T cq, int j, int k)
     return a * dj - cq * dj * dj;
 }
 
-template <typename T>
-__device__ __forceinline__ void factor(T a, T cq, int k, int L, Factor<T> &F)
+template <typename T, int L>
+__device__ __forceinline__ void factor(T a, T cq, int k, Factor<T> &F)
 {
-    T lg[kMaxL];
+    T lg[L];
     T mx = -T(1e30);
 #pragma unroll
-    for (int j = 0; j < kMaxL; ++j) {
+    for (int j = 0; j < L; ++j) {
         lg[j] = logit_of(a, cq, j, k);
-        if (j < L) mx = lg[j] > mx ? lg[j] : mx;
+        mx = lg[j] > mx ? lg[j] : mx;
     }
     F.mx = mx;
     T acc = T(0);
 #pragma unroll
-    for (int j = 0; j < kMaxL; ++j) {
-        if (j < L) acc += M<T>::ex(lg[j] - mx);
+    for (int j = 0; j < L; ++j) {
+        acc += M<T>::ex(lg[j] - mx);
         F.S[j] = acc;
     }
     F.total = acc;
 }
 
-template <typename T, int TCH, int TO>
-__global__ void __launch_bounds__(256) chains_simt_kernel(const ChainArgs A)
+// Draw of one factor and log q of the drawn level. FP64: natural logs, every weight exp'd
+// directly (as the definition reads). FP32: the shared log2-unit arithmetic of proposal.cuh.
+template <typename T, int L>
+__device__ __forceinline__ int draw_level(T a, T cq, T inv2c, int k, uint32_t word, T &logq)
 {
-    const WorkItem it = A.items[blockIdx.x];
-    const ChannelDesc d = A.desc[it.b];
-    const int N = d.N, L = d.L, NOp = d.NOp, cg = A.cg, nC = it.nc;
+    if constexpr (sizeof(T) == 8) {
+        Factor<T> F;
+        factor<T, L>(a, cq, k, F);
+        const T target = M<T>::uni(word) * F.total;
+        int sel = L - 1;
+#pragma unroll
+        for (int l = L - 1; l >= 0; --l)
+            if (target < F.S[l]) sel = l;
+        logq = logit_of(a, cq, sel, k) - F.mx - M<T>::lg(F.total);
+        return sel;
+    } else {
+        float lq;
+        const int sel = factor_draw<L>(a, cq, inv2c, k, uniform_f(word), lq);
+        logq = lq;
+        return sel;
+    }
+}
+
+template <typename T, int L>
+__device__ __forceinline__ T log_q_of(T a, T cq, T inv2c, int k, int j_eval)
+{
+    if constexpr (sizeof(T) == 8) {
+        Factor<T> F;
+        factor<T, L>(a, cq, k, F);
+        return logit_of(a, cq, j_eval, k) - F.mx - M<T>::lg(F.total);
+    } else {
+        return factor_log2q<L>(a, cq, inv2c, k, j_eval);
+    }
+}
+
+// Units: FP64 works in natural logs; FP32 in log2 units (slopes, curvature and the energy
+// scale pre-multiplied by log2 e), as in proposal.cuh.
+template <typename T, int TCH, int TO, int L>
+__device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelDesc &d)
+{
+    const int N = d.N, NOp = d.NOp, cg = A.cg, nC = it.nc;
     const bool pre = d.NO > N;
-    const T clin = (T)d.clin, cq = (T)d.cquad, cf = (T)d.cf;
+    const T unit = sizeof(T) == 8 ? T(1) : (T)kLog2e;
+    const T clin = (T)d.clin * unit, cq = (T)d.cquad * unit, cf = (T)d.cf * unit;
+    const T inv2c = T(0.5) / cq;
     const Layout lay = make_layout(sizeof(T), cg, A.max_n, A.max_nop, A.bt_in_smem);
     extern __shared__ __align__(16) unsigned char smem[];
     T *zt = reinterpret_cast<T *>(smem + lay.zt);
@@ -234,15 +272,10 @@ __global__ void __launch_bounds__(256) chains_simt_kernel(const ChainArgs A)
                 const int c = 4 * cq4 + j;
                 const int e = c * N + n;
                 const int kn = sk[e];
-                Factor<T> F;
-                factor<T>(sa[e], cq, kn, L, F);
-                const T target = M<T>::uni(word_of(w, j)) * F.total;
-                int sel = L - 1;
-#pragma unroll
-                for (int l = kMaxL - 1; l >= 0; --l)
-                    if (l < L && target < F.S[l]) sel = l;
+                T lq;
+                const int sel = draw_level<T, L>(sa[e], cq, inv2c, kn, word_of(w, j), lq);
                 skp[e] = (int8_t)sel;
-                term[e] = -(logit_of(sa[e], cq, sel, kn) - F.mx - M<T>::lg(F.total));
+                term[e] = -lq;
                 xsT[n * cg + c] = (T)odd_of(sel, L);
             }
         }
@@ -256,9 +289,7 @@ __global__ void __launch_bounds__(256) chains_simt_kernel(const ChainArgs A)
             const int kn = sk[e], kpn = skp[e];
             const T dgp = Dp[c * NOp + n];
             const T ap = clin * (pre ? (wt[n] - Dp[c * NOp + N + n]) : (zt[n] - dgp));
-            Factor<T> F;
-            factor<T>(ap, cq, kpn, L, F);
-            term[e] += logit_of(ap, cq, kn, kpn) - F.mx - M<T>::lg(F.total);
+            term[e] += log_q_of<T, L>(ap, cq, inv2c, kpn, kn);
             dterm[e] = T(2 * (kpn - kn)) * (T(2) * zt[n] - sD[e] - dgp);
         }
         __syncthreads();
@@ -277,7 +308,8 @@ __global__ void __launch_bounds__(256) chains_simt_kernel(const ChainArgs A)
                                            A.key0, A.key1);
                 const T logr = s + cf * sd;
                 const T loga = logr < T(0) ? logr : T(0);
-                const T logu = M<T>::lg(M<T>::uni(word_of(w, cc & 3)));
+                const T u = M<T>::uni(word_of(w, cc & 3));
+                const T logu = sizeof(T) == 8 ? M<T>::lg(u) : (T)lg2_approx((float)u);
                 int ok = logu < loga;
                 if (!isfinite((double)logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
                 acc[c] = ok;
@@ -343,6 +375,18 @@ __global__ void __launch_bounds__(256) chains_simt_kernel(const ChainArgs A)
         A.f[ci] = fcur[c];
         A.best_f[ci] = fbest[c];
         A.accepts[ci] += cnt[c];
+    }
+}
+
+template <typename T, int TCH, int TO>
+__global__ void __launch_bounds__(256) chains_simt_kernel(const ChainArgs A)
+{
+    const WorkItem it = A.items[blockIdx.x];
+    const ChannelDesc d = A.desc[it.b];
+    switch (d.L) {
+    case 2: simt_item<T, TCH, TO, 2>(A, it, d); break;
+    case 4: simt_item<T, TCH, TO, 4>(A, it, d); break;
+    default: simt_item<T, TCH, TO, 8>(A, it, d); break;
     }
 }
 

@@ -16,7 +16,7 @@
 //   5. accepted chains keep x', Gt x' and the drift slope of x'.
 // A-operand row layout (128 rows per tile t): row 32q + l holds dimension 64t + 16q + (l & 15) of
 // Gt (l < 16) or of P~ Gt (l >= 16), so each warp's TMEM quadrant carries both quantities of
-// 16 dimensions. Both operands are K-major, no swizzle, in 8 x 16-byte core matrices: K-adjacent
+// 16 dimensions; each thread owns one dimension of 4 chains. Both operands are K-major, no swizzle, in 8 x 16-byte core matrices: K-adjacent
 // core matrices 128 B apart (LBO), 8-row groups (K/8)*128 B apart (SBO).
 // Every wait is bounded: a wait that runs out sets the timeout status bit, the CTA stops issuing
 // work, frees its TMEM and returns.
@@ -24,11 +24,18 @@
 
 #include <cuda_bf16.h>
 
+#include "proposal.cuh"
+
 namespace mcmcdet {
 
 namespace {
 
 constexpr int kWaitLimit = 1 << 22;
+
+// Resident CTAs per SM the register allocation is sized for (512 threads each).
+#ifndef TC_MIN_BLOCKS
+#define TC_MIN_BLOCKS 2
+#endif
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -70,74 +77,35 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t 
         "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 {
-    uint32_t r[16];
+    uint32_t r[8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
+          "=r"(r[7])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Proposal factor (same arithmetic as the CUDA-core FP32 kernel): logits a (j - k) - cq (j - k)^2.
-struct Fac {
-    float mx;
-    float total;
-    float S[kMaxL];
-};
-
-__device__ __forceinline__ float logit_of(float a, float cq, int j, int k)
+// 4 values per lane, summed over the 16 lanes of a half warp and scattered: afterwards lanes
+// 4j .. 4j+3 of the half hold the sum of value j.
+__device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 {
-    const float dj = (float)(j - k);
-    return a * dj - cq * dj * dj;
-}
-
-__device__ __forceinline__ void factor(float a, float cq, int k, int L, Fac &F)
-{
-    float lg[kMaxL];
-    float mx = -1e30f;
-#pragma unroll
-    for (int j = 0; j < kMaxL; ++j) {
-        lg[j] = logit_of(a, cq, j, k);
-        if (j < L) mx = lg[j] > mx ? lg[j] : mx;
-    }
-    F.mx = mx;
-    float acc = 0.f;
-#pragma unroll
-    for (int j = 0; j < kMaxL; ++j) {
-        if (j < L) acc += __expf(lg[j] - mx);
-        F.S[j] = acc;
-    }
-    F.total = acc;
-}
-
-// 8 values per lane, summed over the 16 lanes of a half warp and scattered: afterwards lanes
-// 2j and 2j+1 of the half hold the sum of value j.
-__device__ __forceinline__ float reduce_scatter16(const float (&v)[8], int dl)
-{
-    float a[4], b2[2];
-    const bool hi8 = dl & 8, hi4 = dl & 4, hi2 = dl & 2;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = hi8 ? v[i] : v[4 + i];
-        const float recv = __shfl_xor_sync(0xffffffffu, send, 8);
-        a[i] = (hi8 ? v[4 + i] : v[i]) + recv;
-    }
+    float a[2];
+    const bool hi8 = dl & 8, hi4 = dl & 4;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const float send = hi4 ? a[i] : a[2 + i];
-        const float recv = __shfl_xor_sync(0xffffffffu, send, 4);
-        b2[i] = (hi4 ? a[2 + i] : a[i]) + recv;
+        const float send = hi8 ? v[i] : v[2 + i];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 8);
+        a[i] = (hi8 ? v[2 + i] : v[i]) + recv;
     }
-    const float send = hi2 ? b2[0] : b2[1];
-    const float recv = __shfl_xor_sync(0xffffffffu, send, 2);
-    float c = (hi2 ? b2[1] : b2[0]) + recv;
+    const float send = hi4 ? a[0] : a[1];
+    const float recv = __shfl_xor_sync(0xffffffffu, send, 4);
+    float c = (hi4 ? a[1] : a[0]) + recv;
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
     c += __shfl_xor_sync(0xffffffffu, c, 1);
     return c;
 }
@@ -158,7 +126,7 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
         return r;
     };
     L.a = take((uint32_t)S * MT * 128 * Kp * 2, 1024);
-    L.b = take((uint32_t)C * Kp * 2, 1024);
+    L.b = take((uint32_t)(C / 8) * (((uint32_t)(Kp / 8) * 144u + 127u) / 128u * 128u + 32u), 1024);
     L.red = take(4u * C * 4, 16);
     L.dred = take(4u * C * 4, 16);
     L.acc = take((uint32_t)C * 4, 16);
@@ -171,37 +139,362 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
     return L;
 }
 
+// B operand (x', [C chains x Kp]) core-matrix strides: K-adjacent core matrices 144 B apart and
+// 8-chain groups at a stride that is 32 B past a multiple of 128 B, so that the 16-bit stores of
+// a warp (16 dimensions x 2 chain groups) fall into distinct shared-memory banks.
+__host__ __device__ inline uint32_t b_lbo() { return 144u; }
+__host__ __device__ inline uint32_t b_sbo(int Kp)
+{
+    return ((uint32_t)(Kp / 8) * 144u + 127u) / 128u * 128u + 32u;
+}
+
+struct TcCtx {
+    unsigned char *sA, *sB;
+    float *red, *dred;
+    int *sacc, *simpr;
+    double *sref;
+    int8_t *sfs;
+    uint32_t bar_mma;
+    uint32_t tmem;
+    uint32_t idesc;
+    uint32_t sbo_a, sbo_b;
+    int tid, warp, lane, q, cgi, h, dl, C, S, Kp;
+    uint32_t mma_phase;
+};
+
+// Issue the MMAs of one transition (thread 0) and wait for them (everyone). Returns false on a
+// bounded-wait expiry; every thread of the CTA takes the same branch.
 template <int MT>
-__global__ void __launch_bounds__(512, 1) chains_tc_kernel(const ChainArgs A, const int C,
+__device__ __forceinline__ bool tc_gemm(TcCtx &x)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (x.tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(x.sA), b0 = smem_u32(x.sB);
+        for (int t = 0; t < MT; ++t) {
+            uint32_t first = 1;
+            for (int s = 0; s < x.S; ++s) {
+                const uint32_t ab = a0 + (uint32_t)((s * MT + t) * 128 * x.Kp * 2);
+                for (int ks = 0; ks < x.Kp / 16; ++ks) {
+                    const uint64_t da = smem_desc(ab + ks * 256u, 128u, x.sbo_a);
+                    const uint64_t db = smem_desc(b0 + ks * 2u * b_lbo(), b_lbo(), x.sbo_b);
+                    mma_bf16(x.tmem + (uint32_t)(t * x.C), da, db, x.idesc, first ? 0u : 1u);
+                    first = 0;
+                }
+            }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                x.bar_mma)
+            : "memory");
+    }
+    const bool ok = mbar_wait(x.bar_mma, x.mma_phase);
+    x.mma_phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return !__syncthreads_or(!ok);
+}
+
+// TMEM -> registers: Gt x (g) and P~ Gt x (m) of this thread's dimension for its 8 chains.
+template <int MT>
+__device__ __forceinline__ void tc_read(const TcCtx &x, float (&g)[MT][4], float (&m)[MT][4])
+{
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+        float v[8];
+        tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + 8 * x.cgi), v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float send = x.h ? v[j] : v[4 + j];
+            const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
+            g[t][j] = x.h ? recv : v[j];
+            m[t][j] = x.h ? v[4 + j] : recv;
+        }
+    }
+}
+
+// BF16 bits of a small odd integer (exact: the float has at most 4 significant bits).
+__device__ __forceinline__ unsigned short bf16_bits_of_int(int v)
+{
+    return (unsigned short)(__float_as_uint((float)v) >> 16);
+}
+
+template <int MT, int L>
+__device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const ChannelDesc &d,
+                        bool &alive)
+{
+    const int N = d.N, nC = it.nc, C = x.C;
+    const bool pre = d.NO > N;
+    const float clin = (float)d.clin;
+    const float a2s = clin * kLog2e;              // slope -> log2 units
+    const float c2 = (float)d.cquad * kLog2e;
+    const float inv2c = 0.5f / c2;
+    const float cf2 = (float)d.cf * kLog2e;       // df_tau -> log2 units
+    const int cbase = 8 * x.cgi + 4 * x.h;         // first of this thread's 4 chains (CTA-local)
+    float zt[MT], wt[MT];
+    int nd[MT];
+    int8_t k[MT][4], kb[MT][4];
+    float Dg[MT][4], sl[MT][4];                    // Gt x and the slope (log2 units)
+    const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
+    const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+        const int n = 64 * t + 16 * x.q + x.dl;
+        nd[t] = n;
+        const bool v = n < N;
+        zt[t] = v ? gz[n] : 0.f;
+        wt[t] = v ? gw[n] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = cbase + j;
+            int8_t kv = 0, kbv = 0;
+            if (v && c < nC) {
+                const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
+                kv = A.states[e];
+                kbv = A.best_states[e];
+            }
+            k[t][j] = kv;
+            kb[t][j] = kbv;
+        }
+    }
+    double fcur = 0.0, fbest = 0.0;
+    unsigned cnt = 0;
+    if (x.tid < nC) {
+        const long long ci = (long long)it.b * A.chains + it.c0 + x.tid;
+        fcur = A.f[ci];
+        fbest = A.best_f[ci];
+    }
+    auto write_b = [&](const int8_t (&kk)[MT][4]) {
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const int n = nd[t];
+            if (n >= x.Kp) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = cbase + j;
+                if (c >= C) continue;
+                const int xv = (n < N && c < nC) ? odd_of(kk[t][j], L) : 0;
+                const uint32_t off = (uint32_t)(c >> 3) * x.sbo_b + (uint32_t)(n >> 3) * b_lbo() +
+                                     (uint32_t)(c & 7) * 16u + (uint32_t)(n & 7) * 2u;
+                *reinterpret_cast<unsigned short *>(x.sB + off) = bf16_bits_of_int(xv);
+            }
+        }
+    };
+    write_b(k);
+    if (alive && !tc_gemm<MT>(x)) { alive = false; set_status(A.status, kStatusTimeout); }
+    {
+        float g[MT][4], m[MT][4];
+        if (alive) tc_read<MT>(x, g, m);
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                Dg[t][j] = alive ? g[t][j] : 0.f;
+                sl[t][j] = alive ? a2s * (pre ? (wt[t] - m[t][j]) : (zt[t] - g[t][j])) : 0.f;
+            }
+    }
+
+    for (int i = 0; i < A.iterations && alive; ++i) {
+        const uint32_t t_it = (uint32_t)(A.t_offset + 1 + i);
+        float part[4], dpart[4];
+        int8_t kp[MT][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { part[j] = 0.f; dpart[j] = 0.f; }
+        // 1. proposal draw (log2 q(x'|x) accumulated with a minus sign)
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const int n = nd[t];
+            const bool v = n < N;
+            {
+                const int cq0 = cbase;
+                const bool any = v && cq0 < nC;
+                U4 w = {0, 0, 0, 0};
+                if (any)
+                    w = philox4x32_10(t_it, (uint32_t)n, (uint32_t)it.b,
+                                      (uint32_t)((it.c0 + cq0) >> 2), A.key0, A.key1);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int j = jj;
+                    int sel = k[t][j];
+                    if (any && cq0 + jj < nC) {
+                        float lq;
+                        sel = factor_draw<L>(sl[t][j], c2, inv2c, k[t][j],
+                                             uniform_f(word_of(w, jj)), lq);
+                        part[j] -= lq;
+                    }
+                    kp[t][j] = (int8_t)sel;
+                }
+            }
+        }
+        write_b(kp);
+        // 2. D' = A X'^T on the tensor core
+        if (!tc_gemm<MT>(x)) { alive = false; set_status(A.status, kStatusTimeout); break; }
+        // 3. reverse factor and energy difference
+        float gp[MT][4], mp[MT][4];
+        tc_read<MT>(x, gp, mp);
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const bool v = nd[t] < N;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float ap = a2s * (pre ? (wt[t] - mp[t][j]) : (zt[t] - gp[t][j]));
+                mp[t][j] = ap;   // slope of x', kept for the update
+                if (v && cbase + j < nC) {
+                    part[j] += factor_log2q<L>(ap, c2, inv2c, kp[t][j], k[t][j]);
+                    dpart[j] += (float)(2 * (kp[t][j] - k[t][j])) * (2.f * zt[t] - Dg[t][j] - gp[t][j]);
+                }
+            }
+        }
+        // 4. per-chain reduction and the MH decision (log2 units)
+        const float rs = reduce_scatter16(part, x.dl);
+        const float rd = reduce_scatter16(dpart, x.dl);
+        if ((x.dl & 3) == 0) {
+            const int c = cbase + (x.dl >> 2);
+            x.red[x.q * C + c] = rs;
+            x.dred[x.q * C + c] = rd;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (x.tid < nC) {
+            const int c = x.tid;
+            const float s = x.red[c] + x.red[C + c] + x.red[2 * C + c] + x.red[3 * C + c];
+            const float sd = x.dred[c] + x.dred[C + c] + x.dred[2 * C + c] + x.dred[3 * C + c];
+            const int cc = it.c0 + c;
+            const U4 w = philox4x32_10(t_it, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
+                                       A.key0, A.key1);
+            const float logr = fmaf(cf2, sd, s);
+            const float loga = logr < 0.f ? logr : 0.f;
+            const float logu = lg2_approx(uniform_f(word_of(w, cc & 3)));
+            int ok = logu < loga;
+            if (!isfinite(logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
+            int im = 0;
+            if (ok) {
+                fcur += d.inv_s2 * (double)sd;
+                cnt += 1;
+                if (fcur > fbest) { fbest = fcur; im = 1; }
+            }
+            x.sacc[c] = ok;
+            x.simpr[c] = im;
+        }
+        __syncthreads();
+        // 5. accepted chains take x' and its caches
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = cbase + j;
+            const int ok = c < nC ? x.sacc[c] : 0;
+            const int im = c < nC ? x.simpr[c] : 0;
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                if (ok) {
+                    k[t][j] = kp[t][j];
+                    Dg[t][j] = gp[t][j];
+                    sl[t][j] = mp[t][j];
+                }
+                if (im) kb[t][j] = kp[t][j];
+            }
+        }
+        // periodic FP64 refresh of the tracked energies (decisions never read them)
+        if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                if (nd[t] >= N) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (cbase + j < nC) x.sfs[(cbase + j) * kMaxN + nd[t]] = k[t][j];
+            }
+            __syncthreads();
+            const double *G = A.G64 + d.mat_off;
+            const double *z = A.z64 + d.vec_off;
+            for (int c = x.warp; c < nC; c += blockDim.x >> 5) {
+                double quad = 0.0, lin = 0.0;
+                for (int n = x.lane; n < N; n += 32) {
+                    const double xn = odd_of(x.sfs[c * kMaxN + n], L);
+                    double s = 0.0;
+                    for (int m = 0; m < N; ++m)
+                        s = fma(G[(size_t)n * N + m], (double)odd_of(x.sfs[c * kMaxN + m], L), s);
+                    quad = fma(xn, s, quad);
+                    lin = fma(xn, z[n], lin);
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    quad += __shfl_xor_sync(0xffffffffu, quad, o);
+                    lin += __shfl_xor_sync(0xffffffffu, lin, o);
+                }
+                if (x.lane == 0) x.sref[c] = -(A.yy[it.b] - 2.0 * lin + quad) * d.inv_s2;
+            }
+            __syncthreads();
+            if (x.tid < nC) {
+                const double dr = fabs(x.sref[x.tid] - fcur);
+                atomicMax(A.drift_bits, (unsigned long long)__double_as_longlong(dr));
+                fcur = x.sref[x.tid];
+            }
+        }
+    }
+    // write back this work item
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+        const int n = nd[t];
+        if (n >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = cbase + j;
+            if (c >= nC) continue;
+            const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
+            A.states[e] = k[t][j];
+            A.best_states[e] = kb[t][j];
+        }
+    }
+    if (x.tid < nC) {
+        const long long ci = (long long)it.b * A.chains + it.c0 + x.tid;
+        A.f[ci] = fcur;
+        A.best_f[ci] = fbest;
+        A.accepts[ci] += cnt;
+    }
+}
+
+template <int MT>
+__global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const ChainArgs A, const int C,
                                                            const int S, const int Kp)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcLayout lay = tc_layout(S, MT, Kp, C);
-    unsigned char *sA = smem + lay.a;
-    unsigned char *sB = smem + lay.b;
-    float *red = reinterpret_cast<float *>(smem + lay.red);
-    float *dred = reinterpret_cast<float *>(smem + lay.dred);
-    int *sacc = reinterpret_cast<int *>(smem + lay.acc);
-    int *simpr = reinterpret_cast<int *>(smem + lay.impr);
-    double *sref = reinterpret_cast<double *>(smem + lay.ref);
-    int8_t *sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
+    TcCtx x;
+    x.sA = smem + lay.a;
+    x.sB = smem + lay.b;
+    x.red = reinterpret_cast<float *>(smem + lay.red);
+    x.dred = reinterpret_cast<float *>(smem + lay.dred);
+    x.sacc = reinterpret_cast<int *>(smem + lay.acc);
+    x.simpr = reinterpret_cast<int *>(smem + lay.impr);
+    x.sref = reinterpret_cast<double *>(smem + lay.ref);
+    x.sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.tmem);
-    const uint32_t bar_tma = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, cgi = warp >> 2, h = lane >> 4, dl = lane & 15;
+    const uint32_t bar_tma = smem_u32(&bars[0]);
+    x.bar_mma = smem_u32(&bars[1]);
+    x.tid = threadIdx.x;
+    x.warp = x.tid >> 5;
+    x.lane = x.tid & 31;
+    x.q = x.warp & 3;
+    x.cgi = x.warp >> 2;
+    x.h = x.lane >> 4;
+    x.dl = x.lane & 15;
+    x.C = C;
+    x.S = S;
+    x.Kp = Kp;
+    x.sbo_a = (uint32_t)(Kp / 8) * 128u;
+    x.sbo_b = b_sbo(Kp);
+    x.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
+              ((uint32_t)(128 >> 4) << 24);
+    x.mma_phase = 0;
     const int ncols_alloc = A.tc_tmem_cols;   // TMEM columns to allocate (power of 2, >= 32)
-    const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
 
-    if (tid == 0) {
+    if (x.tid == 0) {
         mbar_init(bar_tma, 1);
-        mbar_init(bar_mma, 1);
+        mbar_init(x.bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (x.warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(ncols_alloc));
@@ -210,51 +503,19 @@ __global__ void __launch_bounds__(512, 1) chains_tc_kernel(const ChainArgs A, co
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    uint32_t tma_phase = 0, mma_phase = 0;
+    x.tmem = *tmem_slot;
+    // zero the B operand once: padding columns / chains stay zero, the rest is rewritten
+    for (int e = x.tid; e < (int)(lay.red - lay.b) / 16; e += blockDim.x)
+        reinterpret_cast<uint4 *>(x.sB)[e] = make_uint4(0, 0, 0, 0);
+    uint32_t tma_phase = 0;
     bool alive = true;
-
-    // Issue the MMAs of one transition (thread 0) and wait for them (everyone).
-    auto gemm = [&]() -> bool {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            for (int t = 0; t < MT; ++t) {
-                uint32_t first = 1;
-                for (int s = 0; s < S; ++s) {
-                    const uint32_t ab = a0 + (uint32_t)((s * MT + t) * 128 * Kp * 2);
-                    for (int ks = 0; ks < Kp / 16; ++ks) {
-                        const uint64_t da = smem_desc(ab + ks * 256u, 128u, sbo);
-                        const uint64_t db = smem_desc(b0 + ks * 256u, 128u, sbo);
-                        mma_bf16(tmem + (uint32_t)(t * C), da, db, idesc, first ? 0u : 1u);
-                        first = 0;
-                    }
-                }
-            }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    bar_mma)
-                : "memory");
-        }
-        const bool ok = mbar_wait(bar_mma, mma_phase);
-        mma_phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        return !__syncthreads_or(!ok);   // every thread takes the same branch
-    };
 
     for (int item = blockIdx.x; item < A.n_items && alive; item += gridDim.x) {
         const WorkItem it = A.items[item];
         const ChannelDesc d = A.desc[it.b];
-        const int N = d.N, L = d.L, nC = it.nc;
-        const bool pre = d.NO > N;
-        const float clin = (float)d.clin, cq = (float)d.cquad, cf = (float)d.cf;
-
         // stage this channel's A operand (TMA bulk copy, mbarrier completion)
         const uint32_t abytes = (uint32_t)S * MT * 128u * (uint32_t)Kp * 2u;
-        if (tid == 0) {
+        if (x.tid == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_tma),
                          "r"(abytes)
                          : "memory");
@@ -264,274 +525,28 @@ __global__ void __launch_bounds__(512, 1) chains_tc_kernel(const ChainArgs A, co
                 const uint32_t n = abytes - off < chunk ? abytes - off : chunk;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
-                    "%2, [%3];" ::"r"(smem_u32(sA) + off),
+                    "%2, [%3];" ::"r"(smem_u32(x.sA) + off),
                     "l"(src + off), "r"(n), "r"(bar_tma)
                     : "memory");
             }
         }
-        // per-thread constants and state
-        float zt[MT], wt[MT];
-        int nd[MT];
-        int8_t k[MT][8], kb[MT][8];
-        float Dg[MT][8], sl[MT][8];
-        const int cbase = 16 * cgi + 8 * h;   // first of this thread's 8 chains (CTA-local)
-        const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
-        const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
-#pragma unroll
-        for (int t = 0; t < MT; ++t) {
-            const int n = 64 * t + 16 * q + dl;
-            nd[t] = n;
-            const bool v = n < N;
-            zt[t] = v ? gz[n] : 0.f;
-            wt[t] = v ? gw[n] : 0.f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = cbase + j;
-                int8_t kv = 0, kbv = 0;
-                if (v && c < nC) {
-                    const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
-                    kv = A.states[e];
-                    kbv = A.best_states[e];
-                }
-                k[t][j] = kv;
-                kb[t][j] = kbv;
-            }
-        }
-        double fcur = 0.0, fbest = 0.0;
-        unsigned cnt = 0;
-        if (tid < nC) {
-            const long long ci = (long long)it.b * A.chains + it.c0 + tid;
-            fcur = A.f[ci];
-            fbest = A.best_f[ci];
-        }
-        // write x (current states) as the B operand; zero the padding
-        auto write_b = [&](int8_t (&kk)[MT][8]) {
-#pragma unroll
-            for (int t = 0; t < MT; ++t) {
-                const int n = nd[t];
-                if (n >= Kp) continue;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int c = cbase + j;
-                    if (c >= C) continue;
-                    const float xv = (n < N && c < nC) ? (float)odd_of(kk[t][j], L) : 0.f;
-                    const uint32_t off = (uint32_t)(c >> 3) * sbo + (uint32_t)(n >> 3) * 128u +
-                                         (uint32_t)(c & 7) * 16u + (uint32_t)(n & 7) * 2u;
-                    *reinterpret_cast<__nv_bfloat16 *>(sB + off) = __float2bfloat16_rn(xv);
-                }
-            }
-        };
-        // zero the whole B operand once (covers K padding rows not owned by any thread)
-        for (int e = tid; e < C * Kp * 2 / 16; e += blockDim.x)
-            reinterpret_cast<uint4 *>(sB)[e] = make_uint4(0, 0, 0, 0);
-        __syncthreads();
-        write_b(k);
         if (__syncthreads_or(!mbar_wait(bar_tma, tma_phase))) {
             alive = false;
             set_status(A.status, kStatusTimeout);
         }
         tma_phase ^= 1u;
-        if (alive && !gemm()) { alive = false; set_status(A.status, kStatusTimeout); }
-        // read D for the current states -> Gt x and the drift slope
-        auto read_d = [&](float (&g)[MT][8], float (&m)[MT][8]) {
-#pragma unroll
-            for (int t = 0; t < MT; ++t) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * C + 16 * cgi), v);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float send = h ? v[j] : v[8 + j];
-                    const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
-                    g[t][j] = h ? recv : v[j];
-                    m[t][j] = h ? v[8 + j] : recv;
-                }
-            }
-        };
-        {
-            float g[MT][8], m[MT][8];
-            if (alive) read_d(g, m);
-#pragma unroll
-            for (int t = 0; t < MT; ++t)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    Dg[t][j] = alive ? g[t][j] : 0.f;
-                    sl[t][j] = alive ? clin * (pre ? (wt[t] - m[t][j]) : (zt[t] - g[t][j])) : 0.f;
-                }
-        }
-
-        for (int i = 0; i < A.iterations && alive; ++i) {
-            const uint32_t t_it = (uint32_t)(A.t_offset + 1 + i);
-            float part[8], dpart[8];
-            int8_t kp[MT][8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) { part[j] = 0.f; dpart[j] = 0.f; }
-            // 1. proposal draw
-#pragma unroll
-            for (int t = 0; t < MT; ++t) {
-                const int n = nd[t];
-                const bool v = n < N;
-#pragma unroll
-                for (int qq = 0; qq < 2; ++qq) {
-                    const int cq0 = cbase + 4 * qq;
-                    U4 w = {0, 0, 0, 0};
-                    if (v && cq0 < nC)
-                        w = philox4x32_10(t_it, (uint32_t)n, (uint32_t)it.b,
-                                          (uint32_t)((it.c0 + cq0) >> 2), A.key0, A.key1);
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int j = 4 * qq + jj;
-                        int sel = k[t][j];
-                        if (v && cq0 + jj < nC) {
-                            Fac F;
-                            factor(sl[t][j], cq, k[t][j], L, F);
-                            const float target = uniform_f(word_of(w, jj)) * F.total;
-                            sel = L - 1;
-#pragma unroll
-                            for (int l = kMaxL - 1; l >= 0; --l)
-                                if (l < L && target < F.S[l]) sel = l;
-                            part[j] -= logit_of(sl[t][j], cq, sel, k[t][j]) - F.mx - __logf(F.total);
-                        }
-                        kp[t][j] = (int8_t)sel;
-                    }
-                }
-            }
-            write_b(kp);
-            // 2. D' = A X'^T on the tensor core
-            if (!gemm()) { alive = false; set_status(A.status, kStatusTimeout); break; }
-            // 3. reverse factor and energy difference
-            float gp[MT][8], mp[MT][8];
-            read_d(gp, mp);
-#pragma unroll
-            for (int t = 0; t < MT; ++t) {
-                const bool v = nd[t] < N;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float ap = clin * (pre ? (wt[t] - mp[t][j]) : (zt[t] - gp[t][j]));
-                    mp[t][j] = ap;   // keep the slope of x' for the update
-                    if (v && cbase + j < nC) {
-                        Fac F;
-                        factor(ap, cq, kp[t][j], L, F);
-                        part[j] += logit_of(ap, cq, k[t][j], kp[t][j]) - F.mx - __logf(F.total);
-                        dpart[j] += (float)(2 * (kp[t][j] - k[t][j])) *
-                                    (2.f * zt[t] - Dg[t][j] - gp[t][j]);
-                    }
-                }
-            }
-            // 4. per-chain reduction and the MH decision
-            const float rs = reduce_scatter16(part, dl);
-            const float rd = reduce_scatter16(dpart, dl);
-            if ((dl & 1) == 0) {
-                const int c = cbase + (dl >> 1);
-                red[q * C + c] = rs;
-                dred[q * C + c] = rd;
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (tid < nC) {
-                const int c = tid;
-                const float s = red[c] + red[C + c] + red[2 * C + c] + red[3 * C + c];
-                const float sd = dred[c] + dred[C + c] + dred[2 * C + c] + dred[3 * C + c];
-                const int cc = it.c0 + c;
-                const U4 w = philox4x32_10(t_it, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
-                                           A.key0, A.key1);
-                const float logr = s + cf * sd;
-                const float loga = logr < 0.f ? logr : 0.f;
-                const float logu = __logf(uniform_f(word_of(w, cc & 3)));
-                int ok = logu < loga;
-                if (!isfinite(logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
-                int im = 0;
-                if (ok) {
-                    fcur += d.inv_s2 * (double)sd;
-                    cnt += 1;
-                    if (fcur > fbest) { fbest = fcur; im = 1; }
-                }
-                sacc[c] = ok;
-                simpr[c] = im;
-            }
-            __syncthreads();
-            // 5. accepted chains take x' and its caches
-            bool any_ref = false;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = cbase + j;
-                const int ok = c < nC ? sacc[c] : 0;
-                const int im = c < nC ? simpr[c] : 0;
-#pragma unroll
-                for (int t = 0; t < MT; ++t) {
-                    if (ok) {
-                        k[t][j] = kp[t][j];
-                        Dg[t][j] = gp[t][j];
-                        sl[t][j] = mp[t][j];
-                    }
-                    if (im) kb[t][j] = kp[t][j];
-                }
-            }
-            // periodic FP64 refresh of the tracked energies (decisions never read them)
-            if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
-                any_ref = true;
-#pragma unroll
-                for (int t = 0; t < MT; ++t) {
-                    if (nd[t] >= N) continue;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (cbase + j < nC) sfs[(cbase + j) * kMaxN + nd[t]] = k[t][j];
-                }
-            }
-            if (any_ref) {
-                __syncthreads();
-                const double *G = A.G64 + d.mat_off;
-                const double *z = A.z64 + d.vec_off;
-                for (int c = warp; c < nC; c += blockDim.x >> 5) {
-                    double quad = 0.0, lin = 0.0;
-                    for (int n = lane; n < N; n += 32) {
-                        const double xn = odd_of(sfs[c * kMaxN + n], L);
-                        double s = 0.0;
-                        for (int m = 0; m < N; ++m)
-                            s = fma(G[(size_t)n * N + m], (double)odd_of(sfs[c * kMaxN + m], L), s);
-                        quad = fma(xn, s, quad);
-                        lin = fma(xn, z[n], lin);
-                    }
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) {
-                        quad += __shfl_xor_sync(0xffffffffu, quad, o);
-                        lin += __shfl_xor_sync(0xffffffffu, lin, o);
-                    }
-                    if (lane == 0) sref[c] = -(A.yy[it.b] - 2.0 * lin + quad) * d.inv_s2;
-                }
-                __syncthreads();
-                if (tid < nC) {
-                    const double dr = fabs(sref[tid] - fcur);
-                    atomicMax(A.drift_bits, (unsigned long long)__double_as_longlong(dr));
-                    fcur = sref[tid];
-                }
-            }
-        }
-        // write back this work item
-#pragma unroll
-        for (int t = 0; t < MT; ++t) {
-            const int n = nd[t];
-            if (n >= N) continue;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = cbase + j;
-                if (c >= nC) continue;
-                const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
-                A.states[e] = k[t][j];
-                A.best_states[e] = kb[t][j];
-            }
-        }
-        if (tid < nC) {
-            const long long ci = (long long)it.b * A.chains + it.c0 + tid;
-            A.f[ci] = fcur;
-            A.best_f[ci] = fbest;
-            A.accepts[ci] += cnt;
+        if (!alive) break;
+        switch (d.L) {
+        case 2: tc_item<MT, 2>(A, x, it, d, alive); break;
+        case 4: tc_item<MT, 4>(A, x, it, d, alive); break;
+        default: tc_item<MT, 8>(A, x, it, d, alive); break;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+    if (x.warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(x.tmem),
                      "r"(ncols_alloc));
 }
 
@@ -601,10 +616,10 @@ bool tc_make_plan(const std::vector<ChannelDesc> &desc, int chains, int split_te
     plan->kdim = Kp;
     plan->max_n = maxn;
     plan->split_terms = S;
-    plan->threads = 8 * C;                    // 4 TMEM quadrants x C/16 column groups x 32
+    plan->threads = 16 * C;                   // 4 TMEM quadrants x C/8 column groups x 32
     plan->tmem_cols = pow2_at_least(MT * C);
     const int by_smem = (int)(228 * 1024 / (L.total + 1024));
-    const int by_thr = std::min(2048 / plan->threads, 65536 / (plan->threads * 128));
+    const int by_thr = std::min(2048 / plan->threads, TC_MIN_BLOCKS);
     const int by_tmem = 512 / plan->tmem_cols;
     plan->ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_thr), by_tmem));
     plan->smem = L.total;
