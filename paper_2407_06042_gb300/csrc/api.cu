@@ -52,6 +52,8 @@ struct mcmc_detector {
     long long tot_states = 0, tot_mat = 0, tot_bt = 0, tot_vec = 0, tot_bits = 0, tot_ant = 0;
     long long tot_tc = 0;
     long long transitions = 0;
+    bool f_valid = false;   // tracked energies hold the current states' values
+    bool d_valid = false;   // d_dexp holds Gt x of the current states
     int cg = 0;
     size_t chain_smem = 0;
     bool bt_in_smem = false;
@@ -60,7 +62,7 @@ struct mcmc_detector {
     // device workspace
     DevBuf d_desc, d_items, d_Gc, d_zc, d_Mc, d_gj, d_yy, d_G64, d_GM64, d_z64, d_w64, d_z32,
         d_w32, d_bt32, d_bt64, d_tc, d_states, d_best_states, d_f, d_best_f, d_accepts,
-        d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf;
+        d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp;
     HostBuf h_stage;
 };
 
@@ -143,6 +145,8 @@ cudaError_t h2d(mcmc_detector *d, void *dst, const void *src, size_t bytes, size
                            cudaMemcpyHostToDevice, d->stream);
 }
 
+mcmc_status ensure_energies(mcmc_detector *d);
+
 mcmc_status read_status(mcmc_detector *d)
 {
     unsigned st = 0;
@@ -188,6 +192,35 @@ __global__ void finalize_desc_kernel(ChannelDesc *desc, const float *noise_var, 
         c.cquad = 2.0 * d2 / alpha;
         c.gamma_t = 0.0;
     }
+}
+
+}  // namespace
+
+namespace {
+
+// FP64 energies of the current states (and a restart of the running best) when the tracked
+// energies are not valid yet: FP32 / MIXED handles read after preprocess or set_chains without a
+// run in between.
+mcmc_status ensure_energies(mcmc_detector *d)
+{
+    if (d->f_valid) return MCMC_OK;
+    RefreshArgs ra{};
+    ra.desc = P<ChannelDesc>(d->d_desc);
+    ra.states = P<int8_t>(d->d_states);
+    ra.G64 = P<double>(d->d_G64);
+    ra.z64 = P<double>(d->d_z64);
+    ra.yy = P<double>(d->d_yy);
+    ra.f = P<double>(d->d_f);
+    ra.best_f = P<double>(d->d_best_f);
+    ra.best_states = P<int8_t>(d->d_best_states);
+    ra.status = status_ptr(d);
+    ra.n_channels = d->n_channels;
+    ra.chains = d->cfg.chains;
+    ra.reset_best = 1;
+    CK(launch_refresh(ra, d->stream), "energies");
+    d->launches++;
+    d->f_valid = true;
+    return MCMC_OK;
 }
 
 }  // namespace
@@ -295,7 +328,7 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
                       &d->d_G64, &d->d_GM64, &d->d_z64, &d->d_w64, &d->d_z32, &d->d_w32,
                       &d->d_bt32, &d->d_bt64, &d->d_tc, &d->d_states, &d->d_best_states, &d->d_f,
                       &d->d_best_f, &d->d_accepts, &d->d_misc, &d->d_in_H, &d->d_in_y,
-                      &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf};
+                      &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf, &d->d_dexp};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (d->h_stage.p) cudaFreeHost(d->h_stage.p);
@@ -426,7 +459,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
         CK(ensure(d->d_Mc, 16 * ntc), "alloc Mc");
         CK(ensure(d->d_GM64, 8 * mat), "alloc GM64");
     }
-    const size_t gj_stage = (size_t)(maxnt + 2 * maxnt * maxnt) * 16;
+    const size_t gj_stage = (size_t)(2 * maxnt * maxnt) * 16;
     const bool stage_gj = pre && gj_stage <= std::min<size_t>(d->smem_optin, 160 * 1024);
     if (pre && !stage_gj) CK(ensure(d->d_gj, 16 * 2 * ntc), "alloc gj");
     if (fp64) CK(ensure(d->d_bt64, 8 * bt), "alloc bt64");
@@ -437,6 +470,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     CK(ensure(d->d_f, 8 * (size_t)n_channels * Np), "alloc f");
     CK(ensure(d->d_best_f, 8 * (size_t)n_channels * Np), "alloc best f");
     CK(ensure(d->d_accepts, 8 * (size_t)n_channels * Np), "alloc accepts");
+    if (!fp64) CK(ensure(d->d_dexp, 4 * (size_t)st), "alloc Gt x export");
 
     // inputs
     const float2 *Hd = static_cast<const float2 *>(H);
@@ -491,7 +525,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     const size_t h_stage = 8 * (size_t)(maxnt * maxnr + maxnr);
     pa.stage_h = h_stage <= std::min<size_t>(d->smem_optin, 128 * 1024);
     pa.stage_gj = stage_gj;
-    CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : (size_t)maxnt * 16, pre, d->stream),
+    CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : 0, pre, d->stream),
        "prep kernels");
     d->launches += pre ? 3 : 2;
     if (mixed) {
@@ -524,8 +558,13 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     ra.n_channels = n_channels;
     ra.chains = Np;
     ra.reset_best = 1;
-    CK(launch_refresh(ra, d->stream), "initial energies");
-    d->launches++;
+    if (fp64) {
+        CK(launch_refresh(ra, d->stream), "initial energies");
+        d->launches++;
+    }
+    // FP32 / MIXED: the first run derives the energies from its first GEMM
+    d->f_valid = fp64;
+    d->d_valid = false;
     d->transitions = 0;
     d->prepared = true;
     return MCMC_OK;
@@ -570,6 +609,8 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
     ca.status = status_ptr(d);
     ca.tc_ops = P<uint8_t>(d->d_tc);
     ca.split_terms = d->cfg.split_terms;
+    ca.init_f = d->f_valid ? 0 : 1;
+    ca.dexp = fp64 ? nullptr : P<float>(d->d_dexp);
     if (mixed) {
         ca.z = P<float>(d->d_z32);
         ca.w = P<float>(d->d_w32);
@@ -578,6 +619,8 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         CK(launch_chains_simt(ca, fp64, d->chain_smem, d->stream), "chain kernel");
     }
     d->launches++;
+    d->f_valid = true;
+    d->d_valid = !fp64;
     d->transitions += (long long)iterations * d->n_channels * d->cfg.chains;
     return MCMC_OK;
 }
@@ -590,6 +633,10 @@ mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr,
     if (!d->prepared) return fail(d, MCMC_ESTATE, "estimate before preprocess");
     if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
+    {
+        mcmc_status es = ensure_energies(d);
+        if (es != MCMC_OK) return es;
+    }
     int8_t *o_idx = best_idx;
     float *o_llr = llr;
     double *o_bf = best_f;
@@ -606,6 +653,7 @@ mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr,
     ea.best_f = P<double>(d->d_best_f);
     ea.G = fp64 ? (const void *)P<double>(d->d_G64) : (const void *)P<float>(d->d_bt32);
     ea.g_is_bt = fp64 ? 0 : 1;
+    ea.dexp = (!fp64 && d->d_valid) ? P<float>(d->d_dexp) : nullptr;
     ea.z = fp64 ? (const void *)P<double>(d->d_z64) : (const void *)P<float>(d->d_z32);
     ea.G64 = P<double>(d->d_G64);
     ea.z64 = P<double>(d->d_z64);
@@ -647,6 +695,10 @@ mcmc_status mcmc_detect_get_chains(mcmc_detector *d, int8_t *states, double *f, 
     d->err.clear();
     if (!d->prepared) return fail(d, MCMC_ESTATE, "get_chains before preprocess");
     if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    {
+        mcmc_status es = ensure_energies(d);
+        if (es != MCMC_OK) return es;
+    }
     const cudaMemcpyKind k = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (states) CK(cudaMemcpyAsync(states, d->d_states.p, d->tot_states, k, d->stream), "copy states");
     if (f) CK(cudaMemcpyAsync(f, d->d_f.p, 8 * (size_t)d->n_channels * d->cfg.chains, k, d->stream), "copy f");
@@ -689,6 +741,8 @@ mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32
     ra.reset_best = 1;
     CK(launch_refresh(ra, d->stream), "refresh energies");
     d->launches++;
+    d->f_valid = true;
+    d->d_valid = false;
     return read_status(d);
 }
 

@@ -260,6 +260,30 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    if (A.init_f) {
+        // tracked energies of the current states from Gt x (FP32 products, FP64 sums); the
+        // running best restarts from them
+        for (int c = warp; c < nC; c += nwarps) {
+            double quad = 0.0, lin = 0.0;
+            for (int n = lane; n < N; n += 32) {
+                const double xn = odd_of(sk[c * N + n], L);
+                quad += xn * (double)sD[c * N + n];
+                lin += xn * (double)zt[n];
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                quad += __shfl_xor_sync(0xffffffffu, quad, o);
+                lin += __shfl_xor_sync(0xffffffffu, lin, o);
+            }
+            if (lane == 0) {
+                const double f0 = -(A.yy[it.b] - 2.0 * lin + quad) * d.inv_s2;
+                fcur[c] = f0;
+                fbest[c] = f0;
+            }
+        }
+        for (int e = threadIdx.x; e < nC * N; e += blockDim.x) skb[e] = sk[e];
+        __syncthreads();
+    }
     for (int i = 0; i < A.iterations; ++i) {
         const uint32_t t = (uint32_t)(A.t_offset + 1 + i);
         // 1. proposal draw, four chains per Philox block
@@ -369,6 +393,7 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
     for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {
         A.states[sbase + e] = sk[e];
         A.best_states[sbase + e] = skb[e];
+        if (A.dexp) A.dexp[sbase + e] = (float)sD[e];
     }
     for (int c = threadIdx.x; c < nC; c += blockDim.x) {
         const long long ci = (long long)it.b * A.chains + it.c0 + c;

@@ -294,6 +294,40 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 sl[t][j] = alive ? a2s * (pre ? (wt[t] - m[t][j]) : (zt[t] - g[t][j])) : 0.f;
             }
     }
+    if (A.init_f && alive) {
+        // tracked energies of the current states from the tensor-core Gt x; the running best
+        // restarts from them
+        float lin[4], quad[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { lin[j] = 0.f; quad[j] = 0.f; }
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            if (nd[t] >= N) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float xn = (float)odd_of(k[t][j], L);
+                lin[j] = fmaf(xn, zt[t], lin[j]);
+                quad[j] = fmaf(xn, Dg[t][j], quad[j]);
+                kb[t][j] = k[t][j];
+            }
+        }
+        const float rl = reduce_scatter16(lin, x.dl);
+        const float rq = reduce_scatter16(quad, x.dl);
+        if ((x.dl & 3) == 0) {
+            const int c = cbase + (x.dl >> 2);
+            x.red[x.q * C + c] = rl;
+            x.dred[x.q * C + c] = rq;
+        }
+        __syncthreads();
+        if (x.tid < nC) {
+            const int c = x.tid;
+            const double l = (double)x.red[c] + x.red[C + c] + x.red[2 * C + c] + x.red[3 * C + c];
+            const double qd = (double)x.dred[c] + x.dred[C + c] + x.dred[2 * C + c] + x.dred[3 * C + c];
+            fcur = -(A.yy[it.b] - 2.0 * l + qd) * d.inv_s2;
+            fbest = fcur;
+        }
+        __syncthreads();
+    }
 
     for (int i = 0; i < A.iterations && alive; ++i) {
         const uint32_t t_it = (uint32_t)(A.t_offset + 1 + i);
@@ -443,6 +477,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
             A.states[e] = k[t][j];
             A.best_states[e] = kb[t][j];
+            if (A.dexp) A.dexp[e] = Dg[t][j];
         }
     }
     if (x.tid < nC) {

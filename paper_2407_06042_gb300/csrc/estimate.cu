@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
         for (int s = sp; s < Np; s += split) {
             const int8_t *ks = S + (long long)s * N;
             T Dn = T(0);
-            for (int m = 0; m < N; ++m) Dn = fma(G[(long long)n * gstride + m], (T)odd_of(ks[m], L), Dn);
+            if (A.dexp) Dn = (T)A.dexp[d.state_off + (long long)s * N + n];
+            else
+                for (int m = 0; m < N; ++m) Dn = fma(G[(long long)n * gstride + m], (T)odd_of(ks[m], L), Dn);
             const int k = ks[n];
             const T r = z[n] - Dn;
             const T fs = (T)(f[s] - fref);

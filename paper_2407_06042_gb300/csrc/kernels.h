@@ -86,6 +86,9 @@ struct ChainArgs {
     unsigned long long *accepts;
     unsigned long long *drift_bits;   // max |f_tracked - f_fp64| as ordered bits
     unsigned *status;
+    int init_f;             // derive the tracked energies of the current states from the first
+                            // GEMM (FP32 / MIXED) and restart the running best from them
+    float *dexp;            // Gt x of the final states (FP32), same layout as the states
     // tcgen05 engine only
     const uint8_t *tc_ops;  // per-channel packed BF16 operand blocks
     int split_terms;
@@ -99,6 +102,7 @@ struct EstimateArgs {
     const double *f;
     const double *best_f;
     const void *G;          // float* or double* Gt (N x N per channel), or the Bt operand
+    const float *dexp;      // Gt x of every chain's state from the chain kernel (FP32), or null
     int g_is_bt;            // G points at the N x NOp operand (row stride NOp)
     const void *z;          // float* or double* zt
     const double *G64;

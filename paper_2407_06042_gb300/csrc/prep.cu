@@ -41,19 +41,41 @@ __global__ void __launch_bounds__(256) gram_kernel(PrepArgs a)
     const float2 *Hp = staged ? Hs : H;
     const float2 *yp = staged ? ys : y;
     cd *G = reinterpret_cast<cd *>(a.Gc) + d.mat_off / 4;   // Nt^2 complex per channel (mat_off counts N^2 = 4 Nt^2)
-    // upper triangle incl. diagonal, mirrored
-    for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
-        const int i = e / nt, j = e % nt;
-        if (j < i) continue;
-        double re = 0.0, im = 0.0;
-        const float2 *ci = Hp + (size_t)i * nr, *cj = Hp + (size_t)j * nr;
+    // 2 x 2 complex blocks (i0, i0+1) x (j0, j0+1) with i0 <= j0 (upper block triangle); each
+    // column pair is read once per r for four complex products
+    const int nb = (nt + 1) / 2;
+    const int nblk = nb * (nb + 1) / 2;
+    for (int e = threadIdx.x; e < nblk; e += blockDim.x) {
+        int bi = 0, rem = e;
+        while (rem >= nb - bi) { rem -= nb - bi; ++bi; }   // row-major over the block triangle
+        const int bj = bi + rem;
+        const int i0 = 2 * bi, j0 = 2 * bj;
+        const bool i1v = i0 + 1 < nt, j1v = j0 + 1 < nt;
+        double acc[2][2][2] = {};
+        const float2 *ci0 = Hp + (size_t)i0 * nr, *ci1 = Hp + (size_t)(i1v ? i0 + 1 : i0) * nr;
+        const float2 *cj0 = Hp + (size_t)j0 * nr, *cj1 = Hp + (size_t)(j1v ? j0 + 1 : j0) * nr;
         for (int r = 0; r < nr; ++r) {
-            const double ar = ci[r].x, ai = ci[r].y, br = cj[r].x, bi = cj[r].y;
-            re = fma(ar, br, re); re = fma(ai, bi, re);
-            im = fma(ar, bi, im); im = fma(-ai, br, im);
+            const float2 u0 = ci0[r], u1 = ci1[r], v0 = cj0[r], v1 = cj1[r];
+            const double ur[2] = {u0.x, u1.x}, ui[2] = {u0.y, u1.y};
+            const double vr[2] = {v0.x, v1.x}, vi[2] = {v0.y, v1.y};
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    // conj(u_p) v_q
+                    acc[p][q][0] = fma(ur[p], vr[q], fma(ui[p], vi[q], acc[p][q][0]));
+                    acc[p][q][1] = fma(ur[p], vi[q], fma(-ui[p], vr[q], acc[p][q][1]));
+                }
         }
-        G[i * nt + j] = {re, im};
-        if (i != j) G[j * nt + i] = {re, -im};
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i = i0 + p, j = j0 + q;
+                if (i >= nt || j >= nt || j < i) continue;
+                G[i * nt + j] = {acc[p][q][0], acc[p][q][1]};
+                if (i != j) G[j * nt + i] = {acc[p][q][0], -acc[p][q][1]};
+            }
     }
     cd *z = reinterpret_cast<cd *>(a.zc) + d.vec_off / 2;
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
@@ -75,51 +97,79 @@ __global__ void __launch_bounds__(256) gram_kernel(PrepArgs a)
 }
 
 // ------------------------------------------------------------------------------------------
-// K2: (G + gamma I)^{-1} by Gauss-Jordan elimination on [G + gamma I | I] (Hermitian positive
-// definite: every pivot is real and positive, no pivoting). The working block lives in shared
-// memory when it fits, else in the global scratch block of this channel.
+// K2: M = (G + gamma I)^{-1} (Remark 1, Eq. (19)) through the Cholesky factorisation
+// G + gamma I = L L^H (Hermitian positive definite for gamma > 0), X = L^{-1} by forward
+// substitution, M = X^H X. The two Nt x Nt blocks live in shared memory when they fit, else in
+// the channel's global scratch block.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
 {
     const int b = blockIdx.x;
     const ChannelDesc d = a.desc[b];
-    const int nt = d.Nt, W = 2 * nt;
+    const int nt = d.Nt;
     const double gamma = d.gamma_t / (d.dmin * d.dmin);   // gamma in the unscaled model
     extern __shared__ double shd[];
-    cd *fac = reinterpret_cast<cd *>(shd);                  // nt factors
-    cd *blk = a.stage_gj ? reinterpret_cast<cd *>(shd) + nt
-                         : reinterpret_cast<cd *>(a.gj) + d.mat_off / 2;   // nt x 2nt
+    cd *Am = a.stage_gj ? reinterpret_cast<cd *>(shd) : reinterpret_cast<cd *>(a.gj) + d.mat_off / 2;
+    cd *X = Am + nt * nt;
     const cd *G = reinterpret_cast<const cd *>(a.Gc) + d.mat_off / 4;
-    for (int e = threadIdx.x; e < nt * W; e += blockDim.x) {
-        const int i = e / W, j = e % W;
-        cd v;
-        if (j < nt) { v = G[i * nt + j]; if (i == j) v.x += gamma; }
-        else v = {(j - nt) == i ? 1.0 : 0.0, 0.0};
-        blk[e] = v;
+    for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+        cd v = G[e];
+        if (e / nt == e % nt) v.x += gamma;
+        Am[e] = v;
+        X[e] = {0.0, 0.0};
     }
     __syncthreads();
+    // right-looking Cholesky, lower factor in Am (the trailing block is kept Hermitian-full)
     for (int k = 0; k < nt; ++k) {
-        const double piv = blk[k * W + k].x;
-        if (threadIdx.x == 0 && !(piv > 0.0)) set_status(a.status, kStatusNumeric);
-        const double inv = 1.0 / piv;
+        const double pv = Am[k * nt + k].x;
+        if (threadIdx.x == 0 && !(pv > 0.0)) set_status(a.status, kStatusNumeric);
+        const double dk = sqrt(pv > 0.0 ? pv : 1.0);
+        const double inv = 1.0 / dk;
         __syncthreads();
-        for (int j = threadIdx.x; j < W; j += blockDim.x) {
-            cd v = blk[k * W + j];
-            blk[k * W + j] = {v.x * inv, v.y * inv};
+        for (int i = k + 1 + threadIdx.x; i < nt; i += blockDim.x) {
+            const cd v = Am[i * nt + k];
+            Am[i * nt + k] = {v.x * inv, v.y * inv};
         }
-        for (int i = threadIdx.x; i < nt; i += blockDim.x) fac[i] = blk[i * W + k];
+        if (threadIdx.x == 0) Am[k * nt + k] = {dk, 0.0};
         __syncthreads();
-        for (int e = threadIdx.x; e < nt * W; e += blockDim.x) {
-            const int i = e / W, j = e % W;
-            if (i == k) continue;
-            blk[e] = csub(blk[e], cmul(fac[i], blk[k * W + j]));
+        const int m = nt - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            // A_ij -= L_ik conj(L_jk)
+            const cd li = Am[i * nt + k], lj = Am[j * nt + k];
+            const cd p = {li.x * lj.x + li.y * lj.y, li.y * lj.x - li.x * lj.y};
+            Am[i * nt + j] = csub(Am[i * nt + j], p);
         }
         __syncthreads();
     }
+    // X = L^{-1}, one column per thread (forward substitution)
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+        X[j * nt + j] = {1.0 / Am[j * nt + j].x, 0.0};
+        for (int i = j + 1; i < nt; ++i) {
+            double sr = 0.0, si = 0.0;
+            for (int m2 = j; m2 < i; ++m2) {
+                const cd l = Am[i * nt + m2], xv = X[m2 * nt + j];
+                sr += l.x * xv.x - l.y * xv.y;
+                si += l.x * xv.y + l.y * xv.x;
+            }
+            const double il = 1.0 / Am[i * nt + i].x;
+            X[i * nt + j] = {-sr * il, -si * il};
+        }
+    }
+    __syncthreads();
+    // M = X^H X (Hermitian; upper triangle computed, mirrored)
     cd *M = reinterpret_cast<cd *>(a.Mc) + d.mat_off / 4;
     for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
         const int i = e / nt, j = e % nt;
-        M[e] = blk[i * W + nt + j];
+        if (j < i) continue;
+        double sr = 0.0, si = 0.0;
+        for (int m2 = j; m2 < nt; ++m2) {   // X lower triangular: rows m2 >= max(i, j) = j
+            const cd xi = X[m2 * nt + i], xj = X[m2 * nt + j];
+            sr += xi.x * xj.x + xi.y * xj.y;   // conj(xi) xj
+            si += xi.x * xj.y - xi.y * xj.x;
+        }
+        M[i * nt + j] = {sr, si};
+        if (i != j) M[j * nt + i] = {sr, -si};
     }
 }
 
