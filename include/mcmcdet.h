@@ -169,6 +169,36 @@ const char *mcmc_detect_last_error(const mcmc_detector *d);
 /* Chain kernel launches enqueued on this handle since creation (all kernels of the run loop). */
 int64_t mcmc_detect_kernel_launches(const mcmc_detector *d);
 
+/* Size of the fixed device scratch array used by mcmc_detect_noalloc (16 MiB). */
+#define MCMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Whole FP32 detection of a small batch without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc -- code running
+ * while a CUDA graph is captured on its stream, real-time loops that must not block on the
+ * allocator, hosts whose device memory belongs to a pool they do not control.
+ *
+ * It performs what mcmc_detect_create + preprocess + run_chains(iterations, 0) + estimate do
+ * for precision MCMC_PREC_FP32 (same kernels, same results), but takes every intermediate buffer
+ * from one file-scope device array of MCMC_NOALLOC_SCRATCH_BYTES that every GPU loading this
+ * library holds until the process exits. Arguments are those of the handle-based calls:
+ *  nt, nr, qam, H_off, y_off: HOST arrays [n_channels]; H, y, noise_var: DEVICE pointers
+ *  (layouts as in mcmc_detect_preprocess); chains (Np, multiple of 4), iterations, seed,
+ *  preconditioned, alpha_scale, tau as in mcmc_config / preprocess; outputs best_idx, llr, best_f:
+ *  DEVICE pointers (layouts as in mcmc_detect_estimate; any may be NULL); stream: cudaStream_t
+ *  or NULL for the default stream. The call synchronises that stream before returning.
+ * Errors: MCMC_EINVAL for bad arguments and for a batch whose intermediate buffers need more than
+ * MCMC_NOALLOC_SCRATCH_BYTES (checked before any work is enqueued); device faults as in estimate.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current: make that first call before any stream capture begins.
+ * Every call shares the array and leaves its contents behind; each call re-initialises what it
+ * reads, and calls that overlap on the GPU (other threads, other streams) race with each other. */
+mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt, const int32_t *nr,
+                                const int32_t *qam, const void *H, const int64_t *H_off,
+                                const void *y, const int64_t *y_off, const float *noise_var,
+                                int32_t chains, int32_t iterations, uint64_t seed,
+                                int32_t preconditioned, float alpha_scale, float tau,
+                                int8_t *best_idx, float *llr, double *best_f, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

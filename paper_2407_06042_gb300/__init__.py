@@ -35,6 +35,7 @@ ABI_FUNCTIONS = [
     "mcmc_detect_run_chains", "mcmc_detect_estimate", "mcmc_detect_get_chains",
     "mcmc_detect_set_chains", "mcmc_detect_synchronize", "mcmc_detect_destroy",
     "mcmc_status_string", "mcmc_detect_last_error", "mcmc_detect_kernel_launches",
+    "mcmc_detect_noalloc",
 ]
 
 
@@ -98,6 +99,10 @@ def load(path: Optional[str] = None):
     l.mcmc_detect_last_error.restype = ctypes.c_char_p
     l.mcmc_detect_kernel_launches.argtypes = [vp]
     l.mcmc_detect_kernel_launches.restype = ctypes.c_int64
+    l.mcmc_detect_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32,
+                                      ctypes.c_uint64, i32, ctypes.c_float, ctypes.c_float, vp,
+                                      vp, vp, vp]
+    l.mcmc_detect_noalloc.restype = ctypes.c_int
     if path is None:
         _lib = l
     return l
