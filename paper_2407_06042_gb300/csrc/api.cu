@@ -457,7 +457,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     CK(ensure(d->d_w32, 4 * vec), "alloc w32");
     if (pre) {
         CK(ensure(d->d_Mc, 16 * ntc), "alloc Mc");
-        CK(ensure(d->d_GM64, 8 * mat), "alloc GM64");
+        if (fp64) CK(ensure(d->d_GM64, 8 * mat), "alloc GM64");
     }
     const size_t gj_stage = (size_t)(2 * maxnt * maxnt) * 16;
     const bool stage_gj = pre && gj_stage <= std::min<size_t>(d->smem_optin, 160 * 1024);
@@ -514,7 +514,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     pa.gj = P<double>(d->d_gj);
     pa.yy = P<double>(d->d_yy);
     pa.G64 = P<double>(d->d_G64);
-    pa.GM64 = P<double>(d->d_GM64);
+    pa.GM64 = (pre && fp64) ? P<double>(d->d_GM64) : nullptr;
     pa.z64 = P<double>(d->d_z64);
     pa.w64 = P<double>(d->d_w64);
     pa.z32 = P<float>(d->d_z32);
@@ -525,12 +525,13 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     const size_t h_stage = 8 * (size_t)(maxnt * maxnr + maxnr);
     pa.stage_h = h_stage <= std::min<size_t>(d->smem_optin, 128 * 1024);
     pa.stage_gj = stage_gj;
+    pa.precond_fp32 = fp64 ? 0 : 1;
     CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : 0, pre, d->stream),
        "prep kernels");
     d->launches += pre ? 3 : 2;
     if (mixed) {
-        CK(tc_launch_pack(d->tc, P<ChannelDesc>(d->d_desc), n_channels, P<double>(d->d_G64),
-                          P<double>(d->d_GM64), P<uint8_t>(d->d_tc), d->stream), "pack operands");
+        CK(tc_launch_pack(d->tc, P<ChannelDesc>(d->d_desc), n_channels, P<float>(d->d_bt32),
+                          P<uint8_t>(d->d_tc), d->stream), "pack operands");
         d->launches++;
     }
 

@@ -586,33 +586,45 @@ __global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const Cha
 }
 
 // ------------------------------------------------------------------------------------------
-// Operand packing: Gt / P~Gt (FP64) -> `S` BF16 split terms in the core-matrix image.
+// Operand packing: [Gt | P~Gt] (FP32) -> `S` BF16 split terms in the core-matrix image. One
+// thread builds one 16-byte core-matrix row (8 consecutive K values of one A row) per term.
 // ------------------------------------------------------------------------------------------
-__global__ void pack_kernel(const ChannelDesc *desc, const double *G64, const double *GM64,
-                            uint8_t *ops, int S, int MT, int Kp)
+__global__ void pack_kernel(const ChannelDesc *desc, const float *bt32, uint8_t *ops, int S,
+                            int MT, int Kp)
 {
     const ChannelDesc d = desc[blockIdx.x];
     const int N = d.N;
     const bool pre = d.NO > N;
-    __nv_bfloat16 *base = reinterpret_cast<__nv_bfloat16 *>(ops + d.tc_off);
-    const int per_term = MT * 128 * Kp;
-    for (int e = threadIdx.x; e < per_term; e += blockDim.x) {
-        const int t = e / (128 * Kp), rem = e % (128 * Kp);
-        const int r = rem / Kp, kk = rem % Kp;
+    const float *bt = bt32 + d.bt_off;
+    uint8_t *base = ops + d.tc_off;
+    const int kgs = Kp / 8;
+    const int units = MT * 128 * kgs;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+        const int t = u / (128 * kgs), rem = u % (128 * kgs);
+        const int r = rem / kgs, kg = rem % kgs;
         const int q = r >> 5, l = r & 31;
         const int n = 64 * t + 16 * q + (l & 15), part = l >> 4;
-        double v = 0.0;
-        if (n < N && kk < N) {
-            if (part == 0) v = G64[d.mat_off + (long long)n * N + kk];
-            else if (pre) v = GM64[d.mat_off + (long long)n * N + kk];
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int kk = 8 * kg + i;
+            float x = 0.f;
+            if (n < N && kk < N && (part == 0 || pre)) x = bt[(size_t)kk * d.NOp + part * N + n];
+            v[i] = x;   // Bt row kk holds [Gt row kk | P~Gt row kk]; both blocks are symmetric
         }
-        // core-matrix position of (r, kk) within the tile
-        const int off = (r >> 3) * (Kp / 8) * 64 + (kk >> 3) * 64 + (r & 7) * 8 + (kk & 7);
-        double rem_v = v;
+        const size_t off = (size_t)((r >> 3) * kgs + kg) * 128 + (r & 7) * 16;
         for (int s = 0; s < S; ++s) {
-            const __nv_bfloat16 bv = __float2bfloat16_rn((float)rem_v);
-            rem_v -= (double)__bfloat162float(bv);
-            base[(size_t)(s * MT + t) * 128 * Kp + off] = bv;
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat16 lo = __float2bfloat16_rn(v[2 * i]);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(v[2 * i + 1]);
+                v[2 * i] -= __bfloat162float(lo);
+                v[2 * i + 1] -= __bfloat162float(hi);
+                w[i] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+            }
+            *reinterpret_cast<uint4 *>(base + (size_t)(s * MT + t) * 128 * Kp * 2 + off) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -668,11 +680,11 @@ long long tc_operand_bytes(const ChannelDesc &, const TcPlan &plan)
 }
 
 cudaError_t tc_launch_pack(const TcPlan &plan, const ChannelDesc *desc, int n_channels,
-                           const double *G64, const double *GM64, uint8_t *tc_ops, cudaStream_t s)
+                           const float *bt32, uint8_t *tc_ops, cudaStream_t s)
 {
     if (n_channels <= 0) return cudaSuccess;
-    pack_kernel<<<n_channels, 256, 0, s>>>(desc, G64, GM64, tc_ops, plan.split_terms,
-                                           plan.m_tiles, plan.kdim);
+    pack_kernel<<<n_channels, 256, 0, s>>>(desc, bt32, tc_ops, plan.split_terms, plan.m_tiles,
+                                           plan.kdim);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,8 @@ struct PrepArgs {
     double *bt64;           // CUDA-core GEMM operand (FP64), or null
     unsigned *status;
     int stage_h;            // stage H and y in shared memory
-    int stage_gj;           // run Gauss-Jordan in shared memory
+    int stage_gj;           // factorise the preconditioner in shared memory
+    int precond_fp32;       // FP32 Cholesky (FP32 / MIXED modes) instead of FP64
 };
 
 struct InitArgs {

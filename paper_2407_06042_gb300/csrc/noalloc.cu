@@ -194,7 +194,6 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
     double *d_gj = (pre && !stage_gj) ? cv.take<double>(4 * ntc) : nullptr;
     double *d_yy = cv.take<double>(n_channels);
     double *d_G64 = cv.take<double>(mat);
-    double *d_GM64 = pre ? cv.take<double>(mat) : nullptr;
     double *d_z64 = cv.take<double>(vec);
     double *d_w64 = cv.take<double>(vec);
     float *d_z32 = cv.take<float>(vec);
@@ -238,7 +237,7 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
     pa.gj = d_gj;
     pa.yy = d_yy;
     pa.G64 = d_G64;
-    pa.GM64 = d_GM64;
+    pa.GM64 = nullptr;   // FP32 mode: the preconditioned operand is emitted straight to FP32
     pa.z64 = d_z64;
     pa.w64 = d_w64;
     pa.z32 = d_z32;
@@ -249,6 +248,7 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
     const size_t h_stage = 8 * (size_t)(maxnt * maxnr + maxnr);
     pa.stage_h = h_stage <= std::min<size_t>((size_t)optin, 128 * 1024);
     pa.stage_gj = stage_gj;
+    pa.precond_fp32 = 1;
     NA_CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : 0, pre, s));
 
     InitArgs ia{};

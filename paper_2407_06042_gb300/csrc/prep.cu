@@ -18,6 +18,23 @@ __device__ __forceinline__ cd cmul(cd a, cd b) { return {a.x * b.x - a.y * b.y, 
 __device__ __forceinline__ cd cmulc(cd a, cd b) { return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; } // conj(a) b
 __device__ __forceinline__ cd csub(cd a, cd b) { return {a.x - b.x, a.y - b.y}; }
 
+// Float-float accumulator: s is the FP32 running sum, e gathers the exact rounding errors of the
+// additions (TwoSum) and of the products (FMA split), so s + e carries ~48 significant bits.
+struct FF {
+    float s = 0.f, e = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = a * b;
+        const float pe = fmaf(a, b, -p);          // exact: a b = p + pe
+        const float t = s + p;                    // TwoSum(s, p)
+        const float z = t - s;
+        const float te = (s - (t - z)) + (p - z);
+        s = t;
+        e += te + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
+
 // ------------------------------------------------------------------------------------------
 // K1: complex Gram matrix, matched filter, ||y||^2 (FP64 accumulation of FP32 inputs: every
 // product of two FP32 values is exact in FP64).
@@ -51,20 +68,24 @@ __global__ void __launch_bounds__(256) gram_kernel(PrepArgs a)
         const int bj = bi + rem;
         const int i0 = 2 * bi, j0 = 2 * bj;
         const bool i1v = i0 + 1 < nt, j1v = j0 + 1 < nt;
-        double acc[2][2][2] = {};
+        // float-float accumulation (Ogita-Rump-Oishi Sum2 over exact products): hi / lo per real
+        // and imaginary part; every product of two FP32 inputs is split exactly with an FMA
+        FF acc[2][2][2];
         const float2 *ci0 = Hp + (size_t)i0 * nr, *ci1 = Hp + (size_t)(i1v ? i0 + 1 : i0) * nr;
         const float2 *cj0 = Hp + (size_t)j0 * nr, *cj1 = Hp + (size_t)(j1v ? j0 + 1 : j0) * nr;
         for (int r = 0; r < nr; ++r) {
             const float2 u0 = ci0[r], u1 = ci1[r], v0 = cj0[r], v1 = cj1[r];
-            const double ur[2] = {u0.x, u1.x}, ui[2] = {u0.y, u1.y};
-            const double vr[2] = {v0.x, v1.x}, vi[2] = {v0.y, v1.y};
+            const float ur[2] = {u0.x, u1.x}, ui[2] = {u0.y, u1.y};
+            const float vr[2] = {v0.x, v1.x}, vi[2] = {v0.y, v1.y};
 #pragma unroll
             for (int p = 0; p < 2; ++p)
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
-                    // conj(u_p) v_q
-                    acc[p][q][0] = fma(ur[p], vr[q], fma(ui[p], vi[q], acc[p][q][0]));
-                    acc[p][q][1] = fma(ur[p], vi[q], fma(-ui[p], vr[q], acc[p][q][1]));
+                    // conj(u_p) v_q = (ur vr + ui vi) + i (ur vi - ui vr)
+                    acc[p][q][0].add_prod(ur[p], vr[q]);
+                    acc[p][q][0].add_prod(ui[p], vi[q]);
+                    acc[p][q][1].add_prod(ur[p], vi[q]);
+                    acc[p][q][1].add_prod(-ui[p], vr[q]);
                 }
         }
 #pragma unroll
@@ -73,8 +94,9 @@ __global__ void __launch_bounds__(256) gram_kernel(PrepArgs a)
             for (int q = 0; q < 2; ++q) {
                 const int i = i0 + p, j = j0 + q;
                 if (i >= nt || j >= nt || j < i) continue;
-                G[i * nt + j] = {acc[p][q][0], acc[p][q][1]};
-                if (i != j) G[j * nt + i] = {acc[p][q][0], -acc[p][q][1]};
+                const double gr = acc[p][q][0].value(), gi = acc[p][q][1].value();
+                G[i * nt + j] = {gr, gi};
+                if (i != j) G[j * nt + i] = {gr, -gi};
             }
     }
     cd *z = reinterpret_cast<cd *>(a.zc) + d.vec_off / 2;
@@ -96,63 +118,70 @@ __global__ void __launch_bounds__(256) gram_kernel(PrepArgs a)
     }
 }
 
+template <typename R> struct CT;
+template <> struct CT<float> { struct type { float x, y; }; };
+template <> struct CT<double> { using type = cd; };
+
 // ------------------------------------------------------------------------------------------
 // K2: M = (G + gamma I)^{-1} (Remark 1, Eq. (19)) through the Cholesky factorisation
 // G + gamma I = L L^H (Hermitian positive definite for gamma > 0), X = L^{-1} by forward
-// substitution, M = X^H X. The two Nt x Nt blocks live in shared memory when they fit, else in
+// substitution, M = X^H X, in FP64 (FP64 mode) or FP32 (FP32 / MIXED: any deterministic
+// preconditioner keeps the chain exact, the proposal staying a function of the state). The two
+// Nt x Nt blocks live in shared memory when they fit, else in the channel's global scratch block.
 // the channel's global scratch block.
 // ------------------------------------------------------------------------------------------
+template <typename R>
 __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
 {
     const int b = blockIdx.x;
     const ChannelDesc d = a.desc[b];
     const int nt = d.Nt;
     const double gamma = d.gamma_t / (d.dmin * d.dmin);   // gamma in the unscaled model
+    using C2 = typename CT<R>::type;
     extern __shared__ double shd[];
-    cd *Am = a.stage_gj ? reinterpret_cast<cd *>(shd) : reinterpret_cast<cd *>(a.gj) + d.mat_off / 2;
-    cd *X = Am + nt * nt;
+    C2 *Am = a.stage_gj ? reinterpret_cast<C2 *>(shd) : reinterpret_cast<C2 *>(a.gj) + d.mat_off / 2;
+    C2 *X = Am + nt * nt;
     const cd *G = reinterpret_cast<const cd *>(a.Gc) + d.mat_off / 4;
     for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
-        cd v = G[e];
-        if (e / nt == e % nt) v.x += gamma;
-        Am[e] = v;
-        X[e] = {0.0, 0.0};
+        const cd g = G[e];
+        Am[e] = {(R)(g.x + (e / nt == e % nt ? gamma : 0.0)), (R)g.y};
+        X[e] = {R(0), R(0)};
     }
     __syncthreads();
     // right-looking Cholesky, lower factor in Am (the trailing block is kept Hermitian-full)
     for (int k = 0; k < nt; ++k) {
-        const double pv = Am[k * nt + k].x;
-        if (threadIdx.x == 0 && !(pv > 0.0)) set_status(a.status, kStatusNumeric);
-        const double dk = sqrt(pv > 0.0 ? pv : 1.0);
-        const double inv = 1.0 / dk;
+        const R pv = Am[k * nt + k].x;
+        if (threadIdx.x == 0 && !(pv > R(0))) set_status(a.status, kStatusNumeric);
+        const R dk = sqrt(pv > R(0) ? pv : R(1));
+        const R inv = R(1) / dk;
         __syncthreads();
         for (int i = k + 1 + threadIdx.x; i < nt; i += blockDim.x) {
-            const cd v = Am[i * nt + k];
+            const C2 v = Am[i * nt + k];
             Am[i * nt + k] = {v.x * inv, v.y * inv};
         }
-        if (threadIdx.x == 0) Am[k * nt + k] = {dk, 0.0};
+        if (threadIdx.x == 0) Am[k * nt + k] = {dk, R(0)};
         __syncthreads();
         const int m = nt - k - 1;
         for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
             const int i = k + 1 + e / m, j = k + 1 + e % m;
             // A_ij -= L_ik conj(L_jk)
-            const cd li = Am[i * nt + k], lj = Am[j * nt + k];
-            const cd p = {li.x * lj.x + li.y * lj.y, li.y * lj.x - li.x * lj.y};
-            Am[i * nt + j] = csub(Am[i * nt + j], p);
+            const C2 li = Am[i * nt + k], lj = Am[j * nt + k];
+            const C2 v = Am[i * nt + j];
+            Am[i * nt + j] = {v.x - (li.x * lj.x + li.y * lj.y), v.y - (li.y * lj.x - li.x * lj.y)};
         }
         __syncthreads();
     }
     // X = L^{-1}, one column per thread (forward substitution)
     for (int j = threadIdx.x; j < nt; j += blockDim.x) {
-        X[j * nt + j] = {1.0 / Am[j * nt + j].x, 0.0};
+        X[j * nt + j] = {R(1) / Am[j * nt + j].x, R(0)};
         for (int i = j + 1; i < nt; ++i) {
-            double sr = 0.0, si = 0.0;
+            R sr = R(0), si = R(0);
             for (int m2 = j; m2 < i; ++m2) {
-                const cd l = Am[i * nt + m2], xv = X[m2 * nt + j];
+                const C2 l = Am[i * nt + m2], xv = X[m2 * nt + j];
                 sr += l.x * xv.x - l.y * xv.y;
                 si += l.x * xv.y + l.y * xv.x;
             }
-            const double il = 1.0 / Am[i * nt + i].x;
+            const R il = R(1) / Am[i * nt + i].x;
             X[i * nt + j] = {-sr * il, -si * il};
         }
     }
@@ -162,14 +191,14 @@ __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
     for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
         const int i = e / nt, j = e % nt;
         if (j < i) continue;
-        double sr = 0.0, si = 0.0;
+        R sr = R(0), si = R(0);
         for (int m2 = j; m2 < nt; ++m2) {   // X lower triangular: rows m2 >= max(i, j) = j
-            const cd xi = X[m2 * nt + i], xj = X[m2 * nt + j];
+            const C2 xi = X[m2 * nt + i], xj = X[m2 * nt + j];
             sr += xi.x * xj.x + xi.y * xj.y;   // conj(xi) xj
             si += xi.x * xj.y - xi.y * xj.x;
         }
-        M[i * nt + j] = {sr, si};
-        if (i != j) M[j * nt + i] = {sr, -si};
+        M[i * nt + j] = {(double)sr, (double)si};
+        if (i != j) M[j * nt + i] = {(double)sr, -(double)si};
     }
 }
 
@@ -180,15 +209,26 @@ __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
 //   zt = d [Re z; Im z],  wt = P~ zt = [Re(M z); Im(M z)] / d
 //   Bt (N x NOp, the CUDA-core GEMM operand): row m = [Gt row m | GMt row m | 0 pad]
 // ------------------------------------------------------------------------------------------
+// Entry (r, c) of real([(G + gamma I)^{-1} G]) = real(I - gamma M) (the stacked embedding).
+__device__ __forceinline__ double gm_entry(const cd *M, int nt, double gamma, int r, int c)
+{
+    const cd m = M[(r % nt) * nt + (c % nt)];
+    const int q = (r >= nt) * 2 + (c >= nt);
+    const double v = (q == 0 || q == 3) ? m.x : (q == 1 ? -m.y : m.y);
+    return -gamma * v + (r == c ? 1.0 : 0.0);
+}
+
 template <typename T>
 __device__ void emit_bt(const PrepArgs &a, const ChannelDesc &d, T *bt)
 {
-    const int N = d.N;
+    const int N = d.N, nt = d.Nt;
+    const cd *M = reinterpret_cast<const cd *>(a.Mc) + d.mat_off / 4;
+    const double gamma = d.gamma_t / (d.dmin * d.dmin);
     for (int e = threadIdx.x; e < N * d.NOp; e += blockDim.x) {
         const int m = e / d.NOp, o = e % d.NOp;
         double v = 0.0;
         if (o < N) v = a.G64[d.mat_off + (long long)m * N + o];
-        else if (o < d.NO) v = a.GM64[d.mat_off + (long long)m * N + (o - N)];
+        else if (o < d.NO) v = gm_entry(M, nt, gamma, m, o - N);
         bt[e] = (T)v;
     }
 }
@@ -217,14 +257,10 @@ __global__ void __launch_bounds__(256) emit_kernel(PrepArgs a)
     if (pre) {
         const cd *M = reinterpret_cast<const cd *>(a.Mc) + d.mat_off / 4;
         const double gamma = d.gamma_t / d2;
-        double *GM = a.GM64 + d.mat_off;
-        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-            const int r = e / N, c = e % N;
-            const cd m = M[(r % nt) * nt + (c % nt)];
-            const int q = (r >= nt) * 2 + (c >= nt);
-            double v = (q == 0 || q == 3) ? m.x : (q == 1 ? -m.y : m.y);
-            v = -gamma * v + (r == c ? 1.0 : 0.0);
-            GM[e] = v;
+        if (a.GM64) {
+            double *GM = a.GM64 + d.mat_off;
+            for (int e = threadIdx.x; e < N * N; e += blockDim.x)
+                GM[e] = gm_entry(M, nt, gamma, e / N, e % N);
         }
         for (int i = threadIdx.x; i < nt; i += blockDim.x) {
             double re = 0.0, im = 0.0;
@@ -332,12 +368,13 @@ cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
     gram_kernel<<<n_channels, 256, a.stage_h ? h_stage_bytes : 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (preconditioned) {
+        auto k = a.precond_fp32 ? precond_kernel<float> : precond_kernel<double>;
         if (gj_stage_bytes > 48 * 1024) {
-            e = cudaFuncSetAttribute(precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)gj_stage_bytes);
             if (e != cudaSuccess) return e;
         }
-        precond_kernel<<<n_channels, 256, gj_stage_bytes, s>>>(a);
+        k<<<n_channels, 256, gj_stage_bytes, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     emit_kernel<<<n_channels, 256, 0, s>>>(a);

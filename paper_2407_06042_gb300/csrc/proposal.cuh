@@ -10,7 +10,7 @@
 //     w_j = 2^(l2(j) - l2(j*)),  l2(j) - l2(j*) = (j - j*) (a2 - c2 (j + j* - 2k)),
 // which is <= 0 (no overflow) with w_{j*} = 1 (the total never underflows). The cumulative
 // weights S_j are summed in ascending level order, and a draw with uniform u takes the smallest
-// j with u S_{L-1} < S_j (the count of j < L-1 with S_j <= u S_{L-1}).
+// j with u S_{L-1} < S_j (binary search over the S_j).
 #pragma once
 
 #include "common.cuh"
@@ -43,30 +43,59 @@ __device__ __forceinline__ float vertex_level(float a2, float inv2c, float kf)
     return m;
 }
 
-// Weights of every level and their total; returns j* (as float).
+// The relative logit as a polynomial in j: l2(j) - l2(j*) = (j - j*) (P - c2 j)
+// = (-c2 j + B) j + C0 with P = a2 - c2 (j* - 2k), B = P + c2 j*, C0 = -j* P, evaluated by Horner
+// (two FMAs per level for compile-time j).
+struct Poly {
+    float B, C0;
+};
+
+__device__ __forceinline__ Poly rel_poly(float a2, float c2, float js, float kf)
+{
+    const float P = fmaf(-c2, js - 2.f * kf, a2);
+    return Poly{fmaf(c2, js, P), -js * P};
+}
+
+__device__ __forceinline__ float rel_logit2(const Poly &p, float c2, float jf)
+{
+    return fmaf(fmaf(-c2, jf, p.B), jf, p.C0);
+}
+
+// Cumulative weights S_j (levels ascending) of the factor and the vertex polynomial.
 template <int L>
-__device__ __forceinline__ float factor_weights(float a2, float c2, float inv2c, float kf,
-                                                float (&w)[L], float &total)
+__device__ __forceinline__ Poly factor_cumulative(float a2, float c2, float inv2c, float kf,
+                                                  float (&S)[L])
 {
     const float js = vertex_level<L>(a2, inv2c, kf);
-    const float P = fmaf(-c2, js - 2.f * kf, a2);   // a2 - c2 (j* - 2k)
+    const Poly p = rel_poly(a2, c2, js, kf);
     float acc = 0.f;
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-        const float dj = (float)j - js;
-        const float e = dj * fmaf(-c2, (float)j, P);
-        w[j] = ex2_approx(e);
-        acc += w[j];
+        acc += ex2_approx(rel_logit2(p, c2, (float)j));
+        S[j] = acc;
     }
-    total = acc;
-    return js;
+    return p;
 }
 
-// log2 of the unnormalised weight of level j relative to the vertex (same formula as above).
-__device__ __forceinline__ float rel_logit2(float a2, float c2, float js, float kf, float jf)
+// Smallest j with target < S_j (S nondecreasing, target < S_{L-1} in exact arithmetic): a binary
+// search over the cumulative weights, log2 L compares.
+template <int L>
+__device__ __forceinline__ int cdf_search(const float (&S)[L], float target)
 {
-    const float P = fmaf(-c2, js - 2.f * kf, a2);
-    return (jf - js) * fmaf(-c2, jf, P);
+    if constexpr (L == 2) {
+        return S[0] <= target ? 1 : 0;
+    } else if constexpr (L == 4) {
+        const bool b1 = S[1] <= target;
+        const float m = b1 ? S[2] : S[0];
+        const bool b0 = m <= target;
+        return (b1 ? 2 : 0) + (b0 ? 1 : 0);
+    } else {
+        const bool b2 = S[3] <= target;
+        const bool b1 = (b2 ? S[5] : S[1]) <= target;
+        const float m = b2 ? (b1 ? S[6] : S[4]) : (b1 ? S[2] : S[0]);
+        const bool b0 = m <= target;
+        return (b2 ? 4 : 0) + (b1 ? 2 : 0) + (b0 ? 1 : 0);
+    }
 }
 
 // Draw from the factor with uniform u; returns the level and log2 q of it.
@@ -74,18 +103,11 @@ template <int L>
 __device__ __forceinline__ int factor_draw(float a2, float c2, float inv2c, int k, float u,
                                            float &log2q)
 {
-    float w[L], total;
+    float S[L];
     const float kf = (float)k;
-    const float js = factor_weights<L>(a2, c2, inv2c, kf, w, total);
-    const float target = u * total;
-    float S = 0.f;
-    int sel = 0;
-#pragma unroll
-    for (int j = 0; j < L - 1; ++j) {
-        S += w[j];
-        sel += (S <= target) ? 1 : 0;
-    }
-    log2q = rel_logit2(a2, c2, js, kf, (float)sel) - lg2_approx(total);
+    const Poly p = factor_cumulative<L>(a2, c2, inv2c, kf, S);
+    const int sel = cdf_search<L>(S, u * S[L - 1]);
+    log2q = rel_logit2(p, c2, (float)sel) - lg2_approx(S[L - 1]);
     return sel;
 }
 
@@ -93,10 +115,10 @@ __device__ __forceinline__ int factor_draw(float a2, float c2, float inv2c, int 
 template <int L>
 __device__ __forceinline__ float factor_log2q(float a2, float c2, float inv2c, int k, int j_eval)
 {
-    float w[L], total;
+    float S[L];
     const float kf = (float)k;
-    const float js = factor_weights<L>(a2, c2, inv2c, kf, w, total);
-    return rel_logit2(a2, c2, js, kf, (float)j_eval) - lg2_approx(total);
+    const Poly p = factor_cumulative<L>(a2, c2, inv2c, kf, S);
+    return rel_logit2(p, c2, (float)j_eval) - lg2_approx(S[L - 1]);
 }
 
 }  // namespace mcmcdet

@@ -28,10 +28,10 @@ bool tc_make_plan(const std::vector<ChannelDesc> &desc, int chains, int split_te
 // Bytes of one channel's packed BF16 operand block.
 long long tc_operand_bytes(const ChannelDesc &c, const TcPlan &plan);
 
-// Packs Gt / P~Gt (FP64) into the BF16 split operand blocks, canonical tcgen05 layout.
+// Packs [Gt | P~Gt] (the FP32 CUDA-core operand, N x NOp per channel) into the BF16 split
+// operand blocks in the canonical tcgen05 layout.
 cudaError_t tc_launch_pack(const TcPlan &plan, const ChannelDesc *desc, int n_channels,
-                           const double *G64, const double *GM64, uint8_t *tc_ops,
-                           cudaStream_t s);
+                           const float *bt32, uint8_t *tc_ops, cudaStream_t s);
 
 cudaError_t tc_launch_chains(const ChainArgs &a, const TcPlan &plan, cudaStream_t s);
 
