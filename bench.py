@@ -93,6 +93,86 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def pipe_peaks():
+    """Measured pipe throughputs of this GPU (ops/s): MUFU ex2, FP32 FMA, FP32x2 FMA lanes, FP64."""
+    import ctypes
+    from paper_2407_06042_gb300 import build as _b
+    lib = ctypes.CDLL(_b.build_peaks())
+    out = (ctypes.c_double * 4)()
+    if lib.mcmc_pipe_peaks(out) != 0:
+        return None
+    return {"ex2": out[0], "fma": out[1], "fma2_lanes": out[2], "dfma": out[3]}
+
+
+def _kernel_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+CHAIN_SOURCES = {
+    "mixed": ["paper_2407_06042_gb300/csrc/chains_tc.cu", "paper_2407_06042_gb300/csrc/proposal.cuh",
+              "paper_2407_06042_gb300/csrc/common.cuh"],
+    "fp32": ["paper_2407_06042_gb300/csrc/chains_simt.cu", "paper_2407_06042_gb300/csrc/proposal.cuh",
+             "paper_2407_06042_gb300/csrc/common.cuh"],
+}
+PROFILE_FILES = {"mixed": "profiles/chains_tc_rayleigh_32x32_64qam.md",
+                 "fp32": "profiles/chains_simt_rayleigh_32x32_64qam.md"}
+
+
+def profiled_traffic(precision):
+    """DRAM bytes per full-size launch of the chain kernel from the committed ncu summary, or
+    None when the kernel sources changed since that capture."""
+    f = PROFILE_FILES.get(precision)
+    if not f or not os.path.exists(os.path.join(ROOT, f)):
+        return None
+    want, traffic = None, None
+    for line in open(os.path.join(ROOT, f)):
+        if line.startswith("source_hash:"):
+            want = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_full_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    if want != _kernel_hash(CHAIN_SOURCES[precision]):
+        return None
+    return traffic
+
+
+def chain_roofline(precision, w, units, chain_ms):
+    """Roofline of the chain loop (the dominant kernel). Its binding resource is the proposal
+    arithmetic: per chain-iteration the method evaluates, for every real dimension, two
+    categorical factors of L weights (one exponential each) and their two log-normalisers, plus
+    one log per MH test. Those transcendental operations run on the MUFU pipe, whose measured
+    ex2 rate is the peak. The Gram products (tensor pipe, MIXED) are reported beside it."""
+    N = 2 * w["nt"]
+    L = int(np.sqrt(w["qam"]))
+    per_ci = N * (2 * L + 2) + 1
+    peaks = pipe_peaks() or {}
+    t = chain_ms * 1e-3
+    achieved = per_ci * units / t
+    peak = peaks.get("ex2")
+    gemm = 2 * N * (2 * N)
+    out = {"bound": "alu", "achieved": achieved / 1e9,
+           "peak": (peak / 1e9) if peak else None, "unit": "Gop/s",
+           "frac": (achieved / peak) if peak else None,
+           "traffic": profiled_traffic(precision),
+           "pipe": "MUFU transcendental (ex2/lg2), measured ex2 rate of this GPU",
+           "per_unit": f"{per_ci} transcendental ops per chain-iteration (N(2L+2)+1, N={N}, L={L})",
+           "launch_ms": chain_ms, "peaks_measured": peaks}
+    if precision == "mixed":
+        tf = gemm * units / t / 1e12
+        out["tensor"] = {"achieved_tflops": tf, "peak_tflops": 1899.4, "frac": tf / 1899.4,
+                         "per_unit": f"{gemm} Gram flops per chain-iteration (D' = X'[Gt|PGt])"}
+    else:
+        fma = peaks.get("fma")
+        gf = gemm * units / t
+        out["fp32_gemm"] = {"achieved_tflops": gf / 1e12,
+                            "peak_tflops": (2 * fma / 1e12) if fma else None,
+                            "frac": (gf / (2 * fma)) if fma else None}
+    return out
+
+
 def load_batch(scale: float, rank: int):
     w = dict(workload.WORKLOADS[WORKLOAD])
     n = max(1, int(round(w["per_snr"] * scale)))
@@ -325,22 +405,11 @@ def main():
         ms32, kms32, _, _ = timed(d32, max(1, args.steps // 2), 1)
         ber32 = ber_of(batch, o_llr.cpu().numpy(), o_idx.cpu().numpy())
         fp32_line = {"value": units_rank * world / (ms32 * 1e-3), "ms_per_step": ms32,
-                     "chain_kernel_ms": kms32, "ber": ber32}
+                     "chain_kernel_ms": kms32, "ber": ber32,
+                     "roofline": chain_roofline("fp32", w, units_rank, kms32)}
         d32.destroy()
 
-    # roofline of the dominant kernel (the chain loop): algorithmic FP32 work per chain-iteration
-    N = 2 * w["nt"]
-    L = int(np.sqrt(w["qam"]))
-    NO = 2 * N
-    gemm_flops = 2 * N * NO                   # D' = X' [Gt | P~Gt]
-    prop_flops = N * (2 * 4 * L + 12)         # forward + reverse logits, CDF, energy terms
-    flops_per_ci = gemm_flops + prop_flops
-    achieved_tf = flops_per_ci * units_rank / (chain_ms * 1e-3) / 1e12
-    peak_tf = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 CUDA-core peak: SMs x lanes x FMA x max clock
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved_tf / peak_tf, "traffic": None,
-                "kernel": "chain loop", "per_unit": f"{flops_per_ci} FP32 flop per chain-iteration",
-                "launch_ms": chain_ms}
+    roofline = chain_roofline(precision, w, units_rank, chain_ms)
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -17,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmcmcdet.so")
+PEAKS_SRC = os.path.join(HERE, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(OUT_DIR, "libmcmcpeaks.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -85,6 +87,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_peaks(force: bool = False) -> str:
+    """Compile the pipe-throughput microbenchmarks (bench.py's roofline denominators)."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    nvcc = _nvcc()
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc, *ARCH, "-O3", "-shared", "-Xcompiler", "-fPIC", "-o", tmp, PEAKS_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
 
 
 if __name__ == "__main__":  # pragma: no cover

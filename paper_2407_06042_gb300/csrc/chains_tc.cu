@@ -112,7 +112,7 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 
 // Shared-memory layout of the kernel (bytes).
 struct TcLayout {
-    uint32_t a, b, red, dred, acc, impr, ref, fref, bar, tmem, total;
+    uint32_t a, b, red, dred, acc, impr, ref, fref, kb, bar, tmem, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
@@ -133,6 +133,7 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
     L.impr = take((uint32_t)C * 4, 16);
     L.ref = take((uint32_t)C * 8, 16);       // FP64 refresh results per chain
     L.fref = take((uint32_t)C * kMaxN, 16);  // states for the FP64 refresh
+    L.kb = take((uint32_t)C * kMaxN, 16);    // best visited state of every chain
     L.bar = take(16, 8);
     L.tmem = take(4, 4);
     L.total = (o + 127) / 128 * 128;
@@ -154,6 +155,7 @@ struct TcCtx {
     int *sacc, *simpr;
     double *sref;
     int8_t *sfs;
+    int8_t *skb;
     uint32_t bar_mma;
     uint32_t tmem;
     uint32_t idesc;
@@ -163,7 +165,7 @@ struct TcCtx {
 };
 
 // Issue the MMAs of one transition (thread 0) and wait for them (everyone). Returns false on a
-// bounded-wait expiry; every thread of the CTA takes the same branch.
+// bounded-wait expiry of this thread's wait; callers combine the verdicts in a CTA-wide vote.
 template <int MT>
 __device__ __forceinline__ bool tc_gemm(TcCtx &x)
 {
@@ -193,7 +195,7 @@ __device__ __forceinline__ bool tc_gemm(TcCtx &x)
     const bool ok = mbar_wait(x.bar_mma, x.mma_phase);
     x.mma_phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return !__syncthreads_or(!ok);
+    return ok;   // the caller folds it into its next CTA-wide vote
 }
 
 // TMEM -> registers: Gt x (g) and P~ Gt x (m) of this thread's dimension for its 8 chains.
@@ -220,42 +222,50 @@ __device__ __forceinline__ unsigned short bf16_bits_of_int(int v)
     return (unsigned short)(__float_as_uint((float)v) >> 16);
 }
 
-template <int MT, int L>
+// One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
+// every chain column is live, so no per-(dimension, chain) validity test is needed. Levels are
+// held as exact small floats.
+template <int MT, int L, bool FULL>
 __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const ChannelDesc &d,
                         bool &alive)
 {
     const int N = d.N, nC = it.nc, C = x.C;
     const bool pre = d.NO > N;
-    const float clin = (float)d.clin;
-    const float a2s = clin * kLog2e;              // slope -> log2 units
+    const float a2s = (float)d.clin * kLog2e;     // slope -> log2 units
     const float c2 = (float)d.cquad * kLog2e;
     const float inv2c = 0.5f / c2;
     const float cf2 = (float)d.cf * kLog2e;       // df_tau -> log2 units
+    const float lm1 = (float)(L - 1);
     const int cbase = 8 * x.cgi + 4 * x.h;         // first of this thread's 4 chains (CTA-local)
     float zt[MT], wt[MT];
     int nd[MT];
-    int8_t k[MT][4], kb[MT][4];
+    bool live[MT][4];
+    float k[MT][4];
     float Dg[MT][4], sl[MT][4];                    // Gt x and the slope (log2 units)
+    int8_t *skb = x.skb;                           // best visited states [C][kMaxN]
     const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
     const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
+    uint32_t boff[MT];                             // byte offset of this thread's B element, chain cbase
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
         const int n = 64 * t + 16 * x.q + x.dl;
         nd[t] = n;
-        const bool v = n < N;
+        const bool v = FULL || n < N;
         zt[t] = v ? gz[n] : 0.f;
         wt[t] = v ? gw[n] : 0.f;
+        boff[t] = (uint32_t)(cbase >> 3) * x.sbo_b + (uint32_t)(n >> 3) * b_lbo() +
+                  (uint32_t)(cbase & 7) * 16u + (uint32_t)(n & 7) * 2u;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = cbase + j;
-            int8_t kv = 0, kbv = 0;
-            if (v && c < nC) {
+            live[t][j] = FULL || (v && c < nC);
+            float kv = 0.f;
+            if (live[t][j]) {
                 const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
-                kv = A.states[e];
-                kbv = A.best_states[e];
+                kv = (float)A.states[e];
+                skb[c * kMaxN + n] = A.best_states[e];
             }
             k[t][j] = kv;
-            kb[t][j] = kbv;
         }
     }
     double fcur = 0.0, fbest = 0.0;
@@ -265,24 +275,25 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         fcur = A.f[ci];
         fbest = A.best_f[ci];
     }
-    auto write_b = [&](const int8_t (&kk)[MT][4]) {
+    // x as BF16 into the B operand: bits of the exact float 2k - (L-1); dead slots write 0
+    auto write_b = [&](const float (&kk)[MT][4]) {
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
-            const int n = nd[t];
-            if (n >= x.Kp) continue;
+            if (!FULL && nd[t] >= x.Kp) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int c = cbase + j;
-                if (c >= C) continue;
-                const int xv = (n < N && c < nC) ? odd_of(kk[t][j], L) : 0;
-                const uint32_t off = (uint32_t)(c >> 3) * x.sbo_b + (uint32_t)(n >> 3) * b_lbo() +
-                                     (uint32_t)(c & 7) * 16u + (uint32_t)(n & 7) * 2u;
-                *reinterpret_cast<unsigned short *>(x.sB + off) = bf16_bits_of_int(xv);
+                if (!FULL && cbase + j >= C) continue;
+                const float xv = live[t][j] ? fmaf(2.f, kk[t][j], -lm1) : 0.f;
+                *reinterpret_cast<unsigned short *>(x.sB + boff[t] + 16u * j) =
+                    (unsigned short)(__float_as_uint(xv) >> 16);
             }
         }
     };
     write_b(k);
-    if (alive && !tc_gemm<MT>(x)) { alive = false; set_status(A.status, kStatusTimeout); }
+    if (alive) {
+        const bool ok = tc_gemm<MT>(x);
+        if (__syncthreads_or(!ok)) { alive = false; set_status(A.status, kStatusTimeout); }
+    }
     {
         float g[MT][4], m[MT][4];
         if (alive) tc_read<MT>(x, g, m);
@@ -302,13 +313,13 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         for (int j = 0; j < 4; ++j) { lin[j] = 0.f; quad[j] = 0.f; }
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
-            if (nd[t] >= N) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float xn = (float)odd_of(k[t][j], L);
+                if (!live[t][j]) continue;
+                const float xn = fmaf(2.f, k[t][j], -lm1);
                 lin[j] = fmaf(xn, zt[t], lin[j]);
                 quad[j] = fmaf(xn, Dg[t][j], quad[j]);
-                kb[t][j] = k[t][j];
+                skb[(cbase + j) * kMaxN + nd[t]] = (int8_t)k[t][j];
             }
         }
         const float rl = reduce_scatter16(lin, x.dl);
@@ -332,51 +343,43 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     for (int i = 0; i < A.iterations && alive; ++i) {
         const uint32_t t_it = (uint32_t)(A.t_offset + 1 + i);
         float part[4], dpart[4];
-        int8_t kp[MT][4];
+        float kp[MT][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) { part[j] = 0.f; dpart[j] = 0.f; }
         // 1. proposal draw (log2 q(x'|x) accumulated with a minus sign)
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             const int n = nd[t];
-            const bool v = n < N;
-            {
-                const int cq0 = cbase;
-                const bool any = v && cq0 < nC;
-                U4 w = {0, 0, 0, 0};
-                if (any)
-                    w = philox4x32_10(t_it, (uint32_t)n, (uint32_t)it.b,
-                                      (uint32_t)((it.c0 + cq0) >> 2), A.key0, A.key1);
+            U4 w = {0, 0, 0, 0};
+            if (FULL || live[t][0])
+                w = philox4x32_10(t_it, (uint32_t)n, (uint32_t)it.b,
+                                  (uint32_t)((it.c0 + cbase) >> 2), A.key0, A.key1);
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int j = jj;
-                    int sel = k[t][j];
-                    if (any && cq0 + jj < nC) {
-                        float lq;
-                        sel = factor_draw<L>(sl[t][j], c2, inv2c, k[t][j],
-                                             uniform_f(word_of(w, jj)), lq);
-                        part[j] -= lq;
-                    }
-                    kp[t][j] = (int8_t)sel;
+            for (int j = 0; j < 4; ++j) {
+                float sel = k[t][j];
+                if (live[t][j]) {
+                    float lq;
+                    sel = factor_draw_f<L>(sl[t][j], c2, inv2c, k[t][j], uniform_f(word_of(w, j)), lq);
+                    part[j] -= lq;
                 }
+                kp[t][j] = sel;
             }
         }
         write_b(kp);
-        // 2. D' = A X'^T on the tensor core
-        if (!tc_gemm<MT>(x)) { alive = false; set_status(A.status, kStatusTimeout); break; }
+        // 2. D' = A X'^T on the tensor core (the timeout verdict joins the next CTA barrier)
+        const bool mma_ok = tc_gemm<MT>(x);
         // 3. reverse factor and energy difference
         float gp[MT][4], mp[MT][4];
         tc_read<MT>(x, gp, mp);
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
-            const bool v = nd[t] < N;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float ap = a2s * (pre ? (wt[t] - mp[t][j]) : (zt[t] - gp[t][j]));
                 mp[t][j] = ap;   // slope of x', kept for the update
-                if (v && cbase + j < nC) {
-                    part[j] += factor_log2q<L>(ap, c2, inv2c, kp[t][j], k[t][j]);
-                    dpart[j] += (float)(2 * (kp[t][j] - k[t][j])) * (2.f * zt[t] - Dg[t][j] - gp[t][j]);
+                if (live[t][j]) {
+                    part[j] += factor_log2q_f<L>(ap, c2, inv2c, kp[t][j], k[t][j]);
+                    dpart[j] = fmaf(2.f * (kp[t][j] - k[t][j]), 2.f * zt[t] - Dg[t][j] - gp[t][j], dpart[j]);
                 }
             }
         }
@@ -389,7 +392,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             x.dred[x.q * C + c] = rd;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        if (__syncthreads_or(!mma_ok)) { alive = false; set_status(A.status, kStatusTimeout); break; }
         if (x.tid < nC) {
             const int c = x.tid;
             const float s = x.red[c] + x.red[C + c] + x.red[2 * C + c] + x.red[3 * C + c];
@@ -408,35 +411,30 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 cnt += 1;
                 if (fcur > fbest) { fbest = fcur; im = 1; }
             }
-            x.sacc[c] = ok;
-            x.simpr[c] = im;
+            x.sacc[c] = ok | (im << 1);
         }
         __syncthreads();
         // 5. accepted chains take x' and its caches
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = cbase + j;
-            const int ok = c < nC ? x.sacc[c] : 0;
-            const int im = c < nC ? x.simpr[c] : 0;
+            const int fl = (FULL || c < nC) ? x.sacc[c] : 0;
+            const bool ok = fl & 1, im = fl & 2;
 #pragma unroll
             for (int t = 0; t < MT; ++t) {
-                if (ok) {
-                    k[t][j] = kp[t][j];
-                    Dg[t][j] = gp[t][j];
-                    sl[t][j] = mp[t][j];
-                }
-                if (im) kb[t][j] = kp[t][j];
+                k[t][j] = ok ? kp[t][j] : k[t][j];
+                Dg[t][j] = ok ? gp[t][j] : Dg[t][j];
+                sl[t][j] = ok ? mp[t][j] : sl[t][j];
+                if (im && live[t][j]) skb[c * kMaxN + nd[t]] = (int8_t)kp[t][j];
             }
         }
         // periodic FP64 refresh of the tracked energies (decisions never read them)
         if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
 #pragma unroll
-            for (int t = 0; t < MT; ++t) {
-                if (nd[t] >= N) continue;
+            for (int t = 0; t < MT; ++t)
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (cbase + j < nC) x.sfs[(cbase + j) * kMaxN + nd[t]] = k[t][j];
-            }
+                    if (live[t][j]) x.sfs[(cbase + j) * kMaxN + nd[t]] = (int8_t)k[t][j];
             __syncthreads();
             const double *G = A.G64 + d.mat_off;
             const double *z = A.z64 + d.vec_off;
@@ -444,10 +442,10 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 double quad = 0.0, lin = 0.0;
                 for (int n = x.lane; n < N; n += 32) {
                     const double xn = odd_of(x.sfs[c * kMaxN + n], L);
-                    double s = 0.0;
+                    double sacc = 0.0;
                     for (int m = 0; m < N; ++m)
-                        s = fma(G[(size_t)n * N + m], (double)odd_of(x.sfs[c * kMaxN + m], L), s);
-                    quad = fma(xn, s, quad);
+                        sacc = fma(G[(size_t)n * N + m], (double)odd_of(x.sfs[c * kMaxN + m], L), sacc);
+                    quad = fma(xn, sacc, quad);
                     lin = fma(xn, z[n], lin);
                 }
 #pragma unroll
@@ -468,15 +466,12 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     // write back this work item
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
-        const int n = nd[t];
-        if (n >= N) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int c = cbase + j;
-            if (c >= nC) continue;
-            const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
-            A.states[e] = k[t][j];
-            A.best_states[e] = kb[t][j];
+            if (!live[t][j]) continue;
+            const long long e = d.state_off + (long long)(it.c0 + cbase + j) * N + nd[t];
+            A.states[e] = (int8_t)k[t][j];
+            A.best_states[e] = skb[(cbase + j) * kMaxN + nd[t]];
             if (A.dexp) A.dexp[e] = Dg[t][j];
         }
     }
@@ -486,6 +481,14 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         A.best_f[ci] = fbest;
         A.accepts[ci] += cnt;
     }
+}
+
+template <int MT, int L>
+__device__ __forceinline__ void tc_item_dispatch(const ChainArgs &A, TcCtx &x, const WorkItem &it,
+                                                 const ChannelDesc &d, bool &alive)
+{
+    if (d.N == 64 * MT && it.nc == x.C) tc_item<MT, L, true>(A, x, it, d, alive);
+    else tc_item<MT, L, false>(A, x, it, d, alive);
 }
 
 template <int MT>
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const Cha
     x.simpr = reinterpret_cast<int *>(smem + lay.impr);
     x.sref = reinterpret_cast<double *>(smem + lay.ref);
     x.sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
+    x.skb = reinterpret_cast<int8_t *>(smem + lay.kb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.tmem);
     const uint32_t bar_tma = smem_u32(&bars[0]);
@@ -572,9 +576,9 @@ __global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const Cha
         tma_phase ^= 1u;
         if (!alive) break;
         switch (d.L) {
-        case 2: tc_item<MT, 2>(A, x, it, d, alive); break;
-        case 4: tc_item<MT, 4>(A, x, it, d, alive); break;
-        default: tc_item<MT, 8>(A, x, it, d, alive); break;
+        case 2: tc_item_dispatch<MT, 2>(A, x, it, d, alive); break;
+        case 4: tc_item_dispatch<MT, 4>(A, x, it, d, alive); break;
+        default: tc_item_dispatch<MT, 8>(A, x, it, d, alive); break;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();

@@ -121,4 +121,40 @@ __device__ __forceinline__ float factor_log2q(float a2, float c2, float inv2c, i
     return rel_logit2(p, c2, (float)j_eval) - lg2_approx(S[L - 1]);
 }
 
+// Float-level forms (levels held as exact small floats, no integer conversions): draw returns the
+// level as a float.
+template <int L>
+__device__ __forceinline__ float factor_draw_f(float a2, float c2, float inv2c, float kf, float u,
+                                               float &log2q)
+{
+    float S[L];
+    const Poly p = factor_cumulative<L>(a2, c2, inv2c, kf, S);
+    const float target = u * S[L - 1];
+    float sel;
+    if constexpr (L == 2) {
+        sel = S[0] <= target ? 1.f : 0.f;
+    } else if constexpr (L == 4) {
+        const bool b1 = S[1] <= target;
+        const bool b0 = (b1 ? S[2] : S[0]) <= target;
+        sel = (b1 ? 2.f : 0.f) + (b0 ? 1.f : 0.f);
+    } else {
+        const bool b2 = S[3] <= target;
+        const bool b1 = (b2 ? S[5] : S[1]) <= target;
+        const float m = b2 ? (b1 ? S[6] : S[4]) : (b1 ? S[2] : S[0]);
+        const bool b0 = m <= target;
+        sel = (b2 ? 4.f : 0.f) + (b1 ? 2.f : 0.f) + (b0 ? 1.f : 0.f);
+    }
+    log2q = rel_logit2(p, c2, sel) - lg2_approx(S[L - 1]);
+    return sel;
+}
+
+template <int L>
+__device__ __forceinline__ float factor_log2q_f(float a2, float c2, float inv2c, float kf,
+                                                float jf)
+{
+    float S[L];
+    const Poly p = factor_cumulative<L>(a2, c2, inv2c, kf, S);
+    return rel_logit2(p, c2, jf) - lg2_approx(S[L - 1]);
+}
+
 }  // namespace mcmcdet
