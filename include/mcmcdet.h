@@ -82,15 +82,23 @@ typedef struct {
     int32_t refresh_period; /* R > 0: recompute every chain's energy in FP64 every R transitions
                                (FP32/MIXED; FP64 mode is exact throughout); 0: never during a run */
     int32_t split_terms;    /* MIXED: BF16 terms G is split into (2 = hi+lo, 3 = hi+lo+lo2) */
-    int32_t engine;         /* 0: autotuned; otherwise a fixed kernel variant (MCMC_ENGINE_*) */
+    int32_t engine;         /* MCMC_ENGINE_AUTO (autotuned per shape class), _SIMT or _TC, optionally
+                               OR-ed with MCMC_ENGINE_GRAPH */
     int32_t reserved;       /* must be 0 */
     uint64_t seed;          /* Philox key */
     void *stream;           /* cudaStream_t to enqueue on; NULL: the handle creates its own */
 } mcmc_config;
 
+/* Chain-kernel engine. AUTO: every shape class (N, L) of a batch gets the launch shape an
+ * autotuner found fastest when the class was first seen in the process (probe launches timed on
+ * that batch at preprocess): for MIXED precision the tcgen05 kernel at 16 or 32 chains per CTA or
+ * the CUDA-core kernel (FP32 products, at least as accurate as the split-BF16 ones); for FP32 the
+ * CUDA-core kernel's chain tile. SIMT / TC force an engine (TC requires MIXED). GRAPH: each
+ * run_chains captures its launches (one per shape class) into a CUDA graph and replays it. */
 #define MCMC_ENGINE_AUTO 0
-#define MCMC_ENGINE_SIMT 1      /* CUDA-core chain kernel (FP64 / FP32) */
-#define MCMC_ENGINE_TC 2        /* tcgen05 chain kernel (MIXED) */
+#define MCMC_ENGINE_SIMT 1      /* CUDA-core chain kernel (FP64 / FP32 / MIXED) */
+#define MCMC_ENGINE_TC 2        /* tcgen05 chain kernel (MIXED, N <= 128) */
+#define MCMC_ENGINE_GRAPH 4     /* flag: replay run_chains from a captured CUDA graph */
 
 /* Per-batch statistics (host struct, filled by mcmc_detect_estimate when non-NULL). */
 typedef struct {

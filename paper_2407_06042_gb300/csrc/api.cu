@@ -8,8 +8,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -30,6 +33,24 @@ struct HostBuf {
     size_t cap = 0;
 };
 
+// One chain-kernel launch: channels of one shape class on one engine.
+struct Group {
+    int engine = 0;            // MCMC_ENGINE_SIMT or MCMC_ENGINE_TC
+    int tile = 0;              // TC: chains per CTA; SIMT: chains per work item
+    TcPlan plan{};             // TC
+    bool bt_smem = false;      // SIMT: GEMM operand staged in shared memory
+    size_t smem = 0;           // SIMT: dynamic shared memory
+    int max_n = 0, max_nop = 0;
+    std::vector<WorkItem> items;
+    DevBuf d_items;
+};
+
+// Engine choice of one shape class.
+struct Choice {
+    int engine = 0;
+    int tile = 0;
+};
+
 }  // namespace
 
 struct mcmc_detector {
@@ -47,20 +68,19 @@ struct mcmc_detector {
     bool prepared = false;
     int n_channels = 0;
     std::vector<ChannelDesc> desc;
-    std::vector<WorkItem> items;
+    std::vector<Choice> choice;     // per channel
+    std::vector<Group> groups;
+    cudaGraphExec_t graph = nullptr;
+    int tuned_classes = 0;
     int max_n = 0, max_nop = 0, max_nt = 0, max_nr = 0;
     long long tot_states = 0, tot_mat = 0, tot_bt = 0, tot_vec = 0, tot_bits = 0, tot_ant = 0;
     long long tot_tc = 0;
     long long transitions = 0;
     bool f_valid = false;   // tracked energies hold the current states' values
     bool d_valid = false;   // d_dexp holds Gt x of the current states
-    int cg = 0;
-    size_t chain_smem = 0;
-    bool bt_in_smem = false;
-    TcPlan tc{};
 
     // device workspace
-    DevBuf d_desc, d_items, d_Gc, d_zc, d_Mc, d_gj, d_yy, d_G64, d_GM64, d_z64, d_w64, d_z32,
+    DevBuf d_desc, d_Gc, d_zc, d_Mc, d_gj, d_yy, d_G64, d_GM64, d_z64, d_w64, d_z32,
         d_w32, d_bt32, d_bt64, d_tc, d_states, d_best_states, d_f, d_best_f, d_accepts,
         d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp;
     HostBuf h_stage;
@@ -223,6 +243,223 @@ mcmc_status ensure_energies(mcmc_detector *d)
     return MCMC_OK;
 }
 
+// ---- shape classes, engine choice, autotuner --------------------------------------------
+using ClassKey = std::tuple<int, int, int, int, int, int, int>;   // N, L, Np, prec, pre, S, engine cfg
+std::map<ClassKey, Choice> g_tuned;                               // process-wide tuning results
+std::mutex g_tuned_mu;
+
+ClassKey class_key(const mcmc_detector *d, const ChannelDesc &c)
+{
+    return ClassKey{c.N, c.L, d->cfg.chains, d->cfg.precision, d->cfg.preconditioned,
+                    d->cfg.split_terms, d->cfg.engine & 3};
+}
+
+// SIMT launch shape for chains-per-item cg: whether the operand fits shared memory and the size.
+bool simt_fit(const mcmc_detector *d, int cg, int max_n, int max_nop, bool *bt_smem, size_t *smem)
+{
+    const int es = d->cfg.precision == MCMC_PREC_FP64 ? 8 : 4;
+    const size_t budget = std::min<size_t>(d->smem_optin, 110 * 1024);
+    for (int s = 0; s < 2; ++s) {
+        const bool bs = s == 0;
+        if (bs && (size_t)max_n * max_nop * es > budget / 2) continue;
+        const size_t need = chain_smem_bytes_simt(es, cg, max_n, max_nop, bs);
+        if (need <= budget) { *bt_smem = bs; *smem = need; return true; }
+    }
+    return false;
+}
+
+int simt_default_tile(const mcmc_detector *d, int max_n, int max_nop)
+{
+    for (int cg = std::min(64, (d->cfg.chains + 7) / 8 * 8); cg >= 8; cg -= 8) {
+        bool bs;
+        size_t sm;
+        if (simt_fit(d, cg, max_n, max_nop, &bs, &sm)) return cg;
+    }
+    return 0;
+}
+
+Choice default_choice(const mcmc_detector *d, const ChannelDesc &c)
+{
+    const int eng = d->cfg.engine & 3;
+    if (d->cfg.precision == MCMC_PREC_MIXED && c.N <= 128 && eng != MCMC_ENGINE_SIMT)
+        return Choice{MCMC_ENGINE_TC, 32};
+    return Choice{MCMC_ENGINE_SIMT, simt_default_tile(d, c.N, c.NOp)};
+}
+
+// Groups of channels with one engine and one launch shape; items cover every chain.
+mcmc_status build_groups(mcmc_detector *d)
+{
+    const int Np = d->cfg.chains;
+    std::map<std::tuple<int, int, int>, std::vector<int>> by;   // (engine, tile, N-class) -> channels
+    for (int b = 0; b < d->n_channels; ++b) {
+        const Choice ch = d->choice[b];
+        const ChannelDesc &c = d->desc[b];
+        const int cls = ch.engine == MCMC_ENGINE_TC ? (c.N + 15) / 16 * 16 : c.N;
+        by[{ch.engine, ch.tile, cls}].push_back(b);
+    }
+    for (auto &g : d->groups)
+        if (g.d_items.p) cudaFree(g.d_items.p);
+    d->groups.clear();
+    for (auto &kv : by) {
+        Group g;
+        g.engine = std::get<0>(kv.first);
+        g.tile = std::get<1>(kv.first);
+        for (int b : kv.second) {
+            g.max_n = std::max(g.max_n, d->desc[b].N);
+            g.max_nop = std::max(g.max_nop, d->desc[b].NOp);
+        }
+        if (g.engine == MCMC_ENGINE_TC) {
+            if (!tc_make_plan(g.max_n, g.tile, d->cfg.split_terms, d->smem_optin, &g.plan))
+                return fail(d, MCMC_EUNSUPPORTED, "no tensor-core plan for N = %d", g.max_n);
+        } else {
+            if (g.tile <= 0 || !simt_fit(d, g.tile, g.max_n, g.max_nop, &g.bt_smem, &g.smem))
+                return fail(d, MCMC_EUNSUPPORTED, "channels of N = %d do not fit the CUDA-core kernel", g.max_n);
+        }
+        for (int b : kv.second)
+            for (int c0 = 0; c0 < Np; c0 += g.tile)
+                g.items.push_back(WorkItem{b, c0, std::min(g.tile, Np - c0), 0});
+        CK(ensure(g.d_items, sizeof(WorkItem) * g.items.size()), "alloc items");
+        CK(cudaMemcpyAsync(g.d_items.p, g.items.data(), sizeof(WorkItem) * g.items.size(),
+                           cudaMemcpyHostToDevice, d->stream), "copy items");
+        d->groups.push_back(std::move(g));
+    }
+    return MCMC_OK;
+}
+
+ChainArgs chain_args(mcmc_detector *d, int32_t iterations, int64_t t_offset)
+{
+    const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
+    ChainArgs ca{};
+    ca.desc = P<ChannelDesc>(d->d_desc);
+    ca.chains = d->cfg.chains;
+    ca.iterations = iterations;
+    ca.t_offset = t_offset;
+    ca.refresh_period = d->cfg.refresh_period;
+    ca.key0 = (uint32_t)(d->cfg.seed & 0xFFFFFFFFu);
+    ca.key1 = (uint32_t)(d->cfg.seed >> 32);
+    ca.bt = fp64 ? (const void *)P<double>(d->d_bt64) : (const void *)P<float>(d->d_bt32);
+    ca.z = fp64 ? (const void *)P<double>(d->d_z64) : (const void *)P<float>(d->d_z32);
+    ca.w = fp64 ? (const void *)P<double>(d->d_w64) : (const void *)P<float>(d->d_w32);
+    ca.G64 = P<double>(d->d_G64);
+    ca.z64 = P<double>(d->d_z64);
+    ca.yy = P<double>(d->d_yy);
+    ca.states = P<int8_t>(d->d_states);
+    ca.best_states = P<int8_t>(d->d_best_states);
+    ca.f = P<double>(d->d_f);
+    ca.best_f = P<double>(d->d_best_f);
+    ca.accepts = P<unsigned long long>(d->d_accepts);
+    ca.drift_bits = drift_ptr(d);
+    ca.status = status_ptr(d);
+    ca.tc_ops = P<uint8_t>(d->d_tc);
+    ca.split_terms = d->cfg.split_terms;
+    ca.init_f = d->f_valid ? 0 : 1;
+    ca.dexp = fp64 ? nullptr : P<float>(d->d_dexp);
+    return ca;
+}
+
+cudaError_t launch_group(mcmc_detector *d, const Group &g, ChainArgs ca)
+{
+    const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
+    ca.items = static_cast<const WorkItem *>(g.d_items.p);
+    ca.n_items = (int)g.items.size();
+    ca.cg = g.tile;
+    ca.max_n = g.max_n;
+    ca.max_nop = g.max_nop;
+    ca.bt_in_smem = g.bt_smem;
+    if (g.engine == MCMC_ENGINE_TC) return tc_launch_chains(ca, g.plan, d->stream);
+    return launch_chains_simt(ca, fp64, g.smem, d->stream);
+}
+
+// Autotuner: for every shape class not seen before (in this process, for this configuration),
+// time each candidate launch shape on a sample of the class's channels and keep the fastest.
+// Probe runs overwrite chain state; the caller redraws the initial states afterwards.
+mcmc_status autotune(mcmc_detector *d, bool *probed)
+{
+    *probed = false;
+    const int prec = d->cfg.precision;
+    if (prec == MCMC_PREC_FP64 || (d->cfg.engine & 3) != MCMC_ENGINE_AUTO) return MCMC_OK;
+    std::map<ClassKey, std::vector<int>> classes;
+    for (int b = 0; b < d->n_channels; ++b) classes[class_key(d, d->desc[b])].push_back(b);
+    std::vector<Choice> saved = d->choice;
+    for (auto &kv : classes) {
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            auto it = g_tuned.find(kv.first);
+            if (it != g_tuned.end()) {
+                for (int b : kv.second) saved[b] = it->second;
+                continue;
+            }
+        }
+        const ChannelDesc &c0 = d->desc[kv.second[0]];
+        std::vector<Choice> cands;
+        if (prec == MCMC_PREC_MIXED && c0.N <= 128) {
+            cands.push_back(Choice{MCMC_ENGINE_TC, 32});
+            cands.push_back(Choice{MCMC_ENGINE_TC, 16});
+        }
+        for (int cg : {64, 32, 16}) {
+            bool bs;
+            size_t sm;
+            if (cg <= (d->cfg.chains + 7) / 8 * 8 && simt_fit(d, cg, c0.N, c0.NOp, &bs, &sm))
+                cands.push_back(Choice{MCMC_ENGINE_SIMT, cg});
+        }
+        // probe sample: enough channels to fill the GPU twice, at most the class
+        const int want = std::max(1, 4 * d->sm_count * 32 / std::max(1, d->cfg.chains));
+        std::vector<int> sample(kv.second.begin(),
+                                kv.second.begin() + std::min<size_t>(kv.second.size(), (size_t)want));
+        Choice best = cands.empty() ? default_choice(d, c0) : cands[0];
+        float best_ms = 1e30f;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        for (const Choice &cand : cands) {
+            Group g;   // the sample channels only
+            g.engine = cand.engine;
+            g.tile = cand.tile;
+            g.max_n = c0.N;
+            g.max_nop = c0.NOp;
+            bool ok = cand.engine == MCMC_ENGINE_TC
+                          ? tc_make_plan(g.max_n, g.tile, d->cfg.split_terms, d->smem_optin, &g.plan)
+                          : simt_fit(d, g.tile, g.max_n, g.max_nop, &g.bt_smem, &g.smem);
+            if (!ok) continue;
+            for (int b : sample)
+                for (int cc = 0; cc < d->cfg.chains; cc += g.tile)
+                    g.items.push_back(WorkItem{b, cc, std::min(g.tile, d->cfg.chains - cc), 0});
+            CK(ensure(g.d_items, sizeof(WorkItem) * g.items.size()), "alloc probe items");
+            CK(cudaMemcpyAsync(g.d_items.p, g.items.data(), sizeof(WorkItem) * g.items.size(),
+                               cudaMemcpyHostToDevice, d->stream), "copy probe items");
+            ChainArgs ca = chain_args(d, 2, 0);
+            ca.init_f = 1;
+            cudaError_t e = launch_group(d, g, ca);                 // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
+            ca.iterations = 8;
+            if (e == cudaSuccess) e = launch_group(d, g, ca);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, d->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            cudaFree(g.d_items.p);
+            d->launches += 2;
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(d, e, "autotuner probe");
+            }
+            if (ms < best_ms) { best_ms = ms; best = cand; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            g_tuned[kv.first] = best;
+        }
+        for (int b : kv.second) saved[b] = best;
+        *probed = true;
+        d->tuned_classes++;
+    }
+    d->choice = saved;
+    return MCMC_OK;
+}
+
 }  // namespace
 
 // ==========================================================================================
@@ -280,11 +517,11 @@ mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out)
         cfg->max_nr > 4096 || cfg->chains < 4 || cfg->chains > 1024 || (cfg->chains % 4) != 0 ||
         cfg->precision < MCMC_PREC_FP64 || cfg->precision > MCMC_PREC_MIXED ||
         (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < 0 ||
-        cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 || cfg->engine > 2 ||
+        cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 ||
+        (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH)) != 0 || (cfg->engine & 3) == 3 ||
         cfg->reserved != 0)
         return MCMC_EINVAL;
-    if (cfg->precision == MCMC_PREC_MIXED && cfg->engine == MCMC_ENGINE_SIMT) return MCMC_EINVAL;
-    if (cfg->precision != MCMC_PREC_MIXED && cfg->engine == MCMC_ENGINE_TC) return MCMC_EINVAL;
+    if (cfg->precision != MCMC_PREC_MIXED && (cfg->engine & 3) == MCMC_ENGINE_TC) return MCMC_EINVAL;
     mcmc_detector *d = new (std::nothrow) mcmc_detector();
     if (!d) return MCMC_ENOMEM;
     d->cfg = *cfg;
@@ -324,13 +561,16 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
 {
     if (!d) return MCMC_OK;
     if (d->stream) cudaStreamSynchronize(d->stream);
-    DevBuf *bufs[] = {&d->d_desc, &d->d_items, &d->d_Gc, &d->d_zc, &d->d_Mc, &d->d_gj, &d->d_yy,
+    DevBuf *bufs[] = {&d->d_desc, &d->d_Gc, &d->d_zc, &d->d_Mc, &d->d_gj, &d->d_yy,
                       &d->d_G64, &d->d_GM64, &d->d_z64, &d->d_w64, &d->d_z32, &d->d_w32,
                       &d->d_bt32, &d->d_bt64, &d->d_tc, &d->d_states, &d->d_best_states, &d->d_f,
                       &d->d_best_f, &d->d_accepts, &d->d_misc, &d->d_in_H, &d->d_in_y,
                       &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf, &d->d_dexp};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
+    for (auto &g : d->groups)
+        if (g.d_items.p) cudaFree(g.d_items.p);
+    if (d->graph) cudaGraphExecDestroy(d->graph);
     if (d->h_stage.p) cudaFreeHost(d->h_stage.p);
     if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
     cudaGetLastError();
@@ -407,46 +647,34 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     d->tot_bits = bits;
     d->tot_ant = ant;
 
-    // chain-kernel plan
+    // chain-kernel plan: one engine / launch shape per channel (tuned or default)
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
     const bool mixed = d->cfg.precision == MCMC_PREC_MIXED;
-    const int es = fp64 ? 8 : 4;
-    d->items.clear();
+    d->choice.assign(n_channels, Choice{});
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        for (int b = 0; b < n_channels; ++b) {
+            auto it = g_tuned.find(class_key(d, d->desc[b]));
+            d->choice[b] = (it != g_tuned.end() && (d->cfg.engine & 3) == MCMC_ENGINE_AUTO)
+                               ? it->second
+                               : default_choice(d, d->desc[b]);
+        }
+    }
+    long long tot_tc = 0;
     if (mixed) {
-        if (!tc_make_plan(d->desc, Np, d->cfg.split_terms, d->smem_optin, d->sm_count, &d->tc))
-            return fail(d, MCMC_EUNSUPPORTED, "no tensor-core plan for this batch (N up to %d)", maxn);
-        d->tot_tc = 0;
         for (auto &c : d->desc) {
-            c.tc_off = d->tot_tc;
-            d->tot_tc += tc_operand_bytes(c, d->tc);
+            c.tc_off = tot_tc;
+            tot_tc += tc_operand_bytes(c.N, d->cfg.split_terms);
         }
-        for (int b = 0; b < n_channels; ++b)
-            for (int c0 = 0; c0 < Np; c0 += d->tc.chains_per_cta)
-                d->items.push_back(WorkItem{b, c0, std::min(d->tc.chains_per_cta, Np - c0), 0});
-    } else {
-        const size_t budget = std::min<size_t>(d->smem_optin, 110 * 1024);
-        bool bt_smem = true;
-        int cg = std::min(64, (Np + 7) / 8 * 8);
-        for (;;) {
-            size_t need = chain_smem_bytes_simt(es, cg, maxn, maxnop, bt_smem);
-            if (need <= budget) break;
-            if (bt_smem && (size_t)maxn * maxnop * es > budget / 2) { bt_smem = false; continue; }
-            if (cg > 8) { cg -= 8; continue; }
-            if (bt_smem) { bt_smem = false; continue; }
-            return fail(d, MCMC_EUNSUPPORTED, "batch does not fit the CUDA-core kernel");
-        }
-        d->cg = cg;
-        d->bt_in_smem = bt_smem;
-        d->chain_smem = chain_smem_bytes_simt(es, cg, maxn, maxnop, bt_smem);
-        for (int b = 0; b < n_channels; ++b)
-            for (int c0 = 0; c0 < Np; c0 += cg)
-                d->items.push_back(WorkItem{b, c0, std::min(cg, Np - c0), 0});
+    }
+    if (d->graph) {
+        cudaGraphExecDestroy(d->graph);
+        d->graph = nullptr;
     }
 
     // workspace
     const long long ntc = mat / 4;   // complex Nt^2 elements over the batch
     CK(ensure(d->d_desc, sizeof(ChannelDesc) * n_channels), "alloc desc");
-    CK(ensure(d->d_items, sizeof(WorkItem) * d->items.size()), "alloc items");
     CK(ensure(d->d_Gc, 16 * ntc), "alloc Gc");
     CK(ensure(d->d_zc, 8 * vec), "alloc zc");
     CK(ensure(d->d_yy, 8 * n_channels), "alloc yy");
@@ -464,7 +692,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     if (pre && !stage_gj) CK(ensure(d->d_gj, 16 * 2 * ntc), "alloc gj");
     if (fp64) CK(ensure(d->d_bt64, 8 * bt), "alloc bt64");
     else CK(ensure(d->d_bt32, 4 * bt), "alloc bt32");   // FP32 chains; FP32 read-out of every non-FP64 mode
-    if (mixed) CK(ensure(d->d_tc, (size_t)d->tot_tc), "alloc tc operands");
+    if (mixed) CK(ensure(d->d_tc, (size_t)tot_tc), "alloc tc operands");
     CK(ensure(d->d_states, st), "alloc states");
     CK(ensure(d->d_best_states, st), "alloc best states");
     CK(ensure(d->d_f, 8 * (size_t)n_channels * Np), "alloc f");
@@ -495,8 +723,6 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     }
     CK(cudaMemcpyAsync(d->d_desc.p, d->desc.data(), sizeof(ChannelDesc) * n_channels,
                        cudaMemcpyHostToDevice, d->stream), "copy desc");
-    CK(cudaMemcpyAsync(d->d_items.p, d->items.data(), sizeof(WorkItem) * d->items.size(),
-                       cudaMemcpyHostToDevice, d->stream), "copy items");
     CK(cudaMemsetAsync(d->d_misc.p, 0, 256, d->stream), "reset status");
     CK(cudaMemsetAsync(d->d_accepts.p, 0, 8 * (size_t)n_channels * Np, d->stream), "reset accepts");
     finalize_desc_kernel<<<(n_channels + 127) / 128, 128, 0, d->stream>>>(
@@ -530,8 +756,8 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
        "prep kernels");
     d->launches += pre ? 3 : 2;
     if (mixed) {
-        CK(tc_launch_pack(d->tc, P<ChannelDesc>(d->d_desc), n_channels, P<float>(d->d_bt32),
-                          P<uint8_t>(d->d_tc), d->stream), "pack operands");
+        CK(tc_launch_pack(d->cfg.split_terms, P<ChannelDesc>(d->d_desc), n_channels,
+                          P<float>(d->d_bt32), P<uint8_t>(d->d_tc), d->stream), "pack operands");
         d->launches++;
     }
 
@@ -545,6 +771,23 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     ia.key1 = (uint32_t)(d->cfg.seed >> 32);
     CK(launch_init_states(ia, d->stream), "init states");
     d->launches++;
+
+    // autotune unseen shape classes on this batch, then redraw the states the probes touched
+    d->f_valid = fp64;
+    {
+        bool probed = false;
+        mcmc_status ts = autotune(d, &probed);
+        if (ts != MCMC_OK) return ts;
+        if (probed) {
+            CK(launch_init_states(ia, d->stream), "init states");
+            CK(cudaMemsetAsync(d->d_accepts.p, 0, 8 * (size_t)n_channels * Np, d->stream), "reset accepts");
+            d->launches++;
+        }
+    }
+    {
+        mcmc_status gs = build_groups(d);
+        if (gs != MCMC_OK) return gs;
+    }
 
     RefreshArgs ra{};
     ra.desc = P<ChannelDesc>(d->d_desc);
@@ -580,46 +823,40 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         return fail(d, MCMC_EINVAL, "iterations/t_offset out of range");
     if (iterations == 0) return MCMC_OK;
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
-    const bool mixed = d->cfg.precision == MCMC_PREC_MIXED;
-    ChainArgs ca{};
-    ca.desc = P<ChannelDesc>(d->d_desc);
-    ca.items = P<WorkItem>(d->d_items);
-    ca.n_items = (int)d->items.size();
-    ca.chains = d->cfg.chains;
-    ca.cg = d->cg;
-    ca.max_n = d->max_n;
-    ca.max_nop = d->max_nop;
-    ca.bt_in_smem = d->bt_in_smem;
-    ca.iterations = iterations;
-    ca.t_offset = t_offset;
-    ca.refresh_period = d->cfg.refresh_period;
-    ca.key0 = (uint32_t)(d->cfg.seed & 0xFFFFFFFFu);
-    ca.key1 = (uint32_t)(d->cfg.seed >> 32);
-    ca.bt = fp64 ? (const void *)P<double>(d->d_bt64) : (const void *)P<float>(d->d_bt32);
-    ca.z = fp64 ? (const void *)P<double>(d->d_z64) : (const void *)P<float>(d->d_z32);
-    ca.w = fp64 ? (const void *)P<double>(d->d_w64) : (const void *)P<float>(d->d_w32);
-    ca.G64 = P<double>(d->d_G64);
-    ca.z64 = P<double>(d->d_z64);
-    ca.yy = P<double>(d->d_yy);
-    ca.states = P<int8_t>(d->d_states);
-    ca.best_states = P<int8_t>(d->d_best_states);
-    ca.f = P<double>(d->d_f);
-    ca.best_f = P<double>(d->d_best_f);
-    ca.accepts = P<unsigned long long>(d->d_accepts);
-    ca.drift_bits = drift_ptr(d);
-    ca.status = status_ptr(d);
-    ca.tc_ops = P<uint8_t>(d->d_tc);
-    ca.split_terms = d->cfg.split_terms;
-    ca.init_f = d->f_valid ? 0 : 1;
-    ca.dexp = fp64 ? nullptr : P<float>(d->d_dexp);
-    if (mixed) {
-        ca.z = P<float>(d->d_z32);
-        ca.w = P<float>(d->d_w32);
-        CK(tc_launch_chains(ca, d->tc, d->stream), "tensor-core chain kernel");
+    const ChainArgs ca = chain_args(d, iterations, t_offset);
+    if (d->cfg.engine & MCMC_ENGINE_GRAPH) {
+        // every group's launch captured into one graph, replayed on the handle's stream
+        CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t le = cudaSuccess;
+        for (const Group &g : d->groups)
+            if (le == cudaSuccess) le = launch_group(d, g, ca);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(d->stream, &graph);
+        if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(d, le, "chain kernel"); }
+        CK(ce, "end capture");
+        bool updated = false;
+        if (d->graph) {
+            cudaGraphExecUpdateResultInfo info{};
+            updated = cudaGraphExecUpdate(d->graph, graph, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(d->graph);
+                d->graph = nullptr;
+            }
+        }
+        if (!updated) {
+            const cudaError_t ie = cudaGraphInstantiate(&d->graph, graph, 0);
+            if (ie != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(d, ie, "instantiate graph"); }
+        }
+        cudaGraphDestroy(graph);
+        CK(cudaGraphLaunch(d->graph, d->stream), "graph launch");
+        d->launches += (long long)d->groups.size();
     } else {
-        CK(launch_chains_simt(ca, fp64, d->chain_smem, d->stream), "chain kernel");
+        for (const Group &g : d->groups) {
+            CK(launch_group(d, g, ca), g.engine == MCMC_ENGINE_TC ? "tensor-core chain kernel" : "chain kernel");
+            d->launches++;
+        }
     }
-    d->launches++;
     d->f_valid = true;
     d->d_valid = !fp64;
     d->transitions += (long long)iterations * d->n_channels * d->cfg.chains;

@@ -49,7 +49,7 @@ __host__ __device__ inline Layout make_layout(int es, int cg, int N, int NOp, bo
     L.a = take((size_t)cg * N * es);
     L.D = take((size_t)cg * N * es);
     L.Dp = take((size_t)cg * NOp * es);
-    L.xsT = take((size_t)N * cg * es);
+    L.xsT = take((size_t)N * (cg + 4) * es);   // row stride cg + 4: conflict-light column writes
     L.term = take((size_t)cg * N * es);
     L.dterm = take((size_t)cg * N * es);
     L.fcur = take((size_t)cg * 8);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void store_row(T *p, const T (&v)[CNT])
 
 // D'[c][o] = sum_m bt[m][o] xsT[m][c] for the active chains; register tile TCH x TO.
 template <typename T, int TCH, int TO>
-__device__ __forceinline__ void gemm(const T *__restrict__ bt, int NOp, const T *xsT, int cg, int N,
+__device__ __forceinline__ void gemm(const T *__restrict__ bt, int NOp, const T *xsT, int xld, int N,
                                      T *Dp, int nC)
 {
     const int nOT = NOp / TO, nCT = (nC + TCH - 1) / TCH;
@@ -111,7 +111,7 @@ __device__ __forceinline__ void gemm(const T *__restrict__ bt, int NOp, const T 
 #pragma unroll 2
         for (int m = 0; m < N; ++m) {
             T xv[TCH], bv[TO];
-            load_row<T, TCH>(xsT + (size_t)m * cg + c0, xv);
+            load_row<T, TCH>(xsT + (size_t)m * xld + c0, xv);
             load_row<T, TO>(bt + (size_t)m * NOp + o0, bv);
 #pragma unroll
             for (int i = 0; i < TCH; ++i)
@@ -200,6 +200,7 @@ template <typename T, int TCH, int TO, int L>
 __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelDesc &d)
 {
     const int N = d.N, NOp = d.NOp, cg = A.cg, nC = it.nc;
+    const int xld = cg + 4;                        // row stride of xsT
     const bool pre = d.NO > N;
     const T unit = sizeof(T) == 8 ? T(1) : (T)kLog2e;
     const T clin = (T)d.clin * unit, cq = (T)d.cquad * unit, cf = (T)d.cf * unit;
@@ -239,7 +240,7 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
         const int8_t kv = A.states[sbase + e];
         sk[c * N + n] = kv;
         skb[c * N + n] = A.best_states[sbase + e];
-        xsT[n * cg + c] = (T)odd_of(kv, L);
+        xsT[n * xld + c] = (T)odd_of(kv, L);
     }
     for (int c = threadIdx.x; c < cg; c += blockDim.x) {
         const long long ci = (long long)it.b * A.chains + it.c0 + c;
@@ -249,7 +250,7 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
     }
     __syncthreads();
     // Gt x and the drift slope of the current states
-    gemm<T, TCH, TO>(bt, NOp, xsT, cg, N, Dp, nC);
+    gemm<T, TCH, TO>(bt, NOp, xsT, xld, N, Dp, nC);
     __syncthreads();
     for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {
         const int c = e / N, n = e % N;
@@ -300,12 +301,12 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
                 const int sel = draw_level<T, L>(sa[e], cq, inv2c, kn, word_of(w, j), lq);
                 skp[e] = (int8_t)sel;
                 term[e] = -lq;
-                xsT[n * cg + c] = (T)odd_of(sel, L);
+                xsT[n * xld + c] = (T)odd_of(sel, L);
             }
         }
         __syncthreads();
         // 2. D' = X' [Gt | P~ Gt]
-        gemm<T, TCH, TO>(bt, NOp, xsT, cg, N, Dp, nC);
+        gemm<T, TCH, TO>(bt, NOp, xsT, xld, N, Dp, nC);
         __syncthreads();
         // 3. reverse factor and energy difference per (chain, n)
         for (int e = threadIdx.x; e < nC * N; e += blockDim.x) {

@@ -593,11 +593,12 @@ __global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const Cha
 // Operand packing: [Gt | P~Gt] (FP32) -> `S` BF16 split terms in the core-matrix image. One
 // thread builds one 16-byte core-matrix row (8 consecutive K values of one A row) per term.
 // ------------------------------------------------------------------------------------------
-__global__ void pack_kernel(const ChannelDesc *desc, const float *bt32, uint8_t *ops, int S,
-                            int MT, int Kp)
+__global__ void pack_kernel(const ChannelDesc *desc, const float *bt32, uint8_t *ops, int S)
 {
     const ChannelDesc d = desc[blockIdx.x];
     const int N = d.N;
+    if (N > 128) return;
+    const int MT = (N + 63) / 64, Kp = (N + 15) / 16 * 16;
     const bool pre = d.NO > N;
     const float *bt = bt32 + d.bt_off;
     uint8_t *base = ops + d.tc_off;
@@ -642,53 +643,45 @@ int pow2_at_least(int v)
 
 }  // namespace
 
-bool tc_make_plan(const std::vector<ChannelDesc> &desc, int chains, int split_terms,
-                  size_t smem_optin, int sm_count, TcPlan *plan)
+bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, TcPlan *plan)
 {
     *plan = TcPlan{};
-    int maxn = 0;
-    for (const auto &c : desc) maxn = std::max(maxn, c.N);
-    if (maxn < 1 || maxn > 128) return false;
-    const int MT = (maxn + 63) / 64;
-    const int Kp = (maxn + 15) / 16 * 16;
-    // 32 chains per CTA: 256 threads at <= 128 registers, two CTAs per SM overlap one CTA's
-    // tensor-core wait with the other's proposal arithmetic
-    int C = std::min(32, (chains + 15) / 16 * 16);
+    if (max_n < 1 || max_n > 128) return false;
+    if (chains_per_cta < 16 || chains_per_cta > 32 || chains_per_cta % 16) return false;
+    const int MT = (max_n + 63) / 64;
+    const int Kp = (max_n + 15) / 16 * 16;
+    const int C = chains_per_cta;
     const int S = split_terms;
-    TcLayout L = tc_layout(S, MT, Kp, C);
-    while (L.total > smem_optin && C > 16) {
-        C -= 16;
-        L = tc_layout(S, MT, Kp, C);
-    }
+    const TcLayout L = tc_layout(S, MT, Kp, C);
     if (L.total > smem_optin) return false;
     plan->valid = 1;
     plan->chains_per_cta = C;
     plan->m_tiles = MT;
     plan->kdim = Kp;
-    plan->max_n = maxn;
+    plan->max_n = max_n;
     plan->split_terms = S;
     plan->threads = 16 * C;                   // 4 TMEM quadrants x C/8 column groups x 32
     plan->tmem_cols = pow2_at_least(MT * C);
     const int by_smem = (int)(228 * 1024 / (L.total + 1024));
-    const int by_thr = std::min(2048 / plan->threads, TC_MIN_BLOCKS);
+    const int by_thr = std::min(2048 / plan->threads, TC_MIN_BLOCKS * 512 / plan->threads);
     const int by_tmem = 512 / plan->tmem_cols;
     plan->ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_thr), by_tmem));
     plan->smem = L.total;
-    (void)sm_count;
     return true;
 }
 
-long long tc_operand_bytes(const ChannelDesc &, const TcPlan &plan)
+long long tc_operand_bytes(int N, int split_terms)
 {
-    return (long long)plan.split_terms * plan.m_tiles * 128 * plan.kdim * 2;
+    if (N > 128) return 0;
+    const int MT = (N + 63) / 64, Kp = (N + 15) / 16 * 16;
+    return (long long)split_terms * MT * 128 * Kp * 2;
 }
 
-cudaError_t tc_launch_pack(const TcPlan &plan, const ChannelDesc *desc, int n_channels,
+cudaError_t tc_launch_pack(int split_terms, const ChannelDesc *desc, int n_channels,
                            const float *bt32, uint8_t *tc_ops, cudaStream_t s)
 {
     if (n_channels <= 0) return cudaSuccess;
-    pack_kernel<<<n_channels, 256, 0, s>>>(desc, bt32, tc_ops, plan.split_terms, plan.m_tiles,
-                                           plan.kdim);
+    pack_kernel<<<n_channels, 256, 0, s>>>(desc, bt32, tc_ops, split_terms);
     return cudaGetLastError();
 }
 

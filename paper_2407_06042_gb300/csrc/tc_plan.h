@@ -21,16 +21,17 @@ struct TcPlan {
     size_t smem;            // dynamic shared memory per CTA (bytes)
 };
 
-// Chooses the kernel shape for a batch; false if the batch cannot run on this engine.
-bool tc_make_plan(const std::vector<ChannelDesc> &desc, int chains, int split_terms,
-                  size_t smem_optin, int sm_count, TcPlan *plan);
+// Kernel shape for a group of channels with the same K extent (N rounded up to 16) and tile
+// count, `chains_per_cta` chains (multiple of 16) per CTA; false if it does not fit.
+bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, TcPlan *plan);
 
-// Bytes of one channel's packed BF16 operand block.
-long long tc_operand_bytes(const ChannelDesc &c, const TcPlan &plan);
+// Bytes of one channel's packed BF16 operand block (depends on its N only).
+long long tc_operand_bytes(int N, int split_terms);
 
 // Packs [Gt | P~Gt] (the FP32 CUDA-core operand, N x NOp per channel) into the BF16 split
-// operand blocks in the canonical tcgen05 layout.
-cudaError_t tc_launch_pack(const TcPlan &plan, const ChannelDesc *desc, int n_channels,
+// operand block of every channel with N <= 128, in the canonical tcgen05 layout (each block
+// sized for the channel's own K extent and tile count).
+cudaError_t tc_launch_pack(int split_terms, const ChannelDesc *desc, int n_channels,
                            const float *bt32, uint8_t *tc_ops, cudaStream_t s);
 
 cudaError_t tc_launch_chains(const ChainArgs &a, const TcPlan &plan, cudaStream_t s);

@@ -15,6 +15,9 @@ from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
+TC = 2            # MCMC_ENGINE_TC: these tests pin the tensor-core kernel itself
+GRAPH = 4         # MCMC_ENGINE_GRAPH
+
 
 def _small(n=16, snr=12.0, seed=1001):
     return workload.rayleigh_batch(4, 4, 16, [snr], n, seed)
@@ -23,7 +26,7 @@ def _small(n=16, snr=12.0, seed=1001):
 @pytest.mark.parametrize("terms,w_cat,w_acc", [(3, 2e-4, 2e-3), (2, 6.4e-3, 6.4e-2)])
 def test_mixed_step_parity(terms, w_cat, w_acc):
     b = _small(16)
-    det = H.make_detector(b, chains=32, precision="mixed", split_terms=terms, seed=0)
+    det = H.make_detector(b, chains=32, precision="mixed", split_terms=terms, seed=0, engine=TC)
     r = H.step_parity(det, b, H.targets(b), seed=0, steps=25, w_cat=w_cat, w_acc=w_acc)
     assert r["bad"] == 0, r
     assert r["mism"] <= max(4, r["steps"] // 1000), r
@@ -32,10 +35,10 @@ def test_mixed_step_parity(terms, w_cat, w_acc):
 
 def test_mixed_one_launch_equals_single_step_launches():
     b = _small(6)
-    d1 = H.make_detector(b, chains=32, precision="mixed")
+    d1 = H.make_detector(b, chains=32, precision="mixed", engine=TC)
     d1.run_chains(20)
     s1, _ = d1.get_chains()
-    d2 = H.make_detector(b, chains=32, precision="mixed")
+    d2 = H.make_detector(b, chains=32, precision="mixed", engine=TC)
     for t in range(20):
         d2.run_chains(1, t)
     s2, _ = d2.get_chains()
@@ -51,7 +54,7 @@ def test_mixed_one_launch_equals_single_step_launches():
 ])
 def test_mixed_step_parity_shapes(shapes):
     b = workload.generate(shapes, 91)
-    det = H.make_detector(b, chains=36, precision="mixed", split_terms=3, seed=2)
+    det = H.make_detector(b, chains=36, precision="mixed", split_terms=3, seed=2, engine=TC)
     r = H.step_parity(det, b, H.targets(b), seed=2, steps=6, w_cat=2e-4, w_acc=2e-3)
     assert r["bad"] == 0, r
     assert r["mism"] <= max(4, r["steps"] // 500), r
@@ -63,7 +66,7 @@ def test_mixed_ber_within_binomial_interval_of_oracle():
     sign(LLR) lies inside the 95% Clopper-Pearson interval of the oracle's."""
     from scipy.stats import beta
     b = workload.workload("rayleigh_4x4_16qam")
-    det = H.make_detector(b, chains=32, precision="mixed", seed=0)
+    det = H.make_detector(b, chains=32, precision="mixed", seed=0, engine=TC)
     det.run_chains(100)
     out = det.estimate()
     det.destroy()
@@ -81,7 +84,7 @@ def test_mixed_energies_refresh():
     """FP64 refresh every R transitions: the tracked energies equal FP64 evaluations of the
     states right after a refresh point, and the reported drift is small."""
     b = _small(4, snr=20.0)
-    det = H.make_detector(b, chains=32, precision="mixed", refresh_period=10)
+    det = H.make_detector(b, chains=32, precision="mixed", refresh_period=10, engine=TC)
     det.run_chains(30)
     out = det.estimate(stats=True)
     flat, f = det.get_chains()
@@ -93,3 +96,26 @@ def test_mixed_energies_refresh():
             assert abs(f[ch * 32 + c] - fx) <= 1e-9 * abs(fx)
     assert out["stats"]["refresh_drift"] < 1e-2
     det.destroy()
+
+
+def test_uneven_batch_autotuned_and_graph_replay():
+    """Uneven batch (Nt in {2..16}, Nr in {Nt, 2Nt}, QPSK..64-QAM): the autotuned engines keep
+    oracle parity, and replaying the launches from a captured CUDA graph gives bit-identical
+    chains."""
+    b = workload.uneven_batch(40, 1003, nts=(2, 4, 8, 16), snr_range=(8.0, 20.0))
+    det = H.make_detector(b, chains=32, precision="mixed", split_terms=3, seed=4)
+    r = H.step_parity(det, b, H.targets(b), seed=4, steps=5, w_cat=2e-4, w_acc=2e-3)
+    assert r["bad"] == 0, r
+    det.destroy()
+    d1 = H.make_detector(b, chains=32, precision="mixed", seed=4)
+    d1.run_chains(15)
+    d1.run_chains(10, 15)
+    o1 = d1.estimate()
+    d2 = H.make_detector(b, chains=32, precision="mixed", seed=4, engine=GRAPH)
+    d2.run_chains(15)
+    d2.run_chains(10, 15)
+    o2 = d2.estimate()
+    np.testing.assert_array_equal(d1.get_chains()[0], d2.get_chains()[0])
+    np.testing.assert_array_equal(o1["llr"], o2["llr"])
+    d1.destroy()
+    d2.destroy()
