@@ -26,7 +26,7 @@ if ROOT not in sys.path:
 
 import workload  # noqa: E402
 
-WORKLOAD = "rayleigh_32x32_64qam"
+WORKLOAD = "rayleigh_32x32_64qam"   # the headline configuration (fits one GPU)
 METRIC = "chain-iterations/s and detections/s at BER<=1e-3 vs plain FP32, 1 GB300"
 UNIT = "chain-iterations/s"
 
@@ -139,31 +139,38 @@ def profiled_traffic(precision):
     return traffic
 
 
-def chain_roofline(precision, w, units, chain_ms):
+def chain_roofline(precision, w, units, chain_ms, batch=None):
     """Roofline of the chain loop (the dominant kernel). Its binding resource is the proposal
     arithmetic: per chain-iteration the method evaluates, for every real dimension, two
     categorical factors of L weights (one exponential each) and their two log-normalisers, plus
     one log per MH test. Those transcendental operations run on the MUFU pipe, whose measured
     ex2 rate is the peak. The Gram products (tensor pipe, MIXED) are reported beside it."""
-    N = 2 * w["nt"]
-    L = int(np.sqrt(w["qam"]))
-    per_ci = N * (2 * L + 2) + 1
+    if batch is not None and len(set(batch.nt.tolist())) > 1:
+        Ns = 2 * batch.nt.astype(np.float64)
+        Ls = np.sqrt(batch.qam.astype(np.float64))
+        N, L = float(Ns.mean()), float(Ls.mean())
+        per_ci = float((Ns * (2 * Ls + 2) + 1).mean())
+        gemm = float((2 * Ns * 2 * Ns).mean())
+    else:
+        N = 2 * w["nt"]
+        L = int(np.sqrt(w["qam"]))
+        per_ci = N * (2 * L + 2) + 1
+        gemm = 2 * N * (2 * N)
     peaks = pipe_peaks() or {}
     t = chain_ms * 1e-3
     achieved = per_ci * units / t
     peak = peaks.get("ex2")
-    gemm = 2 * N * (2 * N)
     out = {"bound": "alu", "achieved": achieved / 1e9,
            "peak": (peak / 1e9) if peak else None, "unit": "Gop/s",
            "frac": (achieved / peak) if peak else None,
            "traffic": profiled_traffic(precision),
            "pipe": "MUFU transcendental (ex2/lg2), measured ex2 rate of this GPU",
-           "per_unit": f"{per_ci} transcendental ops per chain-iteration (N(2L+2)+1, N={N}, L={L})",
+           "per_unit": f"{per_ci:g} transcendental ops per chain-iteration (N(2L+2)+1, N={N:g}, L={L:g})",
            "launch_ms": chain_ms, "peaks_measured": peaks}
     if precision == "mixed":
         tf = gemm * units / t / 1e12
         out["tensor"] = {"achieved_tflops": tf, "peak_tflops": 1899.4, "frac": tf / 1899.4,
-                         "per_unit": f"{gemm} Gram flops per chain-iteration (D' = X'[Gt|PGt])"}
+                         "per_unit": f"{gemm:g} Gram flops per chain-iteration (D' = X'[Gt|PGt])"}
     else:
         fma = peaks.get("fma")
         gf = gemm * units / t
@@ -173,10 +180,22 @@ def chain_roofline(precision, w, units, chain_ms):
     return out
 
 
-def load_batch(scale: float, rank: int):
-    w = dict(workload.WORKLOADS[WORKLOAD])
-    n = max(1, int(round(w["per_snr"] * scale)))
-    return workload.rayleigh_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["seed"] + 7 * rank), w
+def load_batch(scale: float, rank: int, name: str = WORKLOAD):
+    w = dict(workload.WORKLOADS[name])
+    w["seed"] = w["seed"] + 7 * rank
+    if w["kind"] == "rayleigh":
+        n = max(1, int(round(w["per_snr"] * scale)))
+        b = workload.rayleigh_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["seed"])
+    elif w["kind"] == "kronecker":
+        n = max(1, int(round(w["total"] * scale)))
+        b = workload.kronecker_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["rho"], w["seed"])
+    else:
+        n = max(1, int(round(w["count"] * scale)))
+        b = workload.uneven_batch(n, w["seed"])
+    w.setdefault("nt", int(b.nt.max()))
+    w.setdefault("nr", int(b.nr.max()))
+    w.setdefault("qam", int(b.qam.max()))
+    return b, w
 
 
 def ber_of(batch, llr, best_idx):
@@ -184,16 +203,21 @@ def ber_of(batch, llr, best_idx):
     bits = batch.tx_bits.astype(np.int64)
     hard = (llr < 0).astype(np.int64)
     errs_soft = hard != bits
-    # hard decision bits from the complex Gray labels
-    B2 = int(np.log2(batch.qam[0]))
-    lab = best_idx.astype(np.int64) & ((1 << B2) - 1)
-    hb = ((lab[:, None] >> np.arange(B2 - 1, -1, -1)) & 1).reshape(-1)
-    errs_hard = hb != bits
+    # hard decision bits from the complex Gray labels (per channel: log2 Qc bits per antenna)
+    hbs, a0 = [], 0
+    for b in range(batch.n_channels):
+        B2 = int(np.log2(batch.qam[b]))
+        nt = int(batch.nt[b])
+        lab = best_idx[a0:a0 + nt].astype(np.int64) & ((1 << B2) - 1)
+        hbs.append(((lab[:, None] >> np.arange(B2 - 1, -1, -1)) & 1).reshape(-1))
+        a0 += nt
+    errs_hard = np.concatenate(hbs) != bits
+    uniform = len(set(batch.snr_db.tolist())) <= 16
     per = {}
     nb = batch.nt.astype(np.int64) * np.log2(batch.qam).astype(np.int64)
     off = 0
     for b in range(batch.n_channels):
-        s = float(batch.snr_db[b])
+        s = float(batch.snr_db[b]) if uniform else float(5 * round(batch.snr_db[b] / 5))
         e = per.setdefault(s, [0, 0, 0])
         e[0] += int(errs_soft[off: off + nb[b]].sum())
         e[1] += int(errs_hard[off: off + nb[b]].sum())
@@ -204,34 +228,48 @@ def ber_of(batch, llr, best_idx):
 
 
 def cpu_baseline(batch, w, budget_s: float, rank: int):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload on the host cores."""
+    """The FP64 oracle, as it stands, on a bounded sample of the workload on the host cores:
+    an equal number of channels from every SNR point (or an even spread over the batch when the
+    SNR is continuous), sized from a calibration run so that the sample takes ~budget_s."""
     import oracle
     cores = os.cpu_count() or 1
-    per_snr = max(1, int(budget_s))   # grown below until the sample takes ~budget_s
-    snrs = sorted(set(batch.snr_db.tolist()))
-    by_snr = {s: [i for i in range(batch.n_channels) if batch.snr_db[i] == s] for s in snrs}
     T, Np = w["iterations"], w["chains"]
-    # calibrate on one channel per SNR point
+    snrs = sorted(set(batch.snr_db.tolist()))
+    if len(snrs) <= 16:
+        by = [[i for i in range(batch.n_channels) if batch.snr_db[i] == s] for s in snrs]
+    else:
+        by = [list(range(batch.n_channels))[::max(1, batch.n_channels // 64)]]
     t0 = time.perf_counter()
-    idx = [by_snr[s][0] for s in snrs]
+    idx = [g[0] for g in by]
     oracle.detect_batch(batch, chains=Np, iterations=T, seed=0, channels=idx, threads=cores)
     dt = time.perf_counter() - t0
-    per_snr = max(1, min(len(by_snr[snrs[0]]), int(budget_s / max(dt, 1e-3))))
-    idx = [i for s in snrs for i in by_snr[s][:per_snr]]
+    per = max(1, min(min(len(g) for g in by), int(budget_s / max(dt, 1e-3) * len(idx) / len(by))))
+    idx = [i for g in by for i in g[:per]]
     t0 = time.perf_counter()
     oracle.detect_batch(batch, chains=Np, iterations=T, seed=0, channels=idx, threads=cores)
     dt = time.perf_counter() - t0
     value = len(idx) * Np * T / dt
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(idx)} channels ({per_snr} per SNR point) x {Np} chains x {T} "
+            "sample": f"{len(idx)} channels ({per} per SNR group) x {Np} chains x {T} "
                       f"iterations, FP64 C oracle, one channel per thread", "seconds": dt,
             "detections_per_s": len(idx) / dt}
+
+
+def bench_config(args, w, n_channels, world, refresh, l2_note=None):
+    """The configuration block shared by both arms of the benchmark."""
+    cfg = {"workload": args.workload, "nt": w["nt"], "nr": w["nr"], "qam": w["qam"],
+           "snr_db": w.get("snr_db", "U[10,30]"), "channels": n_channels * world,
+           "chains": w["chains"], "iterations": w["iterations"], "preconditioned": True,
+           "refresh_period": refresh, "parallelism": f"replicas x{world}"}
+    if l2_note:
+        cfg["l2"] = l2_note
+    return cfg
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    batch, w = load_batch(args.scale, 0)
+    batch, w = load_batch(args.scale, 0, args.workload)
     vals = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(batch, w, args.cpu_seconds / max(1, args.steps), 0)
@@ -244,9 +282,11 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean([r["seconds"] for r in vals])),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "nt": w["nt"], "nr": w["nr"],
-                                            "qam": w["qam"], "chains": w["chains"],
-                                            "iterations": w["iterations"]},
+            "data": "synthetic",
+            "config": bench_config(args, w, batch.n_channels, world,
+                                   args.refresh if args.refresh is not None else
+                                   (50 if w["kind"] == "kronecker" else 0),
+                                   "host-resident oracle (no device)"),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -265,6 +305,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-fp32", action="store_true", help="also time the plain FP32 sampler")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workload.WORKLOADS),
+                    help="bench a parity-test configuration instead of the headline one")
+    ap.add_argument("--graph", action="store_true", help="replay run_chains from a CUDA graph")
+    ap.add_argument("--refresh", type=int, default=None, help="FP64 energy refresh period")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
@@ -281,9 +325,10 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    batch, w = load_batch(args.scale, rank)
+    batch, w = load_batch(args.scale, rank, args.workload)
     T, Np = w["iterations"], w["chains"]
     B = batch.n_channels
+    refresh = args.refresh if args.refresh is not None else (50 if w["kind"] == "kronecker" else 0)
 
     precision = args.precision
     if precision == "auto":
@@ -314,7 +359,8 @@ def main():
 
     def make(prec):
         return pkg.Detector(max_channels=B, max_nt=int(batch.nt.max()), max_nr=int(batch.nr.max()),
-                            chains=Np, precision=prec, seed=0, stream=stream)
+                            chains=Np, precision=prec, seed=0, stream=stream, refresh_period=refresh,
+                            engine=pkg.MCMC_ENGINE_GRAPH if args.graph else pkg.MCMC_ENGINE_AUTO)
 
     def step(det):
         det.preprocess(batch.nt, batch.nr, batch.qam, Hd, batch.H_off, yd, batch.y_off, sd)
@@ -406,10 +452,10 @@ def main():
         ber32 = ber_of(batch, o_llr.cpu().numpy(), o_idx.cpu().numpy())
         fp32_line = {"value": units_rank * world / (ms32 * 1e-3), "ms_per_step": ms32,
                      "chain_kernel_ms": kms32, "ber": ber32,
-                     "roofline": chain_roofline("fp32", w, units_rank, kms32)}
+                     "roofline": chain_roofline("fp32", w, units_rank, kms32, batch)}
         d32.destroy()
 
-    roofline = chain_roofline(precision, w, units_rank, chain_ms)
+    roofline = chain_roofline(precision, w, units_rank, chain_ms, batch)
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -421,11 +467,9 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"mixed": "bf16x2+f32", "fp32": "f32", "fp64": "f64"}[precision],
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "nt": w["nt"], "nr": w["nr"], "qam": w["qam"],
-                           "snr_db": w["snr_db"], "channels": B * world, "chains": Np,
-                           "iterations": T, "precision": precision, "preconditioned": True,
-                           "l2": "inputs larger than L2 (H = %d MB)" % (Hd.numel() * 4 // 2**20),
-                           "parallelism": f"replicas x{world}"},
+                "config": bench_config(args, w, B, world, refresh,
+                                       "inputs larger than L2 (H = %d MB)" % (Hd.numel() * 4 // 2**20)),
+                "precision": precision, "graph": bool(args.graph),
                 "detections_per_s": det_per_s, "chain_kernel_ms": chain_ms,
                 "ber": ber, "snr_points_at_ber_le_1e-3": ber_ok,
                 "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
