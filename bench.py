@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workload.WORKLOADS),
                     help="bench a parity-test configuration instead of the headline one")
     ap.add_argument("--graph", action="store_true", help="replay run_chains from a CUDA graph")
+    ap.add_argument("--engine", default="auto", choices=["auto", "tc", "simt"],
+                    help="chain-kernel engine (auto: the library's per-class autotuner)")
     ap.add_argument("--refresh", type=int, default=None, help="FP64 energy refresh period")
     args = ap.parse_args()
     rank, world, local = _env_rank()
@@ -360,7 +362,10 @@ def main():
     def make(prec):
         return pkg.Detector(max_channels=B, max_nt=int(batch.nt.max()), max_nr=int(batch.nr.max()),
                             chains=Np, precision=prec, seed=0, stream=stream, refresh_period=refresh,
-                            engine=pkg.MCMC_ENGINE_GRAPH if args.graph else pkg.MCMC_ENGINE_AUTO)
+                            engine=({"auto": pkg.MCMC_ENGINE_AUTO, "tc": pkg.MCMC_ENGINE_TC,
+                                     "simt": pkg.MCMC_ENGINE_SIMT}[args.engine] if prec == precision
+                                    else pkg.MCMC_ENGINE_AUTO)
+                            | (pkg.MCMC_ENGINE_GRAPH if args.graph else 0))
 
     def step(det):
         det.preprocess(batch.nt, batch.nr, batch.qam, Hd, batch.H_off, yd, batch.y_off, sd)
@@ -469,7 +474,7 @@ def main():
                 "data": "synthetic",
                 "config": bench_config(args, w, B, world, refresh,
                                        "inputs larger than L2 (H = %d MB)" % (Hd.numel() * 4 // 2**20)),
-                "precision": precision, "graph": bool(args.graph),
+                "precision": precision, "graph": bool(args.graph), "engine": args.engine,
                 "detections_per_s": det_per_s, "chain_kernel_ms": chain_ms,
                 "ber": ber, "snr_points_at_ber_le_1e-3": ber_ok,
                 "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
