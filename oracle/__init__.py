@@ -101,6 +101,17 @@ def lib():
             l.oracle_step_chains.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                              ctypes.c_int, ctypes.c_uint32, _ip,
                                              ctypes.POINTER(StepInfo)]
+            l.oracle_mix_log_q.restype = ctypes.c_double
+            l.oracle_mix_log_q.argtypes = [pp, ctypes.c_double, _ip, _dp, _ip]
+            l.oracle_mix_propose.restype = ctypes.c_double
+            l.oracle_mix_propose.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, ctypes.c_double, _ip, _dp, _ip]
+            l.oracle_mix_accept.restype = ctypes.c_int
+            l.oracle_mix_accept.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.c_uint32, ctypes.c_double, _ip, _ip, _dp, _dp,
+                                            ctypes.c_double, ctypes.POINTER(StepInfo)]
+            l.oracle_init_state_learned.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32,
+                                                    ctypes.c_uint32, _dp, _ip]
             l.oracle_run_chain.restype = ctypes.c_int
             l.oracle_run_chain.argtypes = [pp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                            ctypes.c_uint32, ctypes.c_int, _ip, _dp, _ip, _dp]
@@ -208,7 +219,9 @@ class Target:
         if preconditioned:
             P = preconditioner(Hr, sigma2 / (2.0 * d * d))
             beta = d * d / sigma2
-        return cls(Hr, yr, sigma2, L, d, alpha=alpha_scale * sigma2, beta=beta, tau=tau, P=P)
+        t = cls(Hr, yr, sigma2, L, d, alpha=alpha_scale * sigma2, beta=beta, tau=tau, P=P)
+        t.Hc, t.yc = np.asarray(H), np.asarray(y)
+        return t
 
     @property
     def ptr(self):
@@ -251,6 +264,39 @@ class Target:
                     cat_margin=np.array([x.cat_margin for x in infos]),
                     accepted=np.array([x.accepted for x in infos], bool))
         return st, info
+
+    def nn_logp(self, params, k=None, quant=False) -> np.ndarray:
+        """Network log-probabilities [Nt, Qc] at level indices k (None: x = 0) for a channel
+        built by from_channel."""
+        from oracle import mlp
+        F = mlp.features(self.Hc, self.yc, self.sigma2, self.L * self.L, k)
+        return mlp.log_softmax(mlp.forward(params, F, self.L * self.L, quant)[0])
+
+    def mix_log_q(self, lam, k_from, nnlogp_from, k_to) -> float:
+        return lib().oracle_mix_log_q(self.ptr, float(lam), _i(np.ascontiguousarray(k_from, np.int32)),
+                                      _d(np.ascontiguousarray(nnlogp_from, np.float64)),
+                                      _i(np.ascontiguousarray(k_to, np.int32)))
+
+    def mix_step(self, seed, channel, chain, t, k, lam, params=None, nn=None, quant=False):
+        """Learned mixture move numbered t from level indices k (see oracle_mix_propose). The
+        network is params (evaluated by oracle.mlp) or a callable nn(k) -> [Nt, Qc] log-probs."""
+        nnf = nn if nn is not None else (lambda kk: self.nn_logp(params, kk, quant))
+        kk = np.ascontiguousarray(k, np.int32).copy()
+        lx = np.ascontiguousarray(nnf(kk), np.float64)
+        kp = np.zeros(self.N, np.int32)
+        margin = lib().oracle_mix_propose(self.ptr, int(seed), int(channel), int(chain), int(t),
+                                          float(lam), _i(kk), _d(lx), _i(kp))
+        lxp = np.ascontiguousarray(nnf(kp), np.float64)
+        info = StepInfo()
+        lib().oracle_mix_accept(self.ptr, int(seed), int(channel), int(chain), int(t), float(lam),
+                                _i(kk), _i(kp), _d(lx), _d(lxp), margin, ctypes.byref(info))
+        return kk, info
+
+    def init_state_learned(self, seed, channel, chain, nnlogp0) -> np.ndarray:
+        k = np.zeros(self.N, np.int32)
+        lp = np.ascontiguousarray(nnlogp0, np.float64)
+        lib().oracle_init_state_learned(self.ptr, int(seed), int(channel), int(chain), _d(lp), _i(k))
+        return k
 
     def run_chain(self, seed, channel, chain, t_offset, iters, k):
         kk = np.ascontiguousarray(k, np.int32).copy()

@@ -356,6 +356,140 @@ int oracle_run_chain(const oracle_problem *p, uint64_t seed, uint32_t channel, u
     return accepts;
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* Learned proposal (an extension with no counterpart in the paper). Per complex antenna i     */
+/* (real dimensions i and Nt + i, symbol s = kI * L + kQ) the proposal is the mixture          */
+/*     q_mix,i(s | x) = (1 - lambda) q_i(kI | x) q_{Nt+i}(kQ | x) + lambda p_i(s | x)          */
+/* of the product of Algorithm 1's two factors and a network's per-antenna distribution p_i    */
+/* evaluated at x (passed in as natural-log probabilities, Nt x Qc). The move is accepted with */
+/* the Metropolis-Hastings ratio of Eq. (18) written with q_mix, so every such move keeps the  */
+/* target exactly. lambda = 0 is Algorithm 1's transition, uniform for uniform.                */
+/* Random numbers: dimension n's proposal uniform and the acceptance uniform as in Algorithm   */
+/* 1's transition t; the component choice of antenna i from counter                            */
+/* (t, 0x80000000 + i, channel, chain / 4): the network's component iff u < lambda. A network  */
+/* draw takes the smallest s with u_i * S_{Qc-1} < S_s (u_i the in-phase dimension's uniform). */
+/* ------------------------------------------------------------------------------------------ */
+
+static uint32_t mix_word(uint64_t seed, uint32_t t, int i, uint32_t channel, uint32_t chain)
+{
+    return philox_word(seed, t, 0x80000000u + (uint32_t)i, channel, chain);
+}
+
+static double log_add(double a, double b)
+{
+    double m = a > b ? a : b;
+    if (m == -INFINITY) return -INFINITY;
+    return m + log(exp(a - m) + exp(b - m));
+}
+
+/* log q_mix(x_to | x_from) with the network's log-probabilities nnlogp evaluated at x_from. */
+double oracle_mix_log_q(const oracle_problem *p, double lambda, const int *k_from,
+                        const double *nnlogp, const int *k_to)
+{
+    int N = p->N, L = p->L, nt = N / 2, Q = L * L;
+    double d[ORACLE_MAX_N], li[ORACLE_MAX_L], lq[ORACLE_MAX_L];
+    drift(p, k_from, d);
+    double s = 0.0;
+    for (int i = 0; i < nt; ++i) {
+        factor_logits(p, k_from[i], d[i], li);
+        factor_logits(p, k_from[nt + i], d[nt + i], lq);
+        double ld = log_softmax_at(li, L, k_to[i]) + log_softmax_at(lq, L, k_to[nt + i]);
+        double ln = nnlogp[i * Q + k_to[i] * L + k_to[nt + i]];
+        double a = lambda < 1.0 ? log1p(-lambda) + ld : -INFINITY;
+        double b = lambda > 0.0 ? log(lambda) + ln : -INFINITY;
+        s += log_add(a, b);
+    }
+    return s;
+}
+
+/* First half of a learned move numbered t: draws x' from q_mix(. | x) into kp. Returns the
+ * smallest distance of a deciding uniform to its decision boundary (CDF margins relative to
+ * the total, and |u - lambda| of the component choices). */
+double oracle_mix_propose(const oracle_problem *p, uint64_t seed, uint32_t channel,
+                          uint32_t chain, uint32_t t, double lambda, const int *k,
+                          const double *nnlogp, int *kp)
+{
+    int N = p->N, L = p->L, nt = N / 2, Q = L * L;
+    double d[ORACLE_MAX_N], logit[ORACLE_MAX_L];
+    double margin = 1.0;
+    drift(p, k, d);
+    for (int i = 0; i < nt; ++i) {
+        double uc = oracle_uniform(mix_word(seed, t, i, channel, chain));
+        if (fabs(uc - lambda) < margin) margin = fabs(uc - lambda);
+        if (uc < lambda) {
+            double S[ORACLE_MAX_L * ORACLE_MAX_L], acc = 0.0;
+            for (int s = 0; s < Q; ++s) { acc += exp(nnlogp[i * Q + s]); S[s] = acc; }
+            double target = oracle_uniform(philox_word(seed, t, (uint32_t)i, channel, chain)) * S[Q - 1];
+            int sel = Q - 1;
+            for (int s = 0; s < Q; ++s) if (target < S[s]) { sel = s; break; }
+            double lo = sel > 0 ? S[sel - 1] : 0.0;
+            double m1 = (target - lo) / S[Q - 1], m2 = (S[sel] - target) / S[Q - 1];
+            if (sel > 0 && m1 < margin) margin = m1;
+            if (sel < Q - 1 && m2 < margin) margin = m2;
+            kp[i] = sel / L;
+            kp[nt + i] = sel % L;
+            continue;
+        }
+        for (int h = 0; h < 2; ++h) {
+            int n = h ? nt + i : i;
+            factor_logits(p, k[n], d[n], logit);
+            double mx = logit[0];
+            for (int j = 1; j < L; ++j) if (logit[j] > mx) mx = logit[j];
+            double S[ORACLE_MAX_L], acc = 0.0;
+            for (int j = 0; j < L; ++j) { acc += exp(logit[j] - mx); S[j] = acc; }
+            double target = oracle_uniform(philox_word(seed, t, (uint32_t)n, channel, chain)) * S[L - 1];
+            int sel = L - 1;
+            for (int j = 0; j < L; ++j) if (target < S[j]) { sel = j; break; }
+            double lo = sel > 0 ? S[sel - 1] : 0.0;
+            double m1 = (target - lo) / S[L - 1], m2 = (S[sel] - target) / S[L - 1];
+            if (sel > 0 && m1 < margin) margin = m1;
+            if (sel < L - 1 && m2 < margin) margin = m2;
+            kp[n] = sel;
+        }
+    }
+    return margin;
+}
+
+/* Second half: Metropolis-Hastings test of x' against x with the network evaluated at x
+ * (nnlogp_x) and at x' (nnlogp_xp); k becomes the next state. info as for Algorithm 1. */
+int oracle_mix_accept(const oracle_problem *p, uint64_t seed, uint32_t channel, uint32_t chain,
+                      uint32_t t, double lambda, int *k, const int *kp, const double *nnlogp_x,
+                      const double *nnlogp_xp, double margin, oracle_step_info *info)
+{
+    double v = f_tempered(p, kp) - f_tempered(p, k) +
+               oracle_mix_log_q(p, lambda, kp, nnlogp_xp, k) -
+               oracle_mix_log_q(p, lambda, k, nnlogp_x, kp);
+    double log_a = v < 0.0 ? v : 0.0;
+    double log_u = log(oracle_uniform(philox_word(seed, t, 0xFFFFFFFFu, channel, chain)));
+    int acc = (log_a > log_u);
+    if (acc) memcpy(k, kp, sizeof(int) * (size_t)p->N);
+    if (info) {
+        info->log_a = log_a;
+        info->log_u = log_u;
+        info->cat_margin = margin;
+        info->f_new = f_tempered(p, k);
+        info->accepted = acc;
+    }
+    return acc;
+}
+
+/* Warm start: per antenna i a symbol drawn from the network's distribution at x = 0 (nnlogp,
+ * Nt x Qc) by inverse CDF with dimension i's t = 0 word read as a uniform. */
+void oracle_init_state_learned(const oracle_problem *p, uint64_t seed, uint32_t channel,
+                               uint32_t chain, const double *nnlogp, int *k)
+{
+    int L = p->L, nt = p->N / 2, Q = L * L;
+    for (int i = 0; i < nt; ++i) {
+        double S[ORACLE_MAX_L * ORACLE_MAX_L], acc = 0.0;
+        for (int s = 0; s < Q; ++s) { acc += exp(nnlogp[i * Q + s]); S[s] = acc; }
+        double target = oracle_uniform(philox_word(seed, 0u, (uint32_t)i, channel, chain)) * S[Q - 1];
+        int sel = Q - 1;
+        for (int s = 0; s < Q; ++s) if (target < S[s]) { sel = s; break; }
+        k[i] = sel / L;
+        k[nt + i] = sel % L;
+    }
+}
+
 /* One transition numbered t of each of `chains` chains (chain ids chain0 .. chain0+chains-1)
  * from the states in k (chains x N, row-major), in place; infos may be NULL. */
 void oracle_step_chains(const oracle_problem *p, uint64_t seed, uint32_t channel, uint32_t chain0,
