@@ -20,8 +20,8 @@ from . import build as _build
 __all__ = [
     "Detector", "Config", "Stats", "lib", "load", "MCMC_PREC_FP64", "MCMC_PREC_FP32",
     "MCMC_PREC_MIXED", "MCMC_ENGINE_AUTO", "MCMC_ENGINE_SIMT", "MCMC_ENGINE_TC",
-    "MCMC_ENGINE_GRAPH", "McmcError",
-    "ABI_FUNCTIONS",
+    "MCMC_ENGINE_GRAPH", "McmcError", "Mlp",
+    "ABI_FUNCTIONS", "ABI_FUNCTIONS_LEARNED",
 ]
 
 MCMC_PREC_FP64, MCMC_PREC_FP32, MCMC_PREC_MIXED = 0, 1, 2
@@ -37,6 +37,14 @@ ABI_FUNCTIONS = [
     "mcmc_detect_set_chains", "mcmc_detect_synchronize", "mcmc_detect_destroy",
     "mcmc_status_string", "mcmc_detect_last_error", "mcmc_detect_kernel_launches",
     "mcmc_detect_noalloc",
+]
+
+# Every entry point of include/mcmcdet_learned.h.
+ABI_FUNCTIONS_LEARNED = [
+    "mcmc_mlp_param_count", "mcmc_mlp_create", "mcmc_mlp_destroy", "mcmc_mlp_last_error",
+    "mcmc_mlp_set_params", "mcmc_mlp_get_params", "mcmc_mlp_forward", "mcmc_mlp_loss_grad",
+    "mcmc_mlp_train_step", "mcmc_detect_features", "mcmc_detect_set_model",
+    "mcmc_detect_init_learned", "mcmc_detect_mix_step",
 ]
 
 
@@ -104,6 +112,24 @@ def load(path: Optional[str] = None):
                                       ctypes.c_uint64, i32, ctypes.c_float, ctypes.c_float, vp,
                                       vp, vp, vp]
     l.mcmc_detect_noalloc.restype = ctypes.c_int
+    l.mcmc_mlp_param_count.argtypes = [i32]
+    l.mcmc_mlp_param_count.restype = i64
+    l.mcmc_mlp_create.argtypes = [i32, i32, vp, ctypes.POINTER(vp)]
+    l.mcmc_mlp_destroy.argtypes = [vp]
+    l.mcmc_mlp_last_error.argtypes = [vp]
+    l.mcmc_mlp_last_error.restype = ctypes.c_char_p
+    l.mcmc_mlp_set_params.argtypes = [vp, vp, i32]
+    l.mcmc_mlp_get_params.argtypes = [vp, vp, i32]
+    l.mcmc_mlp_forward.argtypes = [vp, i64, vp, vp, i32]
+    l.mcmc_mlp_loss_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    l.mcmc_mlp_train_step.argtypes = [vp, i32, vp, vp, vp, ctypes.c_float, vp]
+    l.mcmc_detect_features.argtypes = [vp, i32, vp]
+    l.mcmc_detect_set_model.argtypes = [vp, vp, ctypes.c_float, i32]
+    l.mcmc_detect_init_learned.argtypes = [vp]
+    l.mcmc_detect_mix_step.argtypes = [vp, i64]
+    for n in ABI_FUNCTIONS_LEARNED:
+        if n not in ("mcmc_mlp_param_count", "mcmc_mlp_last_error"):
+            getattr(l, n).restype = ctypes.c_int
     if path is None:
         _lib = l
     return l
@@ -247,6 +273,43 @@ class Detector:
     def synchronize(self):
         self._check(self._l.mcmc_detect_synchronize(self._h))
 
+    # -- learned proposal (include/mcmcdet_learned.h) --------------------------------------
+    def features(self, X=None, *, at_zero: bool = False):
+        """Network features of the current states (or of x = 0) into a device tensor."""
+        import torch
+        m = self.batch_meta
+        rows = int(m["nt"].sum()) * (1 if at_zero else self.cfg.chains)
+        if X is None:
+            X = torch.empty((rows, 6), dtype=torch.float32, device="cuda")
+        self._check(self._l.mcmc_detect_features(self._h, int(at_zero), _ptr(X)))
+        return X
+
+    def set_model(self, mlp, lam: float, *, tensor_cores: bool = False):
+        self._model = mlp
+        self._check(self._l.mcmc_detect_set_model(self._h, mlp.handle if mlp else None,
+                                                  float(lam), int(tensor_cores)))
+
+    def init_learned(self):
+        self._check(self._l.mcmc_detect_init_learned(self._h))
+
+    def mix_step(self, t: int):
+        self._check(self._l.mcmc_detect_mix_step(self._h, int(t)))
+
+    def run_mixed(self, iterations: int, period: int, t_offset: int = 0):
+        """Transitions t_offset+1 .. t_offset+iterations; transition t is a mixture move when
+        t % period == 0 and an Algorithm 1 transition otherwise."""
+        t = t_offset
+        end = t_offset + iterations
+        while t < end:
+            nxt = min(end, (t // period + 1) * period)
+            plain = nxt - t - (1 if nxt % period == 0 else 0)
+            if plain:
+                self.run_chains(plain, t)
+            t += plain
+            if t < end and (t + 1) % period == 0:
+                self.mix_step(t + 1)
+                t += 1
+
     def destroy(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._l.mcmc_detect_destroy(self._h)
@@ -265,3 +328,78 @@ class Detector:
 
     def __exit__(self, *exc):
         self.destroy()
+
+
+class Mlp:
+    """One ``mcmc_mlp`` handle: the learned proposal's network (include/mcmcdet_learned.h)."""
+
+    def __init__(self, qam: int, *, max_rows: int = 65536, stream=None):
+        self._l = load()
+        self.qam = int(qam)
+        h = ctypes.c_void_p()
+        st = self._l.mcmc_mlp_create(self.qam, int(max_rows), stream, ctypes.byref(h))
+        if st != 0:
+            raise McmcError(st, self._l.mcmc_status_string(st).decode())
+        self._h = h
+        self.max_rows = int(max_rows)
+        self.param_count = int(self._l.mcmc_mlp_param_count(self.qam))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, st: int):
+        if st != 0:
+            msg = self._l.mcmc_mlp_last_error(self._h).decode()
+            raise McmcError(st, msg or self._l.mcmc_status_string(st).decode())
+
+    def set_params(self, params):
+        if _is_host(params):
+            params = np.ascontiguousarray(params, np.float32)
+        self._check(self._l.mcmc_mlp_set_params(self._h, _ptr(params), int(_is_host(params))))
+
+    def get_params(self, out=None):
+        if out is None:
+            out = np.zeros(self.param_count, np.float32)
+        self._check(self._l.mcmc_mlp_get_params(self._h, _ptr(out), int(_is_host(out))))
+        return out
+
+    def forward(self, X, logits=None, *, tensor_cores: bool = False):
+        import torch
+        rows = int(X.shape[0])
+        if logits is None:
+            logits = torch.empty((rows, self.qam), dtype=torch.float32, device=X.device)
+        self._check(self._l.mcmc_mlp_forward(self._h, rows, _ptr(X), _ptr(logits),
+                                             int(tensor_cores)))
+        return logits
+
+    def loss_grad(self, X, labels, idx=None, rows=None):
+        """(loss, gradient) as device tensors; rows defaults to len(idx) or len(X)."""
+        import torch
+        if rows is None:
+            rows = int(idx.shape[0]) if idx is not None else int(X.shape[0])
+        loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+        grad = torch.zeros(self.param_count, dtype=torch.float32, device=X.device)
+        self._check(self._l.mcmc_mlp_loss_grad(self._h, int(rows), _ptr(X), _ptr(labels),
+                                               _ptr(idx), _ptr(loss), _ptr(grad)))
+        return loss, grad
+
+    def train_step(self, X, labels, idx, lr: float, loss=None, rows=None):
+        if rows is None:
+            rows = int(idx.shape[0]) if idx is not None else int(X.shape[0])
+        self._check(self._l.mcmc_mlp_train_step(self._h, int(rows), _ptr(X), _ptr(labels),
+                                                _ptr(idx), float(lr), _ptr(loss)))
+        return loss
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._l.mcmc_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    close = destroy
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.destroy()
+        except Exception:
+            pass

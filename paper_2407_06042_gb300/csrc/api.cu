@@ -2,6 +2,7 @@
 // workspace management, batch planning and kernel launches. No torch types, no exceptions
 // across the ABI.
 #include "../../include/mcmcdet.h"
+#include "../../include/mcmcdet_learned.h"
 
 #include <algorithm>
 #include <cmath>
@@ -17,6 +18,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "mlp.h"
 #include "tc_plan.h"
 
 using namespace mcmcdet;
@@ -84,6 +86,12 @@ struct mcmc_detector {
         d_w32, d_bt32, d_bt64, d_tc, d_states, d_best_states, d_f, d_best_f, d_accepts,
         d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp;
     HostBuf h_stage;
+
+    // learned proposal (not owned network; scratch of the mixture move)
+    mcmc_mlp *mlp = nullptr;
+    float mix_lambda = 0.f;
+    int mix_tc = 0;
+    DevBuf d_mx_gx, d_mx_px, d_mx_gxp, d_mx_pxp, d_mx_prop, d_mx_X, d_mx_logits, d_mx_lqf;
 };
 
 namespace {
@@ -565,7 +573,9 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
                       &d->d_G64, &d->d_GM64, &d->d_z64, &d->d_w64, &d->d_z32, &d->d_w32,
                       &d->d_bt32, &d->d_bt64, &d->d_tc, &d->d_states, &d->d_best_states, &d->d_f,
                       &d->d_best_f, &d->d_accepts, &d->d_misc, &d->d_in_H, &d->d_in_y,
-                      &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf, &d->d_dexp};
+                      &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf, &d->d_dexp,
+                      &d->d_mx_gx, &d->d_mx_px, &d->d_mx_gxp, &d->d_mx_pxp, &d->d_mx_prop,
+                      &d->d_mx_X, &d->d_mx_logits, &d->d_mx_lqf};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto &g : d->groups)
@@ -988,6 +998,185 @@ mcmc_status mcmc_detect_synchronize(mcmc_detector *d)
 {
     if (!d) return MCMC_EINVAL;
     return read_status(d);
+}
+
+}  // extern "C"
+
+// ---- learned proposal (include/mcmcdet_learned.h) -----------------------------------------
+
+namespace {
+
+mcmc_status learned_ok(mcmc_detector *d)
+{
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "learned proposal before preprocess");
+    if (d->cfg.precision == MCMC_PREC_FP64)
+        return fail(d, MCMC_EUNSUPPORTED, "the learned proposal runs on FP32 or MIXED handles");
+    if (!d->cfg.preconditioned)
+        return fail(d, MCMC_EUNSUPPORTED, "the learned proposal needs the preconditioned proposal");
+    return MCMC_OK;
+}
+
+MixGramArgs gram_args(mcmc_detector *d, const int8_t *x, float *gx, float *px, float *X, int L)
+{
+    MixGramArgs g{};
+    g.desc = P<ChannelDesc>(d->d_desc);
+    g.chains = d->cfg.chains;
+    g.L = L;
+    g.bt32 = P<float>(d->d_bt32);
+    g.z32 = P<float>(d->d_z32);
+    g.w32 = P<float>(d->d_w32);
+    g.x = x;
+    g.gx = gx;
+    g.px = px;
+    g.X = X;
+    return g;
+}
+
+MixStepArgs step_args(mcmc_detector *d)
+{
+    MixStepArgs a{};
+    a.desc = P<ChannelDesc>(d->d_desc);
+    a.chains = d->cfg.chains;
+    a.L = 0;
+    if (d->mlp) a.L = d->mlp->Q == 4 ? 2 : d->mlp->Q == 16 ? 4 : 8;
+    a.z32 = P<float>(d->d_z32);
+    a.w32 = P<float>(d->d_w32);
+    a.states = P<int8_t>(d->d_states);
+    a.states_out = P<int8_t>(d->d_states);
+    a.prop = P<int8_t>(d->d_mx_prop);
+    a.gx = P<float>(d->d_mx_gx);
+    a.px = P<float>(d->d_mx_px);
+    a.gxp = P<float>(d->d_mx_gxp);
+    a.pxp = P<float>(d->d_mx_pxp);
+    a.logits = P<float>(d->d_mx_logits);
+    a.lqf = P<float>(d->d_mx_lqf);
+    a.lambda = d->mix_lambda;
+    a.l2w_plain = d->mix_lambda < 1.f ? (float)std::log2(1.0 - (double)d->mix_lambda) : -INFINITY;
+    a.l2w_nn = d->mix_lambda > 0.f ? (float)std::log2((double)d->mix_lambda) : -INFINITY;
+    a.key0 = (uint32_t)(d->cfg.seed & 0xFFFFFFFFu);
+    a.key1 = (uint32_t)(d->cfg.seed >> 32);
+    a.f = P<double>(d->d_f);
+    a.best_f = P<double>(d->d_best_f);
+    a.best_states = P<int8_t>(d->d_best_states);
+    a.accepts = P<unsigned long long>(d->d_accepts);
+    a.status = status_ptr(d);
+    return a;
+}
+
+cudaError_t net_forward(mcmc_detector *d, long long rows, const float *X, float *logits)
+{
+    d->launches++;
+    return d->mix_tc ? mlp_forward_tc(d->mlp, rows, X, logits, d->stream)
+                     : mlp_forward_simt(d->mlp, rows, X, logits, d->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+mcmc_status mcmc_detect_features(mcmc_detector *d, int32_t at_zero, float *X)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!X || (at_zero != 0 && at_zero != 1)) return fail(d, MCMC_EINVAL, "bad arguments");
+    mcmc_status st = learned_ok(d);
+    if (st != MCMC_OK) return st;
+    if (at_zero) {
+        CK(launch_features_zero(gram_args(d, nullptr, nullptr, nullptr, X, 0), d->n_channels,
+                                d->max_nt, d->stream), "features kernel");
+    } else {
+        CK(ensure(d->d_mx_gx, 4 * d->tot_states), "alloc scratch");
+        CK(ensure(d->d_mx_px, 4 * d->tot_states), "alloc scratch");
+        CK(launch_gram_features(gram_args(d, P<int8_t>(d->d_states), P<float>(d->d_mx_gx),
+                                          P<float>(d->d_mx_px), X, 0),
+                                d->n_channels, d->stream), "features kernel");
+    }
+    d->launches++;
+    return MCMC_OK;
+}
+
+mcmc_status mcmc_detect_set_model(mcmc_detector *d, mcmc_mlp *m, float lambda, int32_t tensor_cores)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!m) {
+        d->mlp = nullptr;
+        return MCMC_OK;
+    }
+    if (!(lambda >= 0.f && lambda <= 1.f)) return fail(d, MCMC_EINVAL, "lambda must be in [0, 1]");
+    if (tensor_cores != 0 && tensor_cores != 1) return fail(d, MCMC_EINVAL, "tensor_cores must be 0 or 1");
+    if (d->cfg.precision == MCMC_PREC_FP64)
+        return fail(d, MCMC_EUNSUPPORTED, "the learned proposal runs on FP32 or MIXED handles");
+    if (!d->cfg.preconditioned)
+        return fail(d, MCMC_EUNSUPPORTED, "the learned proposal needs the preconditioned proposal");
+    if (tensor_cores && d->cc_major * 10 + d->cc_minor != 103)
+        return fail(d, MCMC_EUNSUPPORTED, "tensor-core inference needs sm_103");
+    d->mlp = m;
+    d->mix_lambda = lambda;
+    d->mix_tc = tensor_cores;
+    return MCMC_OK;
+}
+
+mcmc_status mcmc_detect_init_learned(mcmc_detector *d)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    mcmc_status st = learned_ok(d);
+    if (st != MCMC_OK) return st;
+    if (!d->mlp) return fail(d, MCMC_ESTATE, "no network attached");
+    const long long rows = d->tot_ant;
+    CK(ensure(d->d_mx_X, 4 * 6 * (size_t)rows), "alloc scratch");
+    CK(ensure(d->d_mx_logits, 4 * (size_t)d->mlp->Q * rows), "alloc scratch");
+    CK(launch_features_zero(gram_args(d, nullptr, nullptr, nullptr, P<float>(d->d_mx_X), 0),
+                            d->n_channels, d->max_nt, d->stream), "features kernel");
+    d->launches++;
+    CK(net_forward(d, rows, P<float>(d->d_mx_X), P<float>(d->d_mx_logits)), "network forward");
+    CK(launch_mix(2, step_args(d), d->n_channels, d->max_nt, d->stream), "warm start kernel");
+    d->launches++;
+    d->f_valid = false;
+    d->d_valid = false;
+    st = ensure_energies(d);
+    if (st != MCMC_OK) return st;
+    return read_status(d);
+}
+
+mcmc_status mcmc_detect_mix_step(mcmc_detector *d, int64_t t)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    mcmc_status st = learned_ok(d);
+    if (st != MCMC_OK) return st;
+    if (!d->mlp) return fail(d, MCMC_ESTATE, "no network attached");
+    if (t < 1 || t > 0xFFFFFFFFll) return fail(d, MCMC_EINVAL, "t out of range");
+    st = ensure_energies(d);
+    if (st != MCMC_OK) return st;
+    const long long rows = d->tot_states / 2;
+    for (DevBuf *b : {&d->d_mx_gx, &d->d_mx_px, &d->d_mx_gxp, &d->d_mx_pxp, &d->d_mx_lqf})
+        CK(ensure(*b, 4 * (size_t)d->tot_states), "alloc scratch");
+    CK(ensure(d->d_mx_prop, d->tot_states), "alloc scratch");
+    CK(ensure(d->d_mx_X, 4 * 6 * (size_t)rows), "alloc scratch");
+    CK(ensure(d->d_mx_logits, 4 * (size_t)d->mlp->Q * rows), "alloc scratch");
+    MixStepArgs a = step_args(d);
+    a.t = (uint32_t)t;
+    const int L = a.L;
+    float *X = P<float>(d->d_mx_X), *lg = P<float>(d->d_mx_logits);
+    CK(launch_gram_features(gram_args(d, P<int8_t>(d->d_states), P<float>(d->d_mx_gx),
+                                      P<float>(d->d_mx_px), X, L), d->n_channels, d->stream),
+       "features kernel");
+    CK(net_forward(d, rows, X, lg), "network forward");
+    CK(launch_mix(0, a, d->n_channels, d->max_nt, d->stream), "mixture draw kernel");
+    CK(launch_gram_features(gram_args(d, P<int8_t>(d->d_mx_prop), P<float>(d->d_mx_gxp),
+                                      P<float>(d->d_mx_pxp), X, L), d->n_channels, d->stream),
+       "features kernel");
+    CK(net_forward(d, rows, X, lg), "network forward");
+    CK(launch_mix(1, a, d->n_channels, d->max_nt, d->stream), "mixture accept kernel");
+    d->launches += 4;
+    d->d_valid = false;
+    long long moved = 0;
+    for (const ChannelDesc &c : d->desc)
+        if (c.L == L) moved += d->cfg.chains;
+    d->transitions += moved;
+    return MCMC_OK;
 }
 
 }  // extern "C"

@@ -117,6 +117,46 @@ struct EstimateArgs {
     unsigned *status;
 };
 
+// Learned proposal: Gram products and features at a set of states (one kernel), and the
+// mixture move / warm start kernels.
+struct MixGramArgs {
+    const ChannelDesc *desc;
+    int chains;
+    int L;                  // channels with this many levels (0: every channel)
+    const float *bt32;      // [Gt | P~ Gt] FP32 operand, N x NOp per channel
+    const float *z32, *w32;
+    const int8_t *x;        // states the products are taken at
+    float *gx, *px;         // out: Gt x, P~ Gt x (state layout)
+    float *X;               // out: features [rows x 6], or null
+};
+
+struct MixStepArgs {
+    const ChannelDesc *desc;
+    int chains;
+    int L;                  // the network's channels: L levels, Q = L^2 outputs
+    const float *z32, *w32;
+    const int8_t *states;   // x
+    int8_t *states_out;     // next state (may alias states)
+    int8_t *prop;           // x'
+    const float *gx, *px;   // products at x
+    const float *gxp, *pxp; // products at x'
+    const float *logits;    // network logits at x (propose), at x' (accept), at 0 (warm start)
+    float *lqf;             // log2 q_mix(x' | x) per (chain, antenna)
+    float lambda;
+    float l2w_plain, l2w_nn;   // log2(1 - lambda), log2(lambda)
+    uint32_t t;
+    uint32_t key0, key1;
+    double *f, *best_f;
+    int8_t *best_states;
+    unsigned long long *accepts;
+    unsigned *status;
+};
+
+cudaError_t launch_gram_features(const MixGramArgs &a, int n_channels, cudaStream_t s);
+cudaError_t launch_features_zero(const MixGramArgs &a, int n_channels, int max_nt, cudaStream_t s);
+// which: 0 propose, 1 accept, 2 warm start
+cudaError_t launch_mix(int which, const MixStepArgs &a, int n_channels, int max_nt, cudaStream_t s);
+
 size_t chain_smem_bytes_simt(int elem_size, int cg, int max_n, int max_nop, bool bt_in_smem);
 
 cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,

@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports every entry point
-that include/mcmcdet.h declares. Only host-only entry points are called (no GPU here)."""
+that include/mcmcdet.h and include/mcmcdet_learned.h declare. Only host-only entry points are
+called (no GPU here)."""
 import ctypes
 import os
 import re
@@ -9,20 +10,41 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _header_functions():
-    src = open(os.path.join(ROOT, "include", "mcmcdet.h")).read()
+def _header_functions(name="mcmcdet.h"):
+    src = open(os.path.join(ROOT, "include", name)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(mcmc_[a-z_]+)\s*\(", src)))
 
 
-def test_library_builds_and_exports_every_declared_symbol():
+@pytest.mark.parametrize("header,attr", [("mcmcdet.h", "ABI_FUNCTIONS"),
+                                         ("mcmcdet_learned.h", "ABI_FUNCTIONS_LEARNED")])
+def test_library_builds_and_exports_every_declared_symbol(header, attr):
     import paper_2407_06042_gb300 as pkg
     lib = pkg.load()
-    declared = _header_functions()
+    declared = _header_functions(header)
     assert declared, "no declarations parsed"
     for name in declared:
         assert hasattr(lib, name), f"{name} not exported"
-    assert sorted(pkg.ABI_FUNCTIONS) == declared
+    assert sorted(getattr(pkg, attr)) == declared
+
+
+def test_learned_host_only_entry_points():
+    """Parameter counts agree with the oracle network's layout; argument checks run on the
+    host before any device call."""
+    import paper_2407_06042_gb300 as pkg
+    import oracle.mlp as omlp
+    lib = pkg.load()
+    for q in (4, 16, 64):
+        assert lib.mcmc_mlp_param_count(q) == omlp.param_count(q)
+    assert lib.mcmc_mlp_param_count(8) == 0
+    h = ctypes.c_void_p()
+    assert lib.mcmc_mlp_create(8, 16, None, ctypes.byref(h)) == 1
+    assert lib.mcmc_mlp_create(16, 0, None, ctypes.byref(h)) == 1
+    assert lib.mcmc_mlp_create(16, 16, None, None) == 1
+    assert lib.mcmc_mlp_destroy(None) == 1
+    assert lib.mcmc_mlp_last_error(None) == b"null handle"
+    assert lib.mcmc_detect_mix_step(None, 1) == 1
+    assert lib.mcmc_detect_set_model(None, None, 0.5, 0) == 1
 
 
 def test_host_only_entry_points():
