@@ -114,7 +114,7 @@ def _kernel_hash(files):
 
 CHAIN_SOURCES = {
     "mixed": ["paper_2407_06042_gb300/csrc/chains_tc.cu", "paper_2407_06042_gb300/csrc/proposal.cuh",
-              "paper_2407_06042_gb300/csrc/common.cuh"],
+              "paper_2407_06042_gb300/csrc/common.cuh", "paper_2407_06042_gb300/csrc/tc_ptx.cuh"],
     "fp32": ["paper_2407_06042_gb300/csrc/chains_simt.cu", "paper_2407_06042_gb300/csrc/proposal.cuh",
              "paper_2407_06042_gb300/csrc/common.cuh"],
 }

@@ -27,10 +27,30 @@ def symbols(flat_states, nt, chains):
     return np.concatenate(out)
 
 
-def chain_samples(det: Detector, feature_times, label_time):
+def best_symbols(best_idx, nt, chains):
+    """Symbol indices kI * L + kQ of the detector's hard decision (complex Gray labels per
+    antenna), repeated for every chain in the row order of the detector's features."""
+    out = []
+    off = 0
+    for n_t, L in nt:
+        B = int(np.log2(L))
+        g = np.asarray(best_idx[off:off + n_t], np.int64) & 0xFF
+        lev = []
+        for part in (g >> B, g & (L - 1)):
+            k = part.copy()
+            k ^= k >> 1
+            k ^= k >> 2
+            lev.append(k)
+        out.append(np.tile(lev[0] * L + lev[1], chains))
+        off += n_t
+    return np.concatenate(out)
+
+
+def chain_samples(det: Detector, feature_times, label_time, *, label="chain"):
     """Training rows from the plain sampler on a freshly preprocessed detector: the features of
     every chain at each transition count in feature_times, and of x = 0 (one row per chain and
-    antenna), all labelled with the chain's symbol after label_time transitions.
+    antenna), all labelled after label_time transitions with the chain's own symbol
+    (label="chain") or with the symbol of the channel's best visited sample (label="best").
     Returns (X [rows x 6] float32 device tensor, labels int32 device tensor)."""
     import torch
     meta = det.batch_meta
@@ -44,8 +64,11 @@ def chain_samples(det: Detector, feature_times, label_time):
             t = tf
         feats.append(det.features())
     det.run_chains(label_time - t, t)
-    flat, _ = det.get_chains()
-    lab = symbols(flat, dims, chains)
+    if label == "best":
+        lab = best_symbols(det.estimate()["best_idx"], dims, chains)
+    else:
+        flat, _ = det.get_chains()
+        lab = symbols(flat, dims, chains)
     X0 = det.features(at_zero=True)
     # x = 0 rows, repeated for every chain of the channel (index map built on the host)
     rep, a0 = [], 0
@@ -82,6 +105,18 @@ def train(mlp: Mlp, X, labels, *, epochs=4, batch=4096, lr=1e-3, seed=0, log_eve
     return hist
 
 
+def hard_bits(best_idx, nt, qam):
+    """Bits of the hard decision: per antenna the complex Gray label's log2(Qc) bits, MSB first."""
+    out = []
+    off = 0
+    for n_t, q in zip(nt, qam):
+        B2 = int(np.log2(int(q)))
+        g = np.asarray(best_idx[off:off + int(n_t)], np.int64) & 0xFF
+        out.append(((g[:, None] >> np.arange(B2 - 1, -1, -1)) & 1).reshape(-1))
+        off += int(n_t)
+    return np.concatenate(out)
+
+
 def ber_curve(det: Detector, tx_bits, checkpoints, *, learned=False, period=0):
     """Uncoded BER of sign(LLR) and of the hard decision after each checkpoint transition count,
     running from a fresh state: uniform random initial states, or the network's warm start
@@ -99,8 +134,9 @@ def ber_curve(det: Detector, tx_bits, checkpoints, *, learned=False, period=0):
             det.run_chains(T - t, t)
         t = T
         r = det.estimate()
+        hb = hard_bits(r["best_idx"], det.batch_meta["nt"], det.batch_meta["qam"])
         out.append(dict(T=T, ber_llr=float(((r["llr"] < 0).astype(np.int64) != bits).mean()),
-                        best_idx=r["best_idx"]))
+                        ber_best=float((hb != bits).mean())))
     return out
 
 
