@@ -189,6 +189,9 @@ def load_batch(scale: float, rank: int, name: str = WORKLOAD):
     elif w["kind"] == "kronecker":
         n = max(1, int(round(w["total"] * scale)))
         b = workload.kronecker_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["rho"], w["seed"])
+    elif w["kind"] == "learned":
+        n = max(1, int(round(w["count"] * scale)))
+        b = workload.learned_eval_batch(w, n, 7 * rank)
     else:
         n = max(1, int(round(w["count"] * scale)))
         b = workload.uneven_batch(n, w["seed"])
@@ -257,8 +260,9 @@ def cpu_baseline(batch, w, budget_s: float, rank: int):
 
 def bench_config(args, w, n_channels, world, refresh, l2_note=None):
     """The configuration block shared by both arms of the benchmark."""
+    snr = w.get("snr_db", "U[%g,%g]" % tuple(w.get("snr_range", (10, 30))))
     cfg = {"workload": args.workload, "nt": w["nt"], "nr": w["nr"], "qam": w["qam"],
-           "snr_db": w.get("snr_db", "U[10,30]"), "channels": n_channels * world,
+           "snr_db": snr, "channels": n_channels * world,
            "chains": w["chains"], "iterations": w["iterations"], "preconditioned": True,
            "refresh_period": refresh, "parallelism": f"replicas x{world}"}
     if l2_note:
@@ -290,6 +294,162 @@ def run_reference(args, rank, world):
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_learned(args, w, batch, rank, world, dist, dev, pkg, torch):
+    """Learned-proposal workload: the network is trained (untimed) on plain-sampler samples by
+    the library's kernels; then the plain FP32 sampler runs `iterations` transitions to set the
+    reference BER, and the learned form (MIXED precision + network warm start) runs the fewest
+    transitions of the checkpoint list that reach that BER. value = the plain sampler's
+    chain-iterations to the reference BER, delivered per second by the learned form."""
+    from paper_2407_06042_gb300 import learned
+    tr = w["train"]
+    stream = torch.cuda.current_stream()
+    B, Np, T_ref = batch.n_channels, w["chains"], w["iterations"]
+
+    def upload(b):
+        return (torch.from_numpy(np.ascontiguousarray(b.H).view(np.float32).copy()).to(dev),
+                torch.from_numpy(np.ascontiguousarray(b.y).view(np.float32).copy()).to(dev),
+                torch.from_numpy(b.sigma2.astype(np.float32)).to(dev))
+
+    def det_of(b, chains, prec, seed=0):
+        return pkg.Detector(max_channels=b.n_channels, max_nt=int(b.nt.max()),
+                            max_nr=int(b.nr.max()), chains=chains, precision=prec, seed=seed,
+                            stream=stream)
+
+    # training (untimed): samples of the plain sampler, Adam in the library's kernels
+    t0 = time.perf_counter()
+    btr = workload.learned_train_batch(w, 7 * rank)
+    dtr = det_of(btr, tr["chains"], "mixed", seed=1)
+    Ht, yt, st = upload(btr)
+    dtr.preprocess(btr.nt, btr.nr, btr.qam, Ht, btr.H_off, yt, btr.y_off, st)
+    X, lab = learned.chain_samples(dtr, tr["feature_times"], tr["label_time"], label=tr["label"])
+    dtr.destroy()
+    mlp = pkg.Mlp(w["qam"], max_rows=tr["batch"])
+    mlp.set_params(learned.init_params(w["qam"], 0))
+    hist = learned.train(mlp, X, lab, epochs=tr["epochs"], batch=tr["batch"], lr=tr["lr"])
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    train_rows = int(X.shape[0])
+    del X, lab
+
+    Hd, yd, sd = upload(batch)
+    bits = batch.tx_bits
+    cps = sorted(set(w["checkpoints"]) | {T_ref})
+    d32 = det_of(batch, Np, "fp32")
+    dl = det_of(batch, Np, "mixed")
+    dl.set_model(mlp, 0.0, tensor_cores=True)
+    for d in (d32, dl):
+        d.preprocess(batch.nt, batch.nr, batch.qam, Hd, batch.H_off, yd, batch.y_off, sd)
+    plain = {c["T"]: c for c in learned.ber_curve(d32, bits, cps)}
+    lrn = {c["T"]: c for c in learned.ber_curve(dl, bits, cps, learned=True)}
+    ber_ref = plain[T_ref]["ber_llr"]
+    T_l = min([T for T in cps if lrn[T]["ber_llr"] <= ber_ref] or [T_ref])
+
+    n_ant = int(batch.nt.sum())
+    n_bits = int((batch.nt.astype(np.int64) * np.log2(batch.qam).astype(np.int64)).sum())
+    o_idx = torch.empty(n_ant, dtype=torch.int8, device=dev)
+    o_llr = torch.empty(n_bits, dtype=torch.float32, device=dev)
+    o_bf = torch.empty(B, dtype=torch.float64, device=dev)
+
+    def timed(det, T, warm):
+        def step():
+            det.preprocess(batch.nt, batch.nr, batch.qam, Hd, batch.H_off, yd, batch.y_off, sd)
+            if warm:
+                det.init_learned()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            det.run_chains(T)
+            b.record(stream)
+            det.estimate(o_idx, o_llr, o_bf, host_io=False)
+            return a, b
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        l0 = det.kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kev = []
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                kev.append(step())
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+        return ms, kms, det.kernel_launches() - l0, clk.summary()
+
+    ms_l, kms_l, launches, clocks = timed(dl, T_l, True)
+    ms_32, kms_32, _, _ = timed(d32, T_ref, False)
+
+    # the tensor-core network on the mixture move's row count (every chain and antenna), alone
+    rows = B * Np * int(batch.nt.max())
+    Xr = dl.features()
+    logits = torch.empty((rows, w["qam"]), dtype=torch.float32, device=dev)
+    mlp.forward(Xr, logits, tensor_cores=True)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record(stream)
+    for _ in range(reps):
+        mlp.forward(Xr, logits, tensor_cores=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    mlp_ms = a.elapsed_time(b) / reps
+    H_ = 256
+    fpr = 2 * (6 * H_ + H_ * H_ + H_ * w["qam"])
+    mlp_tf = rows * fpr / (mlp_ms * 1e-3) / 1e12
+    del Xr, logits
+
+    value = B * Np * T_ref * world / (ms_l * 1e-3)
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = cpu_baseline(batch, w, args.cpu_seconds, rank)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_l,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16x2+f32", "data": "synthetic",
+                "config": bench_config(args, w, B, world, 0,
+                                       "inputs larger than L2 (H = %d MB)" % (Hd.numel() * 4 // 2**20)),
+                "value_definition": "plain-sampler chain-iterations to the reference BER "
+                                    "(B x Np x iterations) per second of the learned form",
+                "precision": "mixed", "detections_per_s": B * world / (ms_l * 1e-3),
+                "chain_kernel_ms": kms_l, "clocks": clocks, "gpu_launches": int(launches),
+                "roofline": chain_roofline("mixed", w, B * Np * T_l, kms_l, batch),
+                "learned": {
+                    "train_rows": train_rows, "train_seconds": train_s,
+                    "train_loss": [round(x, 4) for x in hist],
+                    "checkpoints": cps,
+                    "ber_plain_fp32": [plain[T]["ber_llr"] for T in cps],
+                    "ber_learned_warm_start": [lrn[T]["ber_llr"] for T in cps],
+                    "reference_iterations": T_ref, "reference_ber": ber_ref,
+                    "learned_iterations": T_l,
+                    "ms_per_step_learned": ms_l, "ms_per_step_plain_fp32": ms_32,
+                    "speedup_vs_plain_fp32_at_equal_ber": ms_32 / ms_l,
+                    "mlp_tensor_roofline": {
+                        "bound": "tensor", "rows": rows, "ms": mlp_ms,
+                        "achieved": mlp_tf, "peak": 1899.4, "unit": "TFLOP/s",
+                        "frac": mlp_tf / 1899.4,
+                        "per_unit": f"{fpr} flops per row (6x256 + 256x256 + 256x{w['qam']} MACs)",
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)"}},
+                "e2e": None, "cpu_baseline": cb}
+        print(json.dumps(line), flush=True)
+    for d in (d32, dl):
+        d.destroy()
+    mlp.destroy()
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -328,6 +488,8 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     batch, w = load_batch(args.scale, rank, args.workload)
+    if w["kind"] == "learned":
+        return run_learned(args, w, batch, rank, world, dist, dev, pkg, torch)
     T, Np = w["iterations"], w["chains"]
     B = batch.n_channels
     refresh = args.refresh if args.refresh is not None else (50 if w["kind"] == "kronecker" else 0)

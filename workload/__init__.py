@@ -223,6 +223,16 @@ WORKLOADS = {
     "kronecker_128x128_64qam": dict(kind="kronecker", nt=128, nr=128, qam=64,
                                     snr_db=[26.0, 28.0, 30.0, 32.0, 34.0], total=1024, rho=0.5,
                                     chains=256, iterations=300, seed=1004),
+    # Learned proposal: evaluation on 64x64 16-QAM Rayleigh, SNR U[12,24] dB, 8192 channels,
+    # 64 chains, the plain sampler's reference at 40 iterations; the network is trained on plain-
+    # sampler samples of 32x32 16-QAM Rayleigh at SNR U[12,24] dB (512 channels x 16 chains,
+    # features at 7 points of each chain: ~1.8M rows).
+    "learned_64x64_16qam": dict(kind="learned", nt=64, nr=64, qam=16, snr_range=(12.0, 24.0),
+                                count=8192, chains=64, iterations=40, seed=1005,
+                                checkpoints=[1, 2, 5, 10, 20, 40],
+                                train=dict(nt=32, nr=32, channels=512, chains=16,
+                                           feature_times=[0, 2, 5, 10, 20, 40], label_time=200,
+                                           label="best", epochs=8, batch=4096, lr=1e-3)),
 }
 
 
@@ -238,4 +248,23 @@ def workload(name: str, scale: float = 1.0) -> Batch:
     if w["kind"] == "uneven":
         n = max(1, int(round(w["count"] * scale)))
         return uneven_batch(n, w["seed"])
+    if w["kind"] == "learned":
+        n = max(1, int(round(w["count"] * scale)))
+        return learned_eval_batch(w, n)
     raise KeyError(name)
+
+
+def learned_eval_batch(w: dict, n: int, seed_offset: int = 0) -> Batch:
+    """Evaluation channels of a learned-proposal workload (SNR uniform in its range)."""
+    rng = np.random.default_rng(w["seed"] + seed_offset)
+    snr = rng.uniform(w["snr_range"][0], w["snr_range"][1], n)
+    return generate([(w["nt"], w["nr"], w["qam"], float(s)) for s in snr], w["seed"] + seed_offset)
+
+
+def learned_train_batch(w: dict, seed_offset: int = 0) -> Batch:
+    """Training channels of a learned-proposal workload."""
+    t = w["train"]
+    rng = np.random.default_rng(w["seed"] + 500 + seed_offset)
+    snr = rng.uniform(w["snr_range"][0], w["snr_range"][1], t["channels"])
+    return generate([(t["nt"], t["nr"], w["qam"], float(s)) for s in snr],
+                    w["seed"] + 500 + seed_offset)
