@@ -110,10 +110,11 @@ struct TcCtx {
     uint32_t mma_phase;
 };
 
-// Issue the MMAs of one transition (thread 0) and wait for them (everyone). Returns false on a
-// bounded-wait expiry of this thread's wait; callers combine the verdicts in a CTA-wide vote.
+// Issue the MMAs of one transition (thread 0, after a CTA barrier that publishes the B operand)
+// and, separately, wait for them (everyone). The wait returns false on a bounded-wait expiry of
+// this thread's wait; callers combine the verdicts in a CTA-wide vote.
 template <int MT>
-__device__ __forceinline__ bool tc_gemm(TcCtx &x)
+__device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -138,10 +139,14 @@ __device__ __forceinline__ bool tc_gemm(TcCtx &x)
                 x.bar_mma)
             : "memory");
     }
+}
+
+__device__ __forceinline__ bool tc_gemm_wait(TcCtx &x)
+{
     const bool ok = mbar_wait(x.bar_mma, x.mma_phase);
     x.mma_phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return ok;   // the caller folds it into its next CTA-wide vote
+    return ok;
 }
 
 // TMEM -> registers: Gt x (g) and P~ Gt x (m) of this thread's dimension for its 8 chains.
@@ -162,11 +167,6 @@ __device__ __forceinline__ void tc_read(const TcCtx &x, float (&g)[MT][4], float
     }
 }
 
-// BF16 bits of a small odd integer (exact: the float has at most 4 significant bits).
-__device__ __forceinline__ unsigned short bf16_bits_of_int(int v)
-{
-    return (unsigned short)(__float_as_uint((float)v) >> 16);
-}
 
 // One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
 // every chain column is live, so no per-(dimension, chain) validity test is needed. Levels are
@@ -186,8 +186,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     float zt[MT], wt[MT];
     int nd[MT];
     bool live[MT][4];
-    float k[MT][4];
-    float Dg[MT][4], sl[MT][4];                    // Gt x and the slope (log2 units)
+    // per (tile, chain pair): levels, Gt x and the drift slope (log2 units), as packed pairs
+    uint64_t k2[MT][2], Dg2[MT][2], sl2[MT][2];
     int8_t *skb = x.skb;                           // best visited states [C][kMaxN]
     const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
     const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
@@ -201,18 +201,20 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         wt[t] = v ? gw[n] : 0.f;
         boff[t] = (uint32_t)(cbase >> 3) * x.sbo_b + (uint32_t)(n >> 3) * b_lbo() +
                   (uint32_t)(cbase & 7) * 16u + (uint32_t)(n & 7) * 2u;
+        float kv[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = cbase + j;
             live[t][j] = FULL || (v && c < nC);
-            float kv = 0.f;
+            kv[j] = 0.f;
             if (live[t][j]) {
                 const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
-                kv = (float)A.states[e];
+                kv[j] = (float)A.states[e];
                 skb[c * kMaxN + n] = A.best_states[e];
             }
-            k[t][j] = kv;
         }
+        k2[t][0] = f2_pack(kv[0], kv[1]);
+        k2[t][1] = f2_pack(kv[2], kv[3]);
     }
     double fcur = 0.0, fbest = 0.0;
     unsigned cnt = 0;
@@ -221,23 +223,35 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         fcur = A.f[ci];
         fbest = A.best_f[ci];
     }
+    const uint64_t two2 = f2_splat(2.f), mlm1 = f2_splat(-lm1), mone = f2_splat(-1.f);
     // x as BF16 into the B operand: bits of the exact float 2k - (L-1); dead slots write 0
-    auto write_b = [&](const float (&kk)[MT][4]) {
+    auto write_b = [&](const uint64_t (&kk)[MT][2]) {
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             if (!FULL && nd[t] >= x.Kp) continue;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (!FULL && cbase + j >= C) continue;
-                const float xv = live[t][j] ? fmaf(2.f, kk[t][j], -lm1) : 0.f;
-                *reinterpret_cast<unsigned short *>(x.sB + boff[t] + 16u * j) =
-                    (unsigned short)(__float_as_uint(xv) >> 16);
+            for (int p = 0; p < 2; ++p) {
+                float xv[2];
+                f2_unpack(f2_fma(two2, kk[t][p], mlm1), xv[0], xv[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * p + h;
+                    if (!FULL && cbase + j >= C) continue;
+                    const float v = live[t][j] ? xv[h] : 0.f;
+                    *reinterpret_cast<unsigned short *>(x.sB + boff[t] + 16u * j) =
+                        (unsigned short)(__float_as_uint(v) >> 16);
+                }
             }
         }
     };
-    write_b(k);
+    // slope of a state from its products (log2 units): c_lin (w~ - P~Gt x) or c_lin (z~ - Gt x)
+    auto slope2 = [&](int t, uint64_t g, uint64_t m) {
+        return f2_mul(f2_splat(a2s), f2_fma(mone, pre ? m : g, f2_splat(pre ? wt[t] : zt[t])));
+    };
+    write_b(k2);
     if (alive) {
-        const bool ok = tc_gemm<MT>(x);
+        tc_gemm_issue<MT>(x);
+        const bool ok = tc_gemm_wait(x);
         if (__syncthreads_or(!ok)) { alive = false; set_status(A.status, kStatusTimeout); }
     }
     {
@@ -246,9 +260,11 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
 #pragma unroll
         for (int t = 0; t < MT; ++t)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                Dg[t][j] = alive ? g[t][j] : 0.f;
-                sl[t][j] = alive ? a2s * (pre ? (wt[t] - m[t][j]) : (zt[t] - g[t][j])) : 0.f;
+            for (int p = 0; p < 2; ++p) {
+                const uint64_t gg = alive ? f2_pack(g[t][2 * p], g[t][2 * p + 1]) : 0ull;
+                const uint64_t mm = alive ? f2_pack(m[t][2 * p], m[t][2 * p + 1]) : 0ull;
+                Dg2[t][p] = gg;
+                sl2[t][p] = alive ? slope2(t, gg, mm) : 0ull;
             }
     }
     if (A.init_f && alive) {
@@ -259,13 +275,18 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         for (int j = 0; j < 4; ++j) { lin[j] = 0.f; quad[j] = 0.f; }
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
+            float kv[4], dg[4];
+            f2_unpack(k2[t][0], kv[0], kv[1]);
+            f2_unpack(k2[t][1], kv[2], kv[3]);
+            f2_unpack(Dg2[t][0], dg[0], dg[1]);
+            f2_unpack(Dg2[t][1], dg[2], dg[3]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!live[t][j]) continue;
-                const float xn = fmaf(2.f, k[t][j], -lm1);
+                const float xn = fmaf(2.f, kv[j], -lm1);
                 lin[j] = fmaf(xn, zt[t], lin[j]);
-                quad[j] = fmaf(xn, Dg[t][j], quad[j]);
-                skb[(cbase + j) * kMaxN + nd[t]] = (int8_t)k[t][j];
+                quad[j] = fmaf(xn, dg[j], quad[j]);
+                skb[(cbase + j) * kMaxN + nd[t]] = (int8_t)kv[j];
             }
         }
         const float rl = reduce_scatter16(lin, x.dl);
@@ -288,10 +309,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
 
     for (int i = 0; i < A.iterations && alive; ++i) {
         const uint32_t t_it = (uint32_t)(A.t_offset + 1 + i);
-        float part[4], dpart[4];
-        float kp[MT][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) { part[j] = 0.f; dpart[j] = 0.f; }
+        uint64_t part2[2] = {0ull, 0ull}, dpart2[2] = {0ull, 0ull};
+        uint64_t kp2[MT][2];
         // 1. proposal draw (log2 q(x'|x) accumulated with a minus sign)
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
@@ -301,35 +320,75 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 w = philox4x32_10(t_it, (uint32_t)n, (uint32_t)it.b,
                                   (uint32_t)((it.c0 + cbase) >> 2), A.key0, A.key1);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float sel = k[t][j];
-                if (live[t][j]) {
-                    float lq;
-                    sel = factor_draw_f<L>(sl[t][j], c2, inv2c, k[t][j], uniform_f(word_of(w, j)), lq);
-                    part[j] -= lq;
+            for (int p = 0; p < 2; ++p) {
+                uint64_t sel, lq;
+                factor_draw_f2<L>(sl2[t][p], c2, inv2c, k2[t][p], uniform_f(word_of(w, 2 * p)),
+                                  uniform_f(word_of(w, 2 * p + 1)), sel, lq);
+                if (!FULL) {
+                    float s[2], kk[2], q[2];
+                    f2_unpack(sel, s[0], s[1]);
+                    f2_unpack(k2[t][p], kk[0], kk[1]);
+                    f2_unpack(lq, q[0], q[1]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (!live[t][2 * p + h]) { s[h] = kk[h]; q[h] = 0.f; }
+                    sel = f2_pack(s[0], s[1]);
+                    lq = f2_pack(q[0], q[1]);
                 }
-                kp[t][j] = sel;
+                kp2[t][p] = sel;
+                part2[p] = f2_fma(mone, lq, part2[p]);
             }
         }
-        write_b(kp);
-        // 2. D' = A X'^T on the tensor core (the timeout verdict joins the next CTA barrier)
-        const bool mma_ok = tc_gemm<MT>(x);
+        write_b(kp2);
+        // 2. D' = A X'^T on the tensor core; while it runs, the chains' acceptance uniforms
+        //    (the timeout verdict joins the next CTA barrier)
+        tc_gemm_issue<MT>(x);
+        float logu = 0.f;
+        if (x.tid < nC) {
+            const int cc = it.c0 + x.tid;
+            const U4 w = philox4x32_10(t_it, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
+                                       A.key0, A.key1);
+            logu = lg2_approx(uniform_f(word_of(w, cc & 3)));
+        }
+        const bool mma_ok = tc_gemm_wait(x);
         // 3. reverse factor and energy difference
         float gp[MT][4], mp[MT][4];
         tc_read<MT>(x, gp, mp);
+        uint64_t gp2[MT][2], sp2[MT][2];
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
+            const uint64_t z2 = f2_splat(2.f * zt[t]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float ap = a2s * (pre ? (wt[t] - mp[t][j]) : (zt[t] - gp[t][j]));
-                mp[t][j] = ap;   // slope of x', kept for the update
-                if (live[t][j]) {
-                    part[j] += factor_log2q_f<L>(ap, c2, inv2c, kp[t][j], k[t][j]);
-                    dpart[j] = fmaf(2.f * (kp[t][j] - k[t][j]), 2.f * zt[t] - Dg[t][j] - gp[t][j], dpart[j]);
+            for (int p = 0; p < 2; ++p) {
+                const uint64_t gg = f2_pack(gp[t][2 * p], gp[t][2 * p + 1]);
+                const uint64_t ap = slope2(t, gg, f2_pack(mp[t][2 * p], mp[t][2 * p + 1]));
+                gp2[t][p] = gg;
+                sp2[t][p] = ap;   // slope of x', kept for the update
+                uint64_t lr = factor_log2q_f2<L>(ap, c2, inv2c, kp2[t][p], k2[t][p]);
+                // (x'_n - x_n)(2 zt_n - (Gt x)_n - (Gt x')_n), the levels' difference doubled
+                const uint64_t dk = f2_mul(two2, f2_fma(mone, k2[t][p], kp2[t][p]));
+                const uint64_t e = f2_fma(mone, gg, f2_fma(mone, Dg2[t][p], z2));
+                uint64_t dd = f2_mul(dk, e);
+                if (!FULL) {
+                    float a[2], b[2];
+                    f2_unpack(lr, a[0], a[1]);
+                    f2_unpack(dd, b[0], b[1]);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (!live[t][2 * p + h]) { a[h] = 0.f; b[h] = 0.f; }
+                    lr = f2_pack(a[0], a[1]);
+                    dd = f2_pack(b[0], b[1]);
                 }
+                part2[p] = f2_add(part2[p], lr);
+                dpart2[p] = f2_add(dpart2[p], dd);
             }
         }
         // 4. per-chain reduction and the MH decision (log2 units)
+        float part[4], dpart[4];
+        f2_unpack(part2[0], part[0], part[1]);
+        f2_unpack(part2[1], part[2], part[3]);
+        f2_unpack(dpart2[0], dpart[0], dpart[1]);
+        f2_unpack(dpart2[1], dpart[2], dpart[3]);
         const float rs = reduce_scatter16(part, x.dl);
         const float rd = reduce_scatter16(dpart, x.dl);
         if ((x.dl & 3) == 0) {
@@ -343,12 +402,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             const int c = x.tid;
             const float s = x.red[c] + x.red[C + c] + x.red[2 * C + c] + x.red[3 * C + c];
             const float sd = x.dred[c] + x.dred[C + c] + x.dred[2 * C + c] + x.dred[3 * C + c];
-            const int cc = it.c0 + c;
-            const U4 w = philox4x32_10(t_it, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
-                                       A.key0, A.key1);
             const float logr = fmaf(cf2, sd, s);
             const float loga = logr < 0.f ? logr : 0.f;
-            const float logu = lg2_approx(uniform_f(word_of(w, cc & 3)));
             int ok = logu < loga;
             if (!isfinite(logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
             int im = 0;
@@ -362,25 +417,46 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         __syncthreads();
         // 5. accepted chains take x' and its caches
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = cbase + j;
-            const int fl = (FULL || c < nC) ? x.sacc[c] : 0;
-            const bool ok = fl & 1, im = fl & 2;
+        for (int p = 0; p < 2; ++p) {
+            int fl[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = cbase + 2 * p + h;
+                fl[h] = (FULL || c < nC) ? x.sacc[c] : 0;
+            }
 #pragma unroll
             for (int t = 0; t < MT; ++t) {
-                k[t][j] = ok ? kp[t][j] : k[t][j];
-                Dg[t][j] = ok ? gp[t][j] : Dg[t][j];
-                sl[t][j] = ok ? mp[t][j] : sl[t][j];
-                if (im && live[t][j]) skb[c * kMaxN + nd[t]] = (int8_t)kp[t][j];
+                float ka[2], kb[2], da[2], db[2], sa[2], sb[2];
+                f2_unpack(k2[t][p], ka[0], ka[1]);
+                f2_unpack(kp2[t][p], kb[0], kb[1]);
+                f2_unpack(Dg2[t][p], da[0], da[1]);
+                f2_unpack(gp2[t][p], db[0], db[1]);
+                f2_unpack(sl2[t][p], sa[0], sa[1]);
+                f2_unpack(sp2[t][p], sb[0], sb[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const bool ok = fl[h] & 1, im = fl[h] & 2;
+                    ka[h] = ok ? kb[h] : ka[h];
+                    da[h] = ok ? db[h] : da[h];
+                    sa[h] = ok ? sb[h] : sa[h];
+                    if (im && live[t][2 * p + h]) skb[(cbase + 2 * p + h) * kMaxN + nd[t]] = (int8_t)kb[h];
+                }
+                k2[t][p] = f2_pack(ka[0], ka[1]);
+                Dg2[t][p] = f2_pack(da[0], da[1]);
+                sl2[t][p] = f2_pack(sa[0], sa[1]);
             }
         }
         // periodic FP64 refresh of the tracked energies (decisions never read them)
         if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
 #pragma unroll
-            for (int t = 0; t < MT; ++t)
+            for (int t = 0; t < MT; ++t) {
+                float kv[4];
+                f2_unpack(k2[t][0], kv[0], kv[1]);
+                f2_unpack(k2[t][1], kv[2], kv[3]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (live[t][j]) x.sfs[(cbase + j) * kMaxN + nd[t]] = (int8_t)k[t][j];
+                    if (live[t][j]) x.sfs[(cbase + j) * kMaxN + nd[t]] = (int8_t)kv[j];
+            }
             __syncthreads();
             const double *G = A.G64 + d.mat_off;
             const double *z = A.z64 + d.vec_off;
@@ -412,13 +488,18 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     // write back this work item
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
+        float kv[4], dg[4];
+        f2_unpack(k2[t][0], kv[0], kv[1]);
+        f2_unpack(k2[t][1], kv[2], kv[3]);
+        f2_unpack(Dg2[t][0], dg[0], dg[1]);
+        f2_unpack(Dg2[t][1], dg[2], dg[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!live[t][j]) continue;
             const long long e = d.state_off + (long long)(it.c0 + cbase + j) * N + nd[t];
-            A.states[e] = (int8_t)k[t][j];
+            A.states[e] = (int8_t)kv[j];
             A.best_states[e] = skb[(cbase + j) * kMaxN + nd[t]];
-            if (A.dexp) A.dexp[e] = Dg[t][j];
+            if (A.dexp) A.dexp[e] = dg[j];
         }
     }
     if (x.tid < nC) {

@@ -157,4 +157,125 @@ __device__ __forceinline__ float factor_log2q_f(float a2, float c2, float inv2c,
     return rel_logit2(p, c2, jf) - lg2_approx(S[L - 1]);
 }
 
+// ------------------------------------------------------------------------------------------
+// Two chains per instruction: the same arithmetic on packed FP32 pairs (sm_100+ f32x2 add / mul
+// / fma, each lane rounded like its scalar counterpart), so a pair's results are bit-identical
+// to two scalar evaluations. A pair lives in one 64-bit register (low word = first chain).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t f2_pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2_splat(float a) { return f2_pack(a, a); }
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Vertex levels and relative-logit polynomials of two factors (as vertex_level / rel_poly).
+template <int L>
+struct Poly2 {
+    uint64_t B, C0;
+};
+
+template <int L>
+__device__ __forceinline__ Poly2<L> rel_poly2(uint64_t a2, float c2, float inv2c, uint64_t kf)
+{
+    float v0, v1;
+    f2_unpack(f2_fma(a2, f2_splat(inv2c), kf), v0, v1);
+    const float js0 = fminf(fmaxf(rintf(v0), 0.f), (float)(L - 1));
+    const float js1 = fminf(fmaxf(rintf(v1), 0.f), (float)(L - 1));
+    const uint64_t js = f2_pack(js0, js1);
+    const uint64_t P = f2_fma(f2_splat(-c2), f2_fma(f2_splat(-2.f), kf, js), a2);
+    return Poly2<L>{f2_fma(f2_splat(c2), js, P), f2_mul(f2_pack(-js0, -js1), P)};
+}
+
+template <int L>
+__device__ __forceinline__ uint64_t rel_logit2_2(const Poly2<L> &p, uint64_t mc2, uint64_t jf)
+{
+    return f2_fma(f2_fma(mc2, jf, p.B), jf, p.C0);
+}
+
+// factor_draw_f for two chains: levels (as floats) and log2 q of the drawn levels.
+template <int L>
+__device__ __forceinline__ void factor_draw_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
+                                               float u0, float u1, uint64_t &sel, uint64_t &log2q)
+{
+    const Poly2<L> p = rel_poly2<L>(a2, c2, inv2c, kf);
+    const uint64_t mc2 = f2_splat(-c2);
+    float S0[L], S1[L];
+    uint64_t acc = 0ull;   // (+0.f, +0.f)
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        float l0, l1;
+        f2_unpack(rel_logit2_2(p, mc2, f2_splat((float)j)), l0, l1);
+        acc = f2_add(acc, f2_pack(ex2_approx(l0), ex2_approx(l1)));
+        f2_unpack(acc, S0[j], S1[j]);
+    }
+    float t0, t1;
+    f2_unpack(f2_mul(f2_pack(u0, u1), f2_pack(S0[L - 1], S1[L - 1])), t0, t1);
+    float s0, s1;
+    if constexpr (L == 2) {
+        s0 = S0[0] <= t0 ? 1.f : 0.f;
+        s1 = S1[0] <= t1 ? 1.f : 0.f;
+    } else if constexpr (L == 4) {
+        const bool a1 = S0[1] <= t0, b1 = S1[1] <= t1;
+        const bool a0 = (a1 ? S0[2] : S0[0]) <= t0, b0 = (b1 ? S1[2] : S1[0]) <= t1;
+        s0 = (a1 ? 2.f : 0.f) + (a0 ? 1.f : 0.f);
+        s1 = (b1 ? 2.f : 0.f) + (b0 ? 1.f : 0.f);
+    } else {
+        const bool a2b = S0[3] <= t0, b2b = S1[3] <= t1;
+        const bool a1 = (a2b ? S0[5] : S0[1]) <= t0, b1 = (b2b ? S1[5] : S1[1]) <= t1;
+        const float ma = a2b ? (a1 ? S0[6] : S0[4]) : (a1 ? S0[2] : S0[0]);
+        const float mb = b2b ? (b1 ? S1[6] : S1[4]) : (b1 ? S1[2] : S1[0]);
+        const bool a0 = ma <= t0, b0 = mb <= t1;
+        s0 = (a2b ? 4.f : 0.f) + (a1 ? 2.f : 0.f) + (a0 ? 1.f : 0.f);
+        s1 = (b2b ? 4.f : 0.f) + (b1 ? 2.f : 0.f) + (b0 ? 1.f : 0.f);
+    }
+    sel = f2_pack(s0, s1);
+    float r0, r1;
+    f2_unpack(rel_logit2_2(p, mc2, sel), r0, r1);
+    log2q = f2_pack(r0 - lg2_approx(S0[L - 1]), r1 - lg2_approx(S1[L - 1]));
+}
+
+// factor_log2q_f for two chains: log2 q(j_eval | level k) of each.
+template <int L>
+__device__ __forceinline__ uint64_t factor_log2q_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
+                                                    uint64_t jf)
+{
+    const Poly2<L> p = rel_poly2<L>(a2, c2, inv2c, kf);
+    const uint64_t mc2 = f2_splat(-c2);
+    uint64_t acc = 0ull;
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        float l0, l1;
+        f2_unpack(rel_logit2_2(p, mc2, f2_splat((float)j)), l0, l1);
+        acc = f2_add(acc, f2_pack(ex2_approx(l0), ex2_approx(l1)));
+    }
+    float S0, S1, r0, r1;
+    f2_unpack(acc, S0, S1);
+    f2_unpack(rel_logit2_2(p, mc2, jf), r0, r1);
+    return f2_pack(r0 - lg2_approx(S0), r1 - lg2_approx(S1));
+}
+
 }  // namespace mcmcdet
