@@ -297,14 +297,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Small weights travel in the kernel's parameter block (constant bank): the CUDA-core layers read
+// them as direct FMA operands. W2 and W3 are the BF16 operand images in global memory.
+template <int Q>
 struct MlpTcArgs {
     long long rows;
     const float *X;
-    const float *params;
     const uint8_t *ops;
     float *logits;
-    int Q, Qp;
     unsigned *status;
+    float W1[kMlpHidden * kMlpIn];
+    float b1[kMlpHidden];
+    float b2[kMlpHidden];
+    float b3[Q];
 };
 
 // Issue K = 256 worth of MMAs (16 x K16) from the A image at sa and the B image at sb into
@@ -322,13 +327,91 @@ __device__ __forceinline__ void mlp_issue(uint32_t tmem_d, uint32_t sa, uint32_t
         : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) mlp_tc_kernel(MlpTcArgs a)
+// The CUDA-core parts of one 128-row tile for one half of the hidden units / logits (HALF_ID a
+// compile-time constant, so every weight is a direct constant-bank operand).
+template <int Q, int HALF_ID>
+__device__ __forceinline__ void mlp_layer1(const MlpTcArgs<Q> &a, const float (&x)[kMlpIn],
+                                           unsigned char *hrow)
 {
+    constexpr int HALF = kMlpHidden / 2;
+#pragma unroll
+    for (int c = 0; c < HALF / 8; ++c) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int u = HALF * HALF_ID + 8 * c + 2 * j + h;
+                float s = a.b1[u];
+#pragma unroll
+                for (int q = 0; q < kMlpIn; ++q) s = fmaf(a.W1[u * kMlpIn + q], x[q], s);
+                v[h] = fmaxf(s, 0.f);
+            }
+            pk[j] = pack_bf16(v[0], v[1]);
+        }
+        *reinterpret_cast<uint4 *>(hrow + c * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+template <int Q, int HALF_ID>
+__device__ __forceinline__ void mlp_epilogue2(const MlpTcArgs<Q> &a, uint32_t lane_base,
+                                              unsigned char *hrow)
+{
+    constexpr int HALF = kMlpHidden / 2;
+#pragma unroll
+    for (int c4 = 0; c4 < HALF / 32; ++c4) {
+        float v[32];
+        tmem_ld32(lane_base + (uint32_t)(HALF * HALF_ID + 32 * c4), v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int u = HALF * HALF_ID + 32 * c4 + 8 * c + 2 * j;
+                pk[j] = pack_bf16(fmaxf(v[8 * c + 2 * j] + a.b2[u], 0.f),
+                                  fmaxf(v[8 * c + 2 * j + 1] + a.b2[u + 1], 0.f));
+            }
+            *reinterpret_cast<uint4 *>(hrow + (4 * c4 + c) * 128) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+}
+
+template <int Q, int HALF_ID>
+__device__ __forceinline__ void mlp_epilogue3(const MlpTcArgs<Q> &a, uint32_t lane_base,
+                                              long long r)
+{
+    constexpr int Qp = (Q + 15) / 16 * 16;
+    constexpr int base = (Qp / 2) * HALF_ID;
+#pragma unroll
+    for (int c = 0; c < Qp / 16; ++c) {
+        float v[8];
+        tmem_ld8(lane_base + (uint32_t)(kMlpHidden + base + 8 * c), v);
+        if (r < a.rows) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int n = base + 8 * c + j;
+                if (n < Q) a.logits[r * Q + n] = v[j] + a.b3[n < Q ? n : 0];
+            }
+        }
+    }
+}
+
+// 256 threads: warps w and w + 4 own the rows of TMEM lane quadrant w % 4 and split each row's
+// hidden units (and logits) in halves.
+template <int Q>
+__global__ void __launch_bounds__(256, 1) mlp_tc_kernel(const __grid_constant__ MlpTcArgs<Q> a)
+{
+    constexpr int Qp = (Q + 15) / 16 * 16;
+    constexpr int HALF = kMlpHidden / 2;
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, half = warp >> 2;
+    const int row_l = 32 * quad + lane;            // row of the tile (TMEM lane)
     unsigned char *sW2 = smem;
     unsigned char *sW3 = smem + kW2Bytes;
-    unsigned char *sH = sW3 + (uint32_t)a.Qp * 512u;
+    unsigned char *sH = sW3 + (uint32_t)Qp * 512u;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sH + kHBytes);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
     const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
@@ -349,7 +432,7 @@ __global__ void __launch_bounds__(128, 1) mlp_tc_kernel(MlpTcArgs a)
     const uint32_t tmem = *tslot;
 
     // W2 and W3 images: one bulk copy per CTA
-    const uint32_t wbytes = kW2Bytes + (uint32_t)a.Qp * 512u;
+    const uint32_t wbytes = kW2Bytes + (uint32_t)Qp * 512u;
     if (tid == 0) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld),
                      "r"(wbytes)
@@ -367,47 +450,36 @@ __global__ void __launch_bounds__(128, 1) mlp_tc_kernel(MlpTcArgs a)
     bool alive = !__syncthreads_or(!mbar_wait(bar_ld, 0));
     if (!alive && tid == 0) set_status(a.status, kStatusTimeout);
 
-    const float *W1 = a.params;
-    const float *b1 = a.params + mlp_off_b1();
-    const float *b2 = a.params + mlp_off_b2();
-    const float *b3 = a.params + mlp_off_b3(a.Q);
     const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMlpHidden >> 3) << 17) |
                             ((uint32_t)(128 >> 4) << 24);
-    const uint32_t idesc3 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a.Qp >> 3) << 17) |
+    const uint32_t idesc3 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Qp >> 3) << 17) |
                             ((uint32_t)(128 >> 4) << 24);
     const uint32_t sa = smem_u32(sH), sb2 = smem_u32(sW2), sb3 = smem_u32(sW3);
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    unsigned char *hrow = sH + core_off(tid, 0);
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
+    unsigned char *hrow = sH + core_off(row_l, HALF * half);
     uint32_t phase = 0;
     const long long ntiles = (a.rows + 127) / 128;
 
+    float x[kMlpIn];
+    {
+        const long long r0 = (long long)blockIdx.x * 128 + row_l;
+#pragma unroll
+        for (int j = 0; j < kMlpIn; ++j) x[j] = r0 < a.rows ? a.X[r0 * kMlpIn + j] : 0.f;
+    }
     for (long long tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
-        const long long r = tile * 128 + tid;
-        float x[kMlpIn];
-#pragma unroll
-        for (int j = 0; j < kMlpIn; ++j) x[j] = r < a.rows ? a.X[r * kMlpIn + j] : 0.f;
-        // layer 1 on the CUDA cores -> BF16 A operand (this thread's row)
-        for (int c = 0; c < kMlpHidden / 8; ++c) {
-            uint32_t pk[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float v[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int u = 8 * c + 2 * j + h;
-                    float s = __ldg(b1 + u);
-#pragma unroll
-                    for (int q = 0; q < kMlpIn; ++q) s = fmaf(__ldg(W1 + u * kMlpIn + q), x[q], s);
-                    v[h] = fmaxf(s, 0.f);
-                }
-                pk[j] = pack_bf16(v[0], v[1]);
-            }
-            *reinterpret_cast<uint4 *>(hrow + c * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
+        const long long r = tile * 128 + row_l;
+        // layer 1 on the CUDA cores (this thread's half of the hidden units) -> BF16 A operand
+        if (half == 0) mlp_layer1<Q, 0>(a, x, hrow);
+        else mlp_layer1<Q, 1>(a, x, hrow);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (tid == 0) mlp_issue(tmem, sa, sb2, idesc2, bar_mma);
+        {   // the next tile's features, loaded while the MMAs run
+            const long long rn = (tile + gridDim.x) * 128 + row_l;
+#pragma unroll
+            for (int j = 0; j < kMlpIn; ++j) x[j] = rn < a.rows ? a.X[rn * kMlpIn + j] : 0.f;
+        }
         bool ok = mbar_wait(bar_mma, phase);
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -416,23 +488,9 @@ __global__ void __launch_bounds__(128, 1) mlp_tc_kernel(MlpTcArgs a)
             if (tid == 0) set_status(a.status, kStatusTimeout);
             break;
         }
-        // layer 2 epilogue: + b2, ReLU, BF16 -> A operand (MMAs above have completed)
-        for (int c4 = 0; c4 < kMlpHidden / 32; ++c4) {
-            float v[32];
-            tmem_ld32(lane_base + 32u * c4, v);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                uint32_t pk[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int u = 32 * c4 + 8 * c + 2 * j;
-                    pk[j] = pack_bf16(fmaxf(v[8 * c + 2 * j] + __ldg(b2 + u), 0.f),
-                                      fmaxf(v[8 * c + 2 * j + 1] + __ldg(b2 + u + 1), 0.f));
-                }
-                *reinterpret_cast<uint4 *>(hrow + (4 * c4 + c) * 128) =
-                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            }
-        }
+        // layer 2 epilogue (this thread's half of the columns): + b2, ReLU, BF16 -> A operand
+        if (half == 0) mlp_epilogue2<Q, 0>(a, lane_base, hrow);
+        else mlp_epilogue2<Q, 1>(a, lane_base, hrow);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -445,18 +503,9 @@ __global__ void __launch_bounds__(128, 1) mlp_tc_kernel(MlpTcArgs a)
             if (tid == 0) set_status(a.status, kStatusTimeout);
             break;
         }
-        // layer 3 epilogue: + b3 -> logits
-        for (int c = 0; c < a.Qp / 8; ++c) {
-            float v[8];
-            tmem_ld8(lane_base + kMlpHidden + 8u * c, v);
-            if (r < a.rows) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int n = 8 * c + j;
-                    if (n < a.Q) a.logits[r * a.Q + n] = v[j] + __ldg(b3 + n);
-                }
-            }
-        }
+        // layer 3 epilogue: + b3 -> logits (this thread's half of the Qp columns)
+        if (half == 0) mlp_epilogue3<Q, 0>(a, lane_base, r);
+        else mlp_epilogue3<Q, 1>(a, lane_base, r);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
@@ -524,6 +573,30 @@ cudaError_t forward_rows(mcmc_mlp *m, int R, const float *X, float *logits, cuda
     return e;
 }
 
+template <int Q>
+cudaError_t launch_tc(mcmc_mlp *m, long long rows, const float *X, float *logits, int grid,
+                      cudaStream_t s)
+{
+    constexpr int Qp = (Q + 15) / 16 * 16;
+    const uint32_t smem = mlp_smem_bytes(Qp);
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    MlpTcArgs<Q> a;
+    a.rows = rows;
+    a.X = X;
+    a.ops = m->tc_ops;
+    a.logits = logits;
+    a.status = m->status;
+    const float *h = m->small_host;   // W1, b1 | b2 | b3
+    std::memcpy(a.W1, h, sizeof a.W1);
+    std::memcpy(a.b1, h + kMlpHidden * kMlpIn, sizeof a.b1);
+    std::memcpy(a.b2, h + mlp_off_W2(), sizeof a.b2);
+    std::memcpy(a.b3, h + mlp_off_W2() + kMlpHidden, sizeof a.b3);
+    mlp_tc_kernel<Q><<<grid, 256, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t mlp_forward_simt(mcmc_mlp *m, long long rows, const float *X, float *logits,
@@ -547,26 +620,28 @@ cudaError_t mlp_forward_tc(mcmc_mlp *m, long long rows, const float *X, float *l
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         m->launches++;
+        // the small weights travel in the launch parameters: read them back once
+        float *h = m->small_host;
+        const long long P = mlp_param_count(m->Q);
+        if ((e = cudaMemcpyAsync(h, m->params, 4 * (size_t)mlp_off_W2(), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h + mlp_off_W2(), m->params + mlp_off_b2(), 4 * kMlpHidden,
+                                 cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(h + mlp_off_W2() + kMlpHidden, m->params + mlp_off_b3(m->Q),
+                                 4 * (size_t)(P - mlp_off_b3(m->Q)), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return e;
         m->tc_valid = true;
     }
-    const uint32_t smem = mlp_smem_bytes(m->Qp);
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    MlpTcArgs a{};
-    a.rows = rows;
-    a.X = X;
-    a.params = m->params;
-    a.ops = m->tc_ops;
-    a.logits = logits;
-    a.Q = m->Q;
-    a.Qp = m->Qp;
-    a.status = m->status;
     const long long tiles = (rows + 127) / 128;
     const int grid = (int)std::min<long long>(tiles, std::max(g_sm_count, 1));
-    mlp_tc_kernel<<<grid, 128, smem, s>>>(a);
-    m->launches++;
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    switch (m->Q) {
+    case 4: e = launch_tc<4>(m, rows, X, logits, grid, s); break;
+    case 16: e = launch_tc<16>(m, rows, X, logits, grid, s); break;
+    default: e = launch_tc<64>(m, rows, X, logits, grid, s); break;
+    }
+    if (e == cudaSuccess) m->launches++;
+    return e;
 }
 
 }  // namespace mcmcdet
@@ -729,6 +804,8 @@ mcmc_status mcmc_mlp_create(int32_t qam, int32_t max_rows, void *stream, mcmc_ml
     };
     for (auto &a : allocs)
         if ((e = cudaMalloc(a.p, a.bytes)) != cudaSuccess) return bail(e);
+    if ((e = cudaMallocHost(&m->small_host, 4 * (size_t)(kMlpHidden * kMlpIn + 3 * kMlpHidden))) != cudaSuccess)
+        return bail(e);
     for (void *p : {(void *)m->params, (void *)m->adam_m, (void *)m->adam_v})
         if ((e = cudaMemsetAsync(p, 0, 4 * P, m->stream)) != cudaSuccess) return bail(e);
     if ((e = cudaMemsetAsync(m->status, 0, 256, m->stream)) != cudaSuccess) return bail(e);
@@ -746,6 +823,7 @@ mcmc_status mcmc_mlp_destroy(mcmc_mlp *m)
                     (void *)m->dlog, (void *)m->logit, (void *)m->rowloss, (void *)m->partial,
                     (void *)m->status, (void *)m->tc_ops})
         if (p) cudaFree(p);
+    if (m->small_host) cudaFreeHost(m->small_host);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
     return MCMC_OK;

@@ -27,6 +27,7 @@ struct mcmc_mlp {
     // tensor-core operand images of W2 and W3 (BF16), rebuilt when the parameters change
     uint8_t *tc_ops = nullptr;
     bool tc_valid = false;
+    float *small_host = nullptr;   // pinned host copy of W1, b1 | b2 | b3 (launch parameters)
 };
 
 namespace mcmcdet {
