@@ -289,7 +289,7 @@ int simt_default_tile(const mcmc_detector *d, int max_n, int max_nop)
 Choice default_choice(const mcmc_detector *d, const ChannelDesc &c)
 {
     const int eng = d->cfg.engine & 3;
-    if (d->cfg.precision == MCMC_PREC_MIXED && c.N <= 128 && eng != MCMC_ENGINE_SIMT)
+    if (d->cfg.precision == MCMC_PREC_MIXED && c.N <= kMaxN && eng != MCMC_ENGINE_SIMT)
         return Choice{MCMC_ENGINE_TC, 32};
     return Choice{MCMC_ENGINE_SIMT, simt_default_tile(d, c.N, c.NOp)};
 }
@@ -400,7 +400,7 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
         }
         const ChannelDesc &c0 = d->desc[kv.second[0]];
         std::vector<Choice> cands;
-        if (prec == MCMC_PREC_MIXED && c0.N <= 128) {
+        if (prec == MCMC_PREC_MIXED && c0.N <= kMaxN) {
             cands.push_back(Choice{MCMC_ENGINE_TC, 32});
             cands.push_back(Choice{MCMC_ENGINE_TC, 16});
         }
@@ -439,7 +439,7 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
             ca.init_f = 1;
             cudaError_t e = launch_group(d, g, ca);                 // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
-            ca.iterations = 8;
+            ca.iterations = 24;   // long enough to amortise per-item set-up (streamed operands)
             if (e == cudaSuccess) e = launch_group(d, g, ca);
             if (e == cudaSuccess) e = cudaEventRecord(e1, d->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);

@@ -61,6 +61,10 @@ struct TcLayout {
     uint32_t a, b, red, dred, acc, impr, ref, fref, kb, bar, tmem, total;
 };
 
+// The A operand stays resident for MT <= 2 (N <= 128). Beyond that it no longer fits one SM's
+// shared memory and is streamed from L2 in 128-row x Kp chunks through two buffers.
+__host__ __device__ constexpr bool tc_streamed(int MT) { return MT >= 3; }
+
 __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
 {
     TcLayout L{};
@@ -71,7 +75,7 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
         o += bytes;
         return r;
     };
-    L.a = take((uint32_t)S * MT * 128 * Kp * 2, 1024);
+    L.a = take((uint32_t)(tc_streamed(MT) ? 2 : S * MT) * 128 * Kp * 2, 1024);
     L.b = take((uint32_t)(C / 8) * (((uint32_t)(Kp / 8) * 144u + 127u) / 128u * 128u + 32u), 1024);
     L.red = take(4u * C * 4, 16);
     L.dred = take(4u * C * 4, 16);
@@ -80,7 +84,7 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
     L.ref = take((uint32_t)C * 8, 16);       // FP64 refresh results per chain
     L.fref = take((uint32_t)C * kMaxN, 16);  // states for the FP64 refresh
     L.kb = take((uint32_t)C * kMaxN, 16);    // best visited state of every chain
-    L.bar = take(16, 8);
+    L.bar = take(6 * 8, 8);                  // TMA, MMA, streamed chunks full[2] / empty[2]
     L.tmem = take(4, 4);
     L.total = (o + 127) / 128 * 128;
     return L;
@@ -108,17 +112,114 @@ struct TcCtx {
     uint32_t sbo_a, sbo_b;
     int tid, warp, lane, q, cgi, h, dl, C, S, Kp;
     uint32_t mma_phase;
+    // streamed A operand (thread 0's pipeline state)
+    const uint8_t *asrc;          // this work item's operand block in global memory
+    uint32_t bar_full[2], bar_empty[2];
+    uint32_t full_phase[2], empty_phase[2];
+    bool pend[2];                 // a chunk copy into buffer b is requested and not yet waited for
+    bool fail;                    // a streamed wait ran out
 };
 
 // Issue the MMAs of one transition (thread 0, after a CTA barrier that publishes the B operand)
 // and, separately, wait for them (everyone). The wait returns false on a bounded-wait expiry of
 // this thread's wait; callers combine the verdicts in a CTA-wide vote.
+// Streamed A operand: bulk copy of chunk c (tile c / S, term c % S) into buffer b.
+__device__ __forceinline__ void tc_load_chunk(TcCtx &x, int MT, int c, int b)
+{
+    const uint32_t cb = 128u * (uint32_t)x.Kp * 2u;
+    const int t = c / x.S, s = c % x.S;
+    const uint8_t *src = x.asrc + (size_t)(s * MT + t) * cb;
+    const uint32_t dst = smem_u32(x.sA) + (uint32_t)b * cb;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(x.bar_full[b]), "r"(cb)
+                 : "memory");
+    x.pend[b] = true;
+    const uint32_t chunk = 1u << 15;
+    for (uint32_t off = 0; off < cb; off += chunk) {
+        const uint32_t n = cb - off < chunk ? cb - off : chunk;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                dst + off),
+            "l"(src + off), "r"(n), "r"(x.bar_full[b])
+            : "memory");
+    }
+}
+
+// Thread 0: MMAs of one transition over the streamed chunks, two buffers deep. Chunk c's buffer
+// is refilled with chunk c + 2 once c's MMAs have completed (their commit to empty[b]); the last
+// two chunks are covered by the final commit only, so every full / empty phase is waited once.
+template <int MT>
+__device__ __forceinline__ void tc_stream_mmas(TcCtx &x)
+{
+    const int nch = x.S * MT;
+    const uint32_t cb = 128u * (uint32_t)x.Kp * 2u;
+    const uint32_t b0 = smem_u32(x.sB);
+    for (int c = 0; c < 2 && c < nch; ++c)
+        if (!x.pend[c]) tc_load_chunk(x, MT, c, c);   // else requested at the end of the last one
+    for (int c = 0; c < nch && !x.fail; ++c) {
+        const int b = c & 1;
+        if (!mbar_wait(x.bar_full[b], x.full_phase[b])) { x.fail = true; break; }
+        x.full_phase[b] ^= 1u;
+        x.pend[b] = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int t = c / x.S, s = c % x.S;
+        const uint32_t ab = smem_u32(x.sA) + (uint32_t)b * cb;
+        for (int ks = 0; ks < x.Kp / 16; ++ks) {
+            const uint64_t da = smem_desc(ab + ks * 256u, 128u, x.sbo_a);
+            const uint64_t db = smem_desc(b0 + ks * 2u * b_lbo(), b_lbo(), x.sbo_b);
+            mma_bf16(x.tmem + (uint32_t)(t * x.C), da, db, x.idesc, (s | ks) ? 1u : 0u);
+        }
+        if (c + 2 < nch) {
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    x.bar_empty[b])
+                : "memory");
+            if (!mbar_wait(x.bar_empty[b], x.empty_phase[b])) { x.fail = true; break; }
+            x.empty_phase[b] ^= 1u;
+            tc_load_chunk(x, MT, c + 2, b);
+        }
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(x.bar_mma)
+        : "memory");
+}
+
+// Thread 0, after the transition's MMAs completed: request chunks 0 and 1 for the next one (the
+// operand is the same every transition of a work item).
+template <int MT>
+__device__ __forceinline__ void tc_stream_prefetch(TcCtx &x)
+{
+    if (x.fail) return;
+    for (int c = 0; c < 2 && c < x.S * MT; ++c) tc_load_chunk(x, MT, c, c);
+}
+
+// Thread 0, at the end of a work item (or after a failed wait): wait (bounded) for every chunk copy
+// requested and not yet waited for, so that none is in flight when the buffers are reused or the
+// CTA exits. Returns false if a wait ran out.
+__device__ __forceinline__ bool tc_stream_drain(TcCtx &x)
+{
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        if (!x.pend[b]) continue;
+        if (!mbar_wait(x.bar_full[b], x.full_phase[b])) ok = false;
+        x.full_phase[b] ^= 1u;
+        x.pend[b] = false;
+    }
+    return ok;
+}
+
 template <int MT>
 __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if constexpr (tc_streamed(MT)) {
+        if (x.tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_stream_mmas<MT>(x);
+        }
+        return;
+    }
     if (x.tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = smem_u32(x.sA), b0 = smem_u32(x.sB);
@@ -141,11 +242,19 @@ __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
     }
 }
 
-__device__ __forceinline__ bool tc_gemm_wait(TcCtx &x)
+// prefetch_next: another transition of the same work item follows (streamed operand only).
+template <int MT>
+__device__ __forceinline__ bool tc_gemm_wait(TcCtx &x, bool prefetch_next)
 {
     const bool ok = mbar_wait(x.bar_mma, x.mma_phase);
     x.mma_phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if constexpr (tc_streamed(MT)) {
+        if (x.tid == 0) {
+            if (ok && prefetch_next) tc_stream_prefetch<MT>(x);
+            return ok && !x.fail;
+        }
+    }
     return ok;
 }
 
@@ -251,7 +360,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     write_b(k2);
     if (alive) {
         tc_gemm_issue<MT>(x);
-        const bool ok = tc_gemm_wait(x);
+        const bool ok = tc_gemm_wait<MT>(x, A.iterations > 0);
         if (__syncthreads_or(!ok)) { alive = false; set_status(A.status, kStatusTimeout); }
     }
     {
@@ -350,7 +459,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                                        A.key0, A.key1);
             logu = lg2_approx(uniform_f(word_of(w, cc & 3)));
         }
-        const bool mma_ok = tc_gemm_wait(x);
+        const bool mma_ok = tc_gemm_wait<MT>(x, i + 1 < A.iterations);
         // 3. reverse factor and energy difference
         float gp[MT][4], mp[MT][4];
         tc_read<MT>(x, gp, mp);
@@ -519,8 +628,8 @@ __device__ __forceinline__ void tc_item_dispatch(const ChainArgs &A, TcCtx &x, c
 }
 
 template <int MT>
-__global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const ChainArgs A, const int C,
-                                                           const int S, const int Kp)
+__global__ void __launch_bounds__(512, MT == 1 ? TC_MIN_BLOCKS : 1)
+    chains_tc_kernel(const ChainArgs A, const int C, const int S, const int Kp)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcLayout lay = tc_layout(S, MT, Kp, C);
@@ -553,11 +662,24 @@ __global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const Cha
     x.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
               ((uint32_t)(128 >> 4) << 24);
     x.mma_phase = 0;
+    x.asrc = nullptr;
+    for (int b = 0; b < 2; ++b) {
+        x.bar_full[b] = smem_u32(&bars[2 + b]);
+        x.bar_empty[b] = smem_u32(&bars[4 + b]);
+        x.full_phase[b] = 0;
+        x.empty_phase[b] = 0;
+        x.pend[b] = false;
+    }
+    x.fail = false;
     const int ncols_alloc = A.tc_tmem_cols;   // TMEM columns to allocate (power of 2, >= 32)
 
     if (x.tid == 0) {
         mbar_init(bar_tma, 1);
         mbar_init(x.bar_mma, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(x.bar_full[b], 1);
+            mbar_init(x.bar_empty[b], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (x.warp == 0) {
@@ -579,6 +701,23 @@ __global__ void __launch_bounds__(512, TC_MIN_BLOCKS) chains_tc_kernel(const Cha
     for (int item = blockIdx.x; item < A.n_items && alive; item += gridDim.x) {
         const WorkItem it = A.items[item];
         const ChannelDesc d = A.desc[it.b];
+        x.asrc = A.tc_ops + d.tc_off;
+        if constexpr (tc_streamed(MT)) {
+            // chunks are streamed by the transitions themselves
+            switch (d.L) {
+            case 2: tc_item_dispatch<MT, 2>(A, x, it, d, alive); break;
+            case 4: tc_item_dispatch<MT, 4>(A, x, it, d, alive); break;
+            default: tc_item_dispatch<MT, 8>(A, x, it, d, alive); break;
+            }
+            const bool drained = x.tid != 0 || tc_stream_drain(x);
+            if (__syncthreads_or(!drained || (x.tid == 0 && x.fail)) && alive) {
+                alive = false;
+                set_status(A.status, kStatusTimeout);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            continue;
+        }
         // stage this channel's A operand (TMA bulk copy, mbarrier completion)
         const uint32_t abytes = (uint32_t)S * MT * 128u * (uint32_t)Kp * 2u;
         if (x.tid == 0) {
@@ -624,7 +763,7 @@ __global__ void pack_kernel(const ChannelDesc *desc, const float *bt32, uint8_t 
 {
     const ChannelDesc d = desc[blockIdx.x];
     const int N = d.N;
-    if (N > 128) return;
+    if (N > kMaxN) return;
     const int MT = (N + 63) / 64, Kp = (N + 15) / 16 * 16;
     const bool pre = d.NO > N;
     const float *bt = bt32 + d.bt_off;
@@ -673,7 +812,7 @@ int pow2_at_least(int v)
 bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, TcPlan *plan)
 {
     *plan = TcPlan{};
-    if (max_n < 1 || max_n > 128) return false;
+    if (max_n < 1 || max_n > kMaxN) return false;
     if (chains_per_cta < 16 || chains_per_cta > 32 || chains_per_cta % 16) return false;
     const int MT = (max_n + 63) / 64;
     const int Kp = (max_n + 15) / 16 * 16;
@@ -689,17 +828,21 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
     plan->split_terms = S;
     plan->threads = 16 * C;                   // 4 TMEM quadrants x C/8 column groups x 32
     plan->tmem_cols = pow2_at_least(MT * C);
+    // resident CTAs per SM: shared memory, threads, registers (the launch bounds allow 64 per
+    // thread for one tile, 128 beyond), and TMEM
+    const int regs = MT == 1 ? 65536 / (TC_MIN_BLOCKS * 512) : 128;
     const int by_smem = (int)(228 * 1024 / (L.total + 1024));
-    const int by_thr = std::min(2048 / plan->threads, TC_MIN_BLOCKS * 512 / plan->threads);
+    const int by_thr = std::min(2048 / plan->threads, 65536 / (plan->threads * regs));
+    const int by_occ = std::min(by_smem, by_thr);
     const int by_tmem = 512 / plan->tmem_cols;
-    plan->ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_thr), by_tmem));
+    plan->ctas_per_sm = std::max(1, std::min(by_occ, by_tmem));
     plan->smem = L.total;
     return true;
 }
 
 long long tc_operand_bytes(int N, int split_terms)
 {
-    if (N > 128) return 0;
+    if (N > kMaxN) return 0;
     const int MT = (N + 63) / 64, Kp = (N + 15) / 16 * 16;
     return (long long)split_terms * MT * 128 * Kp * 2;
 }
@@ -722,15 +865,19 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(a.n_items, std::max(1, sms * plan.ctas_per_sm));
     cudaError_t e;
-    if (plan.m_tiles == 1) {
-        auto k = chains_tc_kernel<1>;
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem)) != cudaSuccess) return e;
+    auto go = [&](auto k) {
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem)) != cudaSuccess)
+            return e;
         k<<<grid, plan.threads, plan.smem, s>>>(a, plan.chains_per_cta, plan.split_terms, plan.kdim);
-    } else {
-        auto k = chains_tc_kernel<2>;
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem)) != cudaSuccess) return e;
-        k<<<grid, plan.threads, plan.smem, s>>>(a, plan.chains_per_cta, plan.split_terms, plan.kdim);
+        return cudaSuccess;
+    };
+    switch (plan.m_tiles) {
+    case 1: e = go(chains_tc_kernel<1>); break;
+    case 2: e = go(chains_tc_kernel<2>); break;
+    case 3: e = go(chains_tc_kernel<3>); break;
+    default: e = go(chains_tc_kernel<4>); break;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

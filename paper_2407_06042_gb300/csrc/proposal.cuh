@@ -216,11 +216,27 @@ __device__ __forceinline__ uint64_t rel_logit2_2(const Poly2<L> &p, uint64_t mc2
     return f2_fma(f2_fma(mc2, jf, p.B), jf, p.C0);
 }
 
+// Smallest level count evaluated in packed pairs (below it the two chains run the scalar code;
+// both give identical results).
+#ifndef TC_PAIR_MIN_L
+#define TC_PAIR_MIN_L 2
+#endif
+
 // factor_draw_f for two chains: levels (as floats) and log2 q of the drawn levels.
 template <int L>
 __device__ __forceinline__ void factor_draw_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
                                                float u0, float u1, uint64_t &sel, uint64_t &log2q)
 {
+    if constexpr (L < TC_PAIR_MIN_L) {
+        float a0, a1, k0, k1, q0, q1;
+        f2_unpack(a2, a0, a1);
+        f2_unpack(kf, k0, k1);
+        const float s0 = factor_draw_f<L>(a0, c2, inv2c, k0, u0, q0);
+        const float s1 = factor_draw_f<L>(a1, c2, inv2c, k1, u1, q1);
+        sel = f2_pack(s0, s1);
+        log2q = f2_pack(q0, q1);
+        return;
+    }
     const Poly2<L> p = rel_poly2<L>(a2, c2, inv2c, kf);
     const uint64_t mc2 = f2_splat(-c2);
     float S0[L], S1[L];
@@ -263,6 +279,13 @@ template <int L>
 __device__ __forceinline__ uint64_t factor_log2q_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
                                                     uint64_t jf)
 {
+    if constexpr (L < TC_PAIR_MIN_L) {
+        float a0, a1, k0, k1, j0, j1;
+        f2_unpack(a2, a0, a1);
+        f2_unpack(kf, k0, k1);
+        f2_unpack(jf, j0, j1);
+        return f2_pack(factor_log2q_f<L>(a0, c2, inv2c, k0, j0), factor_log2q_f<L>(a1, c2, inv2c, k1, j1));
+    }
     const Poly2<L> p = rel_poly2<L>(a2, c2, inv2c, kf);
     const uint64_t mc2 = f2_splat(-c2);
     uint64_t acc = 0ull;

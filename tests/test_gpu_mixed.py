@@ -51,6 +51,8 @@ def test_mixed_one_launch_equals_single_step_launches():
     [(36, 40, 16, 18.0), (33, 33, 64, 26.0)],          # N = 72, 66: ragged K and dimensions
     [(64, 64, 16, 20.0), (64, 128, 4, 8.0)],           # N = 128: two A-operand tiles
     [(1, 2, 4, 6.0), (3, 3, 64, 20.0), (8, 16, 16, 14.0)],
+    [(80, 96, 16, 18.0), (100, 100, 4, 12.0)],         # N = 160, 200: streamed operand, 3 / 4 tiles
+    [(128, 128, 64, 28.0)],                            # N = 256: the largest channel
 ])
 def test_mixed_step_parity_shapes(shapes):
     b = workload.generate(shapes, 91)
@@ -119,3 +121,25 @@ def test_uneven_batch_autotuned_and_graph_replay():
     np.testing.assert_array_equal(o1["llr"], o2["llr"])
     d1.destroy()
     d2.destroy()
+
+
+def test_mixed_kronecker_256_refresh():
+    """128x128 64-QAM Kronecker channels (N = 256, streamed tensor-core operand) with the FP64
+    refresh every 10 transitions: step parity, then tracked energies equal to FP64 evaluations
+    right after a refresh point."""
+    b = workload.kronecker_batch(128, 128, 64, [30.0], 2, 0.5, 77)
+    det = H.make_detector(b, chains=32, precision="mixed", split_terms=3, refresh_period=10,
+                          seed=5, engine=TC)
+    r = H.step_parity(det, b, H.targets(b), seed=5, steps=3, w_cat=2e-4, w_acc=2e-3)
+    assert r["bad"] == 0, r
+    det.run_chains(17, 3)
+    out = det.estimate(stats=True)
+    flat, f = det.get_chains()
+    st = H.split_states(det, b, flat)
+    tg = H.targets(b)
+    for ch in range(b.n_channels):
+        for c in range(32):
+            fx = oracle.f_value(tg[ch].Hr, tg[ch].yr, tg[ch].sigma2, tg[ch].values(st[ch][c]))
+            assert abs(f[ch * 32 + c] - fx) <= 1e-9 * abs(fx)
+    assert out["stats"]["refresh_drift"] < 1e-1
+    det.destroy()
