@@ -499,7 +499,7 @@ def main():
         precision = "fp32"
         try:
             probe = pkg.Detector(max_channels=1, max_nt=w["nt"], max_nr=w["nr"], chains=Np,
-                                 precision="mixed")
+                                 precision="mixed", engine=pkg.MCMC_ENGINE_TC)
             one = batch.subset([0])
             hp = torch.from_numpy(np.ascontiguousarray(one.H).view(np.float32).copy()).to(dev)
             yp = torch.from_numpy(np.ascontiguousarray(one.y).view(np.float32).copy()).to(dev)

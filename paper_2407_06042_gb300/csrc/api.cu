@@ -456,7 +456,9 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        {
+        if (sample.size() == (size_t)want) {
+            // only a probe over a full sample speaks for other batches of this class: with a few
+            // channels the engines' parallelism differs from a full batch's
             std::lock_guard<std::mutex> lk(g_tuned_mu);
             g_tuned[kv.first] = best;
         }
