@@ -58,7 +58,7 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 
 // Shared-memory layout of the kernel (bytes).
 struct TcLayout {
-    uint32_t a, b, red, dred, acc, impr, ref, fref, kb, bar, tmem, total;
+    uint32_t a, b, red, dred, acc, impr, ref, fref, kb, dg, bar, tmem, total;
 };
 
 // The A operand stays resident for MT <= 2 (N <= 128). Beyond that it no longer fits one SM's
@@ -84,6 +84,8 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
     L.ref = take((uint32_t)C * 8, 16);       // FP64 refresh results per chain
     L.fref = take((uint32_t)C * kMaxN, 16);  // states for the FP64 refresh
     L.kb = take((uint32_t)C * kMaxN, 16);    // best visited state of every chain
+    // streamed kernels: Gt x of every thread's (tile, chain pair), [2 MT][threads] packed pairs
+    L.dg = take(tc_streamed(MT) ? (uint32_t)(2 * MT) * (16u * C) * 8u : 0u, 16);
     L.bar = take(6 * 8, 8);                  // TMA, MMA, streamed chunks full[2] / empty[2]
     L.tmem = take(4, 4);
     L.total = (o + 127) / 128 * 128;
@@ -106,6 +108,8 @@ struct TcCtx {
     double *sref;
     int8_t *sfs;
     int8_t *skb;
+    uint64_t *sdg;                // Gt x pairs in shared memory (streamed kernels)
+    int nthr;
     uint32_t bar_mma;
     uint32_t tmem;
     uint32_t idesc;
@@ -277,6 +281,21 @@ __device__ __forceinline__ void tc_read(const TcCtx &x, float (&g)[MT][4], float
 }
 
 
+// TMEM -> registers for one 128-row tile t: Gt x (g) and P~ Gt x (m) of this thread's dimension
+// for its 4 chains (the streamed kernels read tile by tile to bound register pressure).
+__device__ __forceinline__ void tc_read_tile(const TcCtx &x, int t, float (&g)[4], float (&m)[4])
+{
+    float v[8];
+    tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + 8 * x.cgi), v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float send = x.h ? v[j] : v[4 + j];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 16);
+        g[j] = x.h ? recv : v[j];
+        m[j] = x.h ? v[4 + j] : recv;
+    }
+}
+
 // One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
 // every chain column is live, so no per-(dimension, chain) validity test is needed. Levels are
 // held as exact small floats.
@@ -296,7 +315,18 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     int nd[MT];
     bool live[MT][4];
     // per (tile, chain pair): levels, Gt x and the drift slope (log2 units), as packed pairs
-    uint64_t k2[MT][2], Dg2[MT][2], sl2[MT][2];
+    uint64_t k2[MT][2], sl2[MT][2];
+    // Gt x of the current states: registers, or shared memory for more than two tiles
+    constexpr bool kDgSmem = tc_streamed(MT);
+    uint64_t Dg2r[kDgSmem ? 1 : MT][2];
+    auto dg_get = [&](int t, int p) -> uint64_t {
+        if constexpr (kDgSmem) return x.sdg[(2 * t + p) * x.nthr + x.tid];
+        else return Dg2r[t][p];
+    };
+    auto dg_set = [&](int t, int p, uint64_t v) {
+        if constexpr (kDgSmem) x.sdg[(2 * t + p) * x.nthr + x.tid] = v;
+        else Dg2r[t][p] = v;
+    };
     int8_t *skb = x.skb;                           // best visited states [C][kMaxN]
     const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
     const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
@@ -372,7 +402,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             for (int p = 0; p < 2; ++p) {
                 const uint64_t gg = alive ? f2_pack(g[t][2 * p], g[t][2 * p + 1]) : 0ull;
                 const uint64_t mm = alive ? f2_pack(m[t][2 * p], m[t][2 * p + 1]) : 0ull;
-                Dg2[t][p] = gg;
+                dg_set(t, p, gg);
                 sl2[t][p] = alive ? slope2(t, gg, mm) : 0ull;
             }
     }
@@ -387,8 +417,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             float kv[4], dg[4];
             f2_unpack(k2[t][0], kv[0], kv[1]);
             f2_unpack(k2[t][1], kv[2], kv[3]);
-            f2_unpack(Dg2[t][0], dg[0], dg[1]);
-            f2_unpack(Dg2[t][1], dg[2], dg[3]);
+            f2_unpack(dg_get(t, 0), dg[0], dg[1]);
+            f2_unpack(dg_get(t, 1), dg[2], dg[3]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!live[t][j]) continue;
@@ -460,23 +490,28 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             logu = lg2_approx(uniform_f(word_of(w, cc & 3)));
         }
         const bool mma_ok = tc_gemm_wait<MT>(x, i + 1 < A.iterations);
-        // 3. reverse factor and energy difference
-        float gp[MT][4], mp[MT][4];
-        tc_read<MT>(x, gp, mp);
-        uint64_t gp2[MT][2], sp2[MT][2];
+        // 3. reverse factor and energy difference (with more than two tiles, the products and
+        //    levels of x' are not kept in registers: the update reads them again)
+        constexpr bool kReread = tc_streamed(MT);
+        constexpr int MTK = kReread ? 1 : MT;   // tiles whose x' caches stay live
+        uint64_t gp2[MTK][2], sp2[MTK][2];
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             const uint64_t z2 = f2_splat(2.f * zt[t]);
+            float gpt[4], mpt[4];
+            tc_read_tile(x, t, gpt, mpt);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
-                const uint64_t gg = f2_pack(gp[t][2 * p], gp[t][2 * p + 1]);
-                const uint64_t ap = slope2(t, gg, f2_pack(mp[t][2 * p], mp[t][2 * p + 1]));
-                gp2[t][p] = gg;
-                sp2[t][p] = ap;   // slope of x', kept for the update
+                const uint64_t gg = f2_pack(gpt[2 * p], gpt[2 * p + 1]);
+                const uint64_t ap = slope2(t, gg, f2_pack(mpt[2 * p], mpt[2 * p + 1]));
+                if constexpr (!kReread) {
+                    gp2[t < MTK ? t : 0][p] = gg;
+                    sp2[t < MTK ? t : 0][p] = ap;   // slope of x', kept for the update
+                }
                 uint64_t lr = factor_log2q_f2<L>(ap, c2, inv2c, kp2[t][p], k2[t][p]);
                 // (x'_n - x_n)(2 zt_n - (Gt x)_n - (Gt x')_n), the levels' difference doubled
                 const uint64_t dk = f2_mul(two2, f2_fma(mone, k2[t][p], kp2[t][p]));
-                const uint64_t e = f2_fma(mone, gg, f2_fma(mone, Dg2[t][p], z2));
+                const uint64_t e = f2_fma(mone, gg, f2_fma(mone, dg_get(t, p), z2));
                 uint64_t dd = f2_mul(dk, e);
                 if (!FULL) {
                     float a[2], b[2];
@@ -533,12 +568,13 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 const int c = cbase + 2 * p + h;
                 fl[h] = (FULL || c < nC) ? x.sacc[c] : 0;
             }
+            if constexpr (kReread) continue;
 #pragma unroll
-            for (int t = 0; t < MT; ++t) {
+            for (int t = 0; t < MTK; ++t) {
                 float ka[2], kb[2], da[2], db[2], sa[2], sb[2];
                 f2_unpack(k2[t][p], ka[0], ka[1]);
                 f2_unpack(kp2[t][p], kb[0], kb[1]);
-                f2_unpack(Dg2[t][p], da[0], da[1]);
+                f2_unpack(dg_get(t, p), da[0], da[1]);
                 f2_unpack(gp2[t][p], db[0], db[1]);
                 f2_unpack(sl2[t][p], sa[0], sa[1]);
                 f2_unpack(sp2[t][p], sb[0], sb[1]);
@@ -551,8 +587,51 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                     if (im && live[t][2 * p + h]) skb[(cbase + 2 * p + h) * kMaxN + nd[t]] = (int8_t)kb[h];
                 }
                 k2[t][p] = f2_pack(ka[0], ka[1]);
-                Dg2[t][p] = f2_pack(da[0], da[1]);
+                dg_set(t, p, f2_pack(da[0], da[1]));
                 sl2[t][p] = f2_pack(sa[0], sa[1]);
+            }
+        }
+        if constexpr (kReread) {
+            // accepted chains: x' levels from the B operand, Gt x' and the slope from TMEM (the
+            // loads are warp-collective: a warp reads when any of its lanes has an acceptance)
+            int fl[4];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = cbase + j;
+                fl[j] = (FULL || c < nC) ? x.sacc[c] : 0;
+                any |= (fl[j] & 1);
+            }
+            if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int t = 0; t < MT; ++t) {
+                    float g[4], m[4];
+                    tc_read_tile(x, t, g, m);
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        float ka[2], da[2], sa[2], sb[2];
+                        f2_unpack(k2[t][p], ka[0], ka[1]);
+                        f2_unpack(dg_get(t, p), da[0], da[1]);
+                        f2_unpack(sl2[t][p], sa[0], sa[1]);
+                        f2_unpack(slope2(t, f2_pack(g[2 * p], g[2 * p + 1]), f2_pack(m[2 * p], m[2 * p + 1])),
+                                  sb[0], sb[1]);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int j = 2 * p + h;
+                            if (!(fl[j] & 1)) continue;
+                            const unsigned short bits =
+                                *reinterpret_cast<const unsigned short *>(x.sB + boff[t] + 16u * j);
+                            const float kb = 0.5f * (__uint_as_float((uint32_t)bits << 16) + lm1);
+                            ka[h] = kb;
+                            da[h] = g[j];
+                            sa[h] = sb[h];
+                            if ((fl[j] & 2) && live[t][j]) skb[(cbase + j) * kMaxN + nd[t]] = (int8_t)kb;
+                        }
+                        k2[t][p] = f2_pack(ka[0], ka[1]);
+                        dg_set(t, p, f2_pack(da[0], da[1]));
+                        sl2[t][p] = f2_pack(sa[0], sa[1]);
+                    }
+                }
             }
         }
         // periodic FP64 refresh of the tracked energies (decisions never read them)
@@ -600,8 +679,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         float kv[4], dg[4];
         f2_unpack(k2[t][0], kv[0], kv[1]);
         f2_unpack(k2[t][1], kv[2], kv[3]);
-        f2_unpack(Dg2[t][0], dg[0], dg[1]);
-        f2_unpack(Dg2[t][1], dg[2], dg[3]);
+        f2_unpack(dg_get(t, 0), dg[0], dg[1]);
+        f2_unpack(dg_get(t, 1), dg[2], dg[3]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!live[t][j]) continue;
@@ -643,6 +722,8 @@ __global__ void __launch_bounds__(512, MT == 1 ? TC_MIN_BLOCKS : 1)
     x.sref = reinterpret_cast<double *>(smem + lay.ref);
     x.sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
     x.skb = reinterpret_cast<int8_t *>(smem + lay.kb);
+    x.sdg = reinterpret_cast<uint64_t *>(smem + lay.dg);
+    x.nthr = blockDim.x;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.tmem);
     const uint32_t bar_tma = smem_u32(&bars[0]);
