@@ -699,7 +699,10 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
         CK(ensure(d->d_Mc, 16 * ntc), "alloc Mc");
         if (fp64) CK(ensure(d->d_GM64, 8 * mat), "alloc GM64");
     }
-    const size_t gj_stage = (size_t)(2 * maxnt * maxnt) * 16;
+    // Gauss-Jordan block (FP64 complex in FP64 mode, FP32 complex otherwise) and the copies of
+    // its pivot row and column
+    const size_t gj_elem = fp64 ? 16 : 8;
+    const size_t gj_stage = (size_t)(maxnt * maxnt + 2 * maxnt) * gj_elem;
     const bool stage_gj = pre && gj_stage <= std::min<size_t>(d->smem_optin, 160 * 1024);
     if (pre && !stage_gj) CK(ensure(d->d_gj, 16 * 2 * ntc), "alloc gj");
     if (fp64) CK(ensure(d->d_bt64, 8 * bt), "alloc bt64");
@@ -764,7 +767,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     pa.stage_h = h_stage <= std::min<size_t>(d->smem_optin, 128 * 1024);
     pa.stage_gj = stage_gj;
     pa.precond_fp32 = fp64 ? 0 : 1;
-    CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : 0, pre, d->stream),
+    CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : 2 * maxnt * gj_elem, pre, d->stream),
        "prep kernels");
     d->launches += pre ? 3 : 2;
     if (mixed) {
@@ -1135,11 +1138,11 @@ mcmc_status mcmc_detect_init_learned(mcmc_detector *d)
     CK(net_forward(d, rows, P<float>(d->d_mx_X), P<float>(d->d_mx_logits)), "network forward");
     CK(launch_mix(2, step_args(d), d->n_channels, d->max_nt, d->stream), "warm start kernel");
     d->launches++;
+    // the energies of the new states come from the chain kernel's first GEMM (as after the
+    // random initial states), or from the FP64 refresh if they are read before a run
     d->f_valid = false;
     d->d_valid = false;
-    st = ensure_energies(d);
-    if (st != MCMC_OK) return st;
-    return read_status(d);
+    return MCMC_OK;
 }
 
 mcmc_status mcmc_detect_mix_step(mcmc_detector *d, int64_t t)

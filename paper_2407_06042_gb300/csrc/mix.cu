@@ -106,9 +106,10 @@ __device__ __forceinline__ float log2_add(float a, float b)
     return m + lg2_approx(ex2_approx(a - m) + ex2_approx(b - m));
 }
 
-// Network distribution of one row in log2 units: returns max logit2 and the log2 normaliser.
+// Network distribution of one row in log2 units: max logit2, the sum of the weights
+// 2^(l2(s) - mx) (summed in s order) and the log2 normaliser.
 template <int Q>
-__device__ __forceinline__ void nn_norm(const float *logits, float &mx, float &lse2)
+__device__ __forceinline__ void nn_norm(const float *logits, float &mx, float &lse2, float &tot)
 {
     mx = -INFINITY;
 #pragma unroll 8
@@ -116,14 +117,22 @@ __device__ __forceinline__ void nn_norm(const float *logits, float &mx, float &l
     float S = 0.f;
 #pragma unroll 8
     for (int s = 0; s < Q; ++s) S += ex2_approx(fmaf(logits[s], kLog2e, -mx));
+    tot = S;
     lse2 = mx + lg2_approx(S);
 }
 
-// Smallest s with u * S_{Q-1} < S_s over the network's weights 2^(l2(s) - mx).
 template <int Q>
-__device__ __forceinline__ int nn_draw(const float *logits, float mx, float lse2, float u)
+__device__ __forceinline__ void nn_norm(const float *logits, float &mx, float &lse2)
 {
-    const float target = u * ex2_approx(lse2 - mx);
+    float tot;
+    nn_norm<Q>(logits, mx, lse2, tot);
+}
+
+// Smallest s with u * S_{Q-1} < S_s over the network's weights 2^(l2(s) - mx) (tot = S_{Q-1}).
+template <int Q>
+__device__ __forceinline__ int nn_draw(const float *logits, float mx, float tot, float u)
+{
+    const float target = u * tot;
     float acc = 0.f;
     int sel = Q - 1;
 #pragma unroll 8
@@ -169,8 +178,8 @@ __global__ void __launch_bounds__(128) propose_kernel(MixStepArgs a)
     const float aI = slope2(d, pre, z[i], w[i], a.gx[base + i], a.px[base + i]);
     const float aQ = slope2(d, pre, z[Nt + i], w[Nt + i], a.gx[base + Nt + i], a.px[base + Nt + i]);
     const float *lg = a.logits + row * Q;
-    float mx, lse2;
-    nn_norm<Q>(lg, mx, lse2);
+    float mx, lse2, tot;
+    nn_norm<Q>(lg, mx, lse2, tot);
     const uint32_t t = a.t;
     const float uc = uniform_f(philox_word(a, t, 0x80000000u + (uint32_t)i, b, c));
     const float uI = uniform_f(philox_word(a, t, (uint32_t)i, b, c));
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(128) propose_kernel(MixStepArgs a)
     int jI, jQ;
     float lDI, lDQ;
     if (uc < a.lambda) {
-        const int s = nn_draw<Q>(lg, mx, lse2, uI);
+        const int s = nn_draw<Q>(lg, mx, tot, uI);
         jI = s / L;
         jQ = s % L;
         lDI = factor_log2q<L>(aI, c2, inv2c, kI, jI);
@@ -265,25 +274,45 @@ __global__ void __launch_bounds__(128) accept_kernel(MixStepArgs a)
     }
 }
 
-// Warm start: one thread per (chain, antenna), drawn from the network at x = 0.
+// Warm start: per channel and group of antennas, the network's cumulative weights at x = 0 are
+// formed once in shared memory (one thread per antenna); then one thread per (antenna, chain)
+// draws with its t = 0 uniform.
+constexpr int kWarmAnt = 4;   // antennas per CTA (block = kWarmAnt x 64 threads)
+
 template <int L>
-__global__ void __launch_bounds__(128) init_learned_kernel(MixStepArgs a)
+__global__ void __launch_bounds__(256) init_learned_kernel(MixStepArgs a)
 {
     constexpr int Q = L * L;
+    __shared__ float S[kWarmAnt][Q];
     const int b = blockIdx.y;
     const ChannelDesc d = a.desc[b];
     if (d.L != L) return;
     const int Nt = d.Nt, N = d.N;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= a.chains * Nt) return;
-    const int c = e / Nt, i = e % Nt;
-    const float *lg = a.logits + (d.ant_off + i) * Q;
-    float mx, lse2;
-    nn_norm<Q>(lg, mx, lse2);
-    const int s = nn_draw<Q>(lg, mx, lse2, uniform_f(philox_word(a, 0u, (uint32_t)i, b, c)));
-    const long long base = d.state_off + (long long)c * N;
-    a.states_out[base + i] = (int8_t)(s / L);
-    a.states_out[base + Nt + i] = (int8_t)(s % L);
+    const int i0 = blockIdx.x * kWarmAnt;
+    if (i0 >= Nt) return;
+    if (threadIdx.x < kWarmAnt && i0 + (int)threadIdx.x < Nt) {
+        const float *lg = a.logits + (d.ant_off + i0 + threadIdx.x) * Q;
+        float mx, lse2;
+        nn_norm<Q>(lg, mx, lse2);
+        float acc = 0.f;
+        for (int s = 0; s < Q; ++s) {
+            acc += ex2_approx(fmaf(lg[s], kLog2e, -mx));
+            S[threadIdx.x][s] = acc;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kWarmAnt * a.chains; e += blockDim.x) {
+        const int ia = e % kWarmAnt, c = e / kWarmAnt;
+        const int i = i0 + ia;
+        if (i >= Nt) continue;
+        const float target = uniform_f(philox_word(a, 0u, (uint32_t)i, b, c)) * S[ia][Q - 1];
+        int sel = Q - 1;
+        for (int s = 0; s < Q; ++s)
+            if (target < S[ia][s]) { sel = s; break; }
+        const long long base = d.state_off + (long long)c * N;
+        a.states_out[base + i] = (int8_t)(sel / L);
+        a.states_out[base + Nt + i] = (int8_t)(sel % L);
+    }
 }
 
 }  // namespace
@@ -308,6 +337,7 @@ cudaError_t launch_mix(int which, const MixStepArgs &a, int n_channels, int max_
     if (n_channels <= 0) return cudaSuccess;
     const dim3 gthreads((a.chains * max_nt + 127) / 128, n_channels);
     const dim3 gwarps((a.chains + 3) / 4, n_channels);
+    const dim3 gwarm((max_nt + kWarmAnt - 1) / kWarmAnt, n_channels);
     switch (which * 10 + a.L) {
     case 2: propose_kernel<2><<<gthreads, 128, 0, s>>>(a); break;
     case 4: propose_kernel<4><<<gthreads, 128, 0, s>>>(a); break;
@@ -315,9 +345,9 @@ cudaError_t launch_mix(int which, const MixStepArgs &a, int n_channels, int max_
     case 12: accept_kernel<2><<<gwarps, 128, 0, s>>>(a); break;
     case 14: accept_kernel<4><<<gwarps, 128, 0, s>>>(a); break;
     case 18: accept_kernel<8><<<gwarps, 128, 0, s>>>(a); break;
-    case 22: init_learned_kernel<2><<<gthreads, 128, 0, s>>>(a); break;
-    case 24: init_learned_kernel<4><<<gthreads, 128, 0, s>>>(a); break;
-    case 28: init_learned_kernel<8><<<gthreads, 128, 0, s>>>(a); break;
+    case 22: init_learned_kernel<2><<<gwarm, 256, 0, s>>>(a); break;
+    case 24: init_learned_kernel<4><<<gwarm, 256, 0, s>>>(a); break;
+    case 28: init_learned_kernel<8><<<gwarm, 256, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -123,12 +123,13 @@ template <> struct CT<float> { struct type { float x, y; }; };
 template <> struct CT<double> { using type = cd; };
 
 // ------------------------------------------------------------------------------------------
-// K2: M = (G + gamma I)^{-1} (Remark 1, Eq. (19)) through the Cholesky factorisation
-// G + gamma I = L L^H (Hermitian positive definite for gamma > 0), X = L^{-1} by forward
-// substitution, M = X^H X, in FP64 (FP64 mode) or FP32 (FP32 / MIXED: any deterministic
-// preconditioner keeps the chain exact, the proposal staying a function of the state). The two
-// Nt x Nt blocks live in shared memory when they fit, else in the channel's global scratch block.
-// the channel's global scratch block.
+// K2: M = (G + gamma I)^{-1} (Remark 1, Eq. (19)) by in-place Gauss-Jordan elimination without
+// pivoting (G + gamma I is Hermitian positive definite for gamma > 0, so every pivot is real and
+// positive in exact arithmetic), in FP64 (FP64 mode) or FP32 (FP32 / MIXED: any deterministic
+// preconditioner keeps the chain exact, the proposal staying a function of the state). Step k
+// copies row k (times the pivot's inverse) and column k, then every element updates in place:
+//     A_kk <- 1/p,  A_kj <- A_kj / p,  A_ik <- -A_ik / p,  A_ij <- A_ij - A_ik A_kj / p.
+// The matrix lives in shared memory when it fits, else in the channel's global scratch block.
 // ------------------------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
@@ -139,66 +140,46 @@ __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
     const double gamma = d.gamma_t / (d.dmin * d.dmin);   // gamma in the unscaled model
     using C2 = typename CT<R>::type;
     extern __shared__ double shd[];
-    C2 *Am = a.stage_gj ? reinterpret_cast<C2 *>(shd) : reinterpret_cast<C2 *>(a.gj) + d.mat_off / 2;
-    C2 *X = Am + nt * nt;
+    C2 *rowk = reinterpret_cast<C2 *>(shd);               // A_kj / p
+    C2 *colk = rowk + nt;                                 // A_ik
+    C2 *Am = a.stage_gj ? colk + nt : reinterpret_cast<C2 *>(a.gj) + d.mat_off / 2;
     const cd *G = reinterpret_cast<const cd *>(a.Gc) + d.mat_off / 4;
     for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
         const cd g = G[e];
         Am[e] = {(R)(g.x + (e / nt == e % nt ? gamma : 0.0)), (R)g.y};
-        X[e] = {R(0), R(0)};
     }
     __syncthreads();
-    // right-looking Cholesky, lower factor in Am (the trailing block is kept Hermitian-full)
     for (int k = 0; k < nt; ++k) {
-        const R pv = Am[k * nt + k].x;
-        if (threadIdx.x == 0 && !(pv > R(0))) set_status(a.status, kStatusNumeric);
-        const R dk = sqrt(pv > R(0) ? pv : R(1));
-        const R inv = R(1) / dk;
-        __syncthreads();
-        for (int i = k + 1 + threadIdx.x; i < nt; i += blockDim.x) {
-            const C2 v = Am[i * nt + k];
-            Am[i * nt + k] = {v.x * inv, v.y * inv};
-        }
-        if (threadIdx.x == 0) Am[k * nt + k] = {dk, R(0)};
-        __syncthreads();
-        const int m = nt - k - 1;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            const int i = k + 1 + e / m, j = k + 1 + e % m;
-            // A_ij -= L_ik conj(L_jk)
-            const C2 li = Am[i * nt + k], lj = Am[j * nt + k];
-            const C2 v = Am[i * nt + j];
-            Am[i * nt + j] = {v.x - (li.x * lj.x + li.y * lj.y), v.y - (li.y * lj.x - li.x * lj.y)};
+        const C2 piv = Am[k * nt + k];
+        if (threadIdx.x == 0 && !(piv.x > R(0))) set_status(a.status, kStatusNumeric);
+        const R den = piv.x * piv.x + piv.y * piv.y;
+        const C2 pinv = {piv.x / den, -piv.y / den};
+        for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+            const C2 r = Am[k * nt + j];
+            rowk[j] = {r.x * pinv.x - r.y * pinv.y, r.x * pinv.y + r.y * pinv.x};
+            colk[j] = Am[j * nt + k];
         }
         __syncthreads();
-    }
-    // X = L^{-1}, one column per thread (forward substitution)
-    for (int j = threadIdx.x; j < nt; j += blockDim.x) {
-        X[j * nt + j] = {R(1) / Am[j * nt + j].x, R(0)};
-        for (int i = j + 1; i < nt; ++i) {
-            R sr = R(0), si = R(0);
-            for (int m2 = j; m2 < i; ++m2) {
-                const C2 l = Am[i * nt + m2], xv = X[m2 * nt + j];
-                sr += l.x * xv.x - l.y * xv.y;
-                si += l.x * xv.y + l.y * xv.x;
+        for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+            const int i = e / nt, j = e % nt;
+            C2 v;
+            if (i == k) {
+                v = j == k ? pinv : rowk[j];
+            } else if (j == k) {
+                const C2 c = colk[i];
+                v = {-(c.x * pinv.x - c.y * pinv.y), -(c.x * pinv.y + c.y * pinv.x)};
+            } else {
+                const C2 c = colk[i], r = rowk[j], o = Am[e];
+                v = {o.x - (c.x * r.x - c.y * r.y), o.y - (c.x * r.y + c.y * r.x)};
             }
-            const R il = R(1) / Am[i * nt + i].x;
-            X[i * nt + j] = {-sr * il, -si * il};
+            Am[e] = v;
         }
+        __syncthreads();
     }
-    __syncthreads();
-    // M = X^H X (Hermitian; upper triangle computed, mirrored)
     cd *M = reinterpret_cast<cd *>(a.Mc) + d.mat_off / 4;
     for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
-        const int i = e / nt, j = e % nt;
-        if (j < i) continue;
-        R sr = R(0), si = R(0);
-        for (int m2 = j; m2 < nt; ++m2) {   // X lower triangular: rows m2 >= max(i, j) = j
-            const C2 xi = X[m2 * nt + i], xj = X[m2 * nt + j];
-            sr += xi.x * xj.x + xi.y * xj.y;   // conj(xi) xj
-            si += xi.x * xj.y - xi.y * xj.x;
-        }
-        M[i * nt + j] = {(double)sr, (double)si};
-        if (i != j) M[j * nt + i] = {(double)sr, -(double)si};
+        const C2 v = Am[e];
+        M[e] = {(double)v.x, (double)v.y};
     }
 }
 
