@@ -265,6 +265,9 @@ def bench_config(args, w, n_channels, world, refresh, l2_note=None):
            "snr_db": snr, "channels": n_channels * world,
            "chains": w["chains"], "iterations": w["iterations"], "preconditioned": True,
            "refresh_period": refresh, "parallelism": f"replicas x{world}"}
+    if getattr(args, "engine", "auto") != "auto":
+        cfg["engine"] = args.engine
+        cfg["tile"] = getattr(args, "tile", 0) or "default"
     if l2_note:
         cfg["l2"] = l2_note
     return cfg
@@ -471,6 +474,8 @@ def main():
     ap.add_argument("--engine", default="auto", choices=["auto", "tc", "simt"],
                     help="chain-kernel engine (auto: the library's per-class autotuner)")
     ap.add_argument("--refresh", type=int, default=None, help="FP64 energy refresh period")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="chains per work item with an explicit --engine (0: the engine's default)")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
@@ -527,7 +532,8 @@ def main():
                             engine=({"auto": pkg.MCMC_ENGINE_AUTO, "tc": pkg.MCMC_ENGINE_TC,
                                      "simt": pkg.MCMC_ENGINE_SIMT}[args.engine] if prec == precision
                                     else pkg.MCMC_ENGINE_AUTO)
-                            | (pkg.MCMC_ENGINE_GRAPH if args.graph else 0))
+                            | (pkg.MCMC_ENGINE_GRAPH if args.graph else 0),
+                            tile=args.tile if (prec == precision and args.engine != "auto") else 0)
 
     def step(det):
         det.preprocess(batch.nt, batch.nr, batch.qam, Hd, batch.H_off, yd, batch.y_off, sd)

@@ -84,7 +84,9 @@ typedef struct {
     int32_t split_terms;    /* MIXED: BF16 terms G is split into (2 = hi+lo, 3 = hi+lo+lo2) */
     int32_t engine;         /* MCMC_ENGINE_AUTO (autotuned per shape class), _SIMT or _TC, optionally
                                OR-ed with MCMC_ENGINE_GRAPH */
-    int32_t reserved;       /* must be 0 */
+    int32_t tile;           /* with an explicit engine: chains per work item (TC: 16 or 32; SIMT: a
+                               multiple of 8, at most 64); 0: the engine's default. Must be 0 with
+                               MCMC_ENGINE_AUTO (the autotuner picks it) */
     uint64_t seed;          /* Philox key */
     void *stream;           /* cudaStream_t to enqueue on; NULL: the handle creates its own */
 } mcmc_config;

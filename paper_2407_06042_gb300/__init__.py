@@ -60,7 +60,7 @@ class Config(ctypes.Structure):
         ("max_channels", ctypes.c_int32), ("max_nt", ctypes.c_int32), ("max_nr", ctypes.c_int32),
         ("chains", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("preconditioned", ctypes.c_int32), ("refresh_period", ctypes.c_int32),
-        ("split_terms", ctypes.c_int32), ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("split_terms", ctypes.c_int32), ("engine", ctypes.c_int32), ("tile", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
     ]
 
@@ -166,7 +166,7 @@ class Detector:
     def __init__(self, *, max_channels: int, max_nt: int, max_nr: int, chains: int,
                  precision: str = "fp32", preconditioned: bool = True, refresh_period: int = 0,
                  split_terms: int = 2, engine: int = MCMC_ENGINE_AUTO, seed: int = 0,
-                 stream=None):
+                 stream=None, tile: int = 0):
         self._l = lib()
         cfg = Config()
         self._l.mcmc_config_default(ctypes.byref(cfg))
@@ -177,6 +177,7 @@ class Detector:
         cfg.refresh_period = int(refresh_period)
         cfg.split_terms = int(split_terms)
         cfg.engine = int(engine)
+        cfg.tile = int(tile)
         cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         cfg.stream = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else (stream or None)
         self.cfg = cfg

@@ -290,7 +290,8 @@ Choice default_choice(const mcmc_detector *d, const ChannelDesc &c)
 {
     const int eng = d->cfg.engine & 3;
     if (d->cfg.precision == MCMC_PREC_MIXED && c.N <= kMaxN && eng != MCMC_ENGINE_SIMT)
-        return Choice{MCMC_ENGINE_TC, 32};
+        return Choice{MCMC_ENGINE_TC, d->cfg.tile ? d->cfg.tile : 32};
+    if (eng == MCMC_ENGINE_SIMT && d->cfg.tile) return Choice{MCMC_ENGINE_SIMT, d->cfg.tile};
     return Choice{MCMC_ENGINE_SIMT, simt_default_tile(d, c.N, c.NOp)};
 }
 
@@ -529,7 +530,9 @@ mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out)
         (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < 0 ||
         cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 ||
         (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH)) != 0 || (cfg->engine & 3) == 3 ||
-        cfg->reserved != 0)
+        cfg->tile < 0 || (cfg->tile != 0 && (cfg->engine & 3) == MCMC_ENGINE_AUTO) ||
+        ((cfg->engine & 3) == MCMC_ENGINE_TC && cfg->tile != 0 && cfg->tile != 16 && cfg->tile != 32) ||
+        ((cfg->engine & 3) == MCMC_ENGINE_SIMT && (cfg->tile % 8 != 0 || cfg->tile > 64)))
         return MCMC_EINVAL;
     if (cfg->precision != MCMC_PREC_MIXED && (cfg->engine & 3) == MCMC_ENGINE_TC) return MCMC_EINVAL;
     mcmc_detector *d = new (std::nothrow) mcmc_detector();
