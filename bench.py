@@ -31,6 +31,27 @@ METRIC = "chain-iterations/s and detections/s at BER<=1e-3 vs plain FP32, 1 GB30
 UNIT = "chain-iterations/s"
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Channel sharding across ranks: every rank draws its own channels (weak scaling), from
+    the workload's seed offset by the rank; no data crosses ranks."""
+    return seed + 7 * rank
+
+
+def max_over_ranks(x: float, dist, device="cpu") -> float:
+    """The slowest rank's value (the job's time); x itself without a process group."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units of all ranks per second of the slowest rank."""
+    return units_per_rank * world / seconds
+
+
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -182,7 +203,7 @@ def chain_roofline(precision, w, units, chain_ms, batch=None):
 
 def load_batch(scale: float, rank: int, name: str = WORKLOAD):
     w = dict(workload.WORKLOADS[name])
-    w["seed"] = w["seed"] + 7 * rank
+    w["seed"] = rank_seed(w["seed"], rank)
     if w["kind"] == "rayleigh":
         n = max(1, int(round(w["per_snr"] * scale)))
         b = workload.rayleigh_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["seed"])
@@ -191,7 +212,7 @@ def load_batch(scale: float, rank: int, name: str = WORKLOAD):
         b = workload.kronecker_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["rho"], w["seed"])
     elif w["kind"] == "learned":
         n = max(1, int(round(w["count"] * scale)))
-        b = workload.learned_eval_batch(w, n, 7 * rank)
+        b = workload.learned_eval_batch(w, n, rank_seed(0, rank))
     else:
         n = max(1, int(round(w["count"] * scale)))
         b = workload.uneven_batch(n, w["seed"])
@@ -323,7 +344,7 @@ def run_learned(args, w, batch, rank, world, dist, dev, pkg, torch):
 
     # training (untimed): samples of the plain sampler, Adam in the library's kernels
     t0 = time.perf_counter()
-    btr = workload.learned_train_batch(w, 7 * rank)
+    btr = workload.learned_train_batch(w, rank_seed(0, rank))
     dtr = det_of(btr, tr["chains"], "mixed", seed=1)
     Ht, yt, st = upload(btr)
     dtr.preprocess(btr.nt, btr.nr, btr.qam, Ht, btr.H_off, yt, btr.y_off, st)
@@ -383,11 +404,7 @@ def run_learned(args, w, batch, rank, world, dist, dev, pkg, torch):
                 kev.append(step())
             e1.record(stream)
             torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
         kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
         return ms, kms, det.kernel_launches() - l0, clk.summary()
 
@@ -565,18 +582,14 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
         return ms / steps, kms, det.kernel_launches() - l0, clk.summary()
 
     det = make(precision)
     ms_step, chain_ms, launches, clocks = timed(det, args.steps, args.warmup)
     units_rank = B * Np * T
-    value = units_rank * world / (ms_step * 1e-3)
+    value = whole_job_rate(units_rank, world, ms_step * 1e-3)
     det_per_s = B * world / (ms_step * 1e-3)
     llr = o_llr.cpu().numpy()
     idx = o_idx.cpu().numpy()
@@ -608,12 +621,8 @@ def main():
         for _ in range(args.steps):
             step_e2e()
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": units_rank * world / dt, "unit": UNIT,
+        dt = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, dev)
+        e2e = {"value": whole_job_rate(units_rank, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(Hh.numel() * 4 + yh.numel() * 4 + sh.numel() * 4),
                "d2h_bytes_per_step": int(hi.numel() + hl.numel() * 4 + hb.numel() * 8),
                "detections_per_s": B * world / dt}

@@ -367,14 +367,9 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
             const double *G = A.G64 + d.mat_off;
             const double *z = A.z64 + d.vec_off;
             for (int c = warp; c < nC; c += nwarps) {
-                double quad = 0.0, lin = 0.0;
-                for (int n = lane; n < N; n += 32) {
-                    const double xn = odd_of(sk[c * N + n], L);
-                    double s = 0.0;
-                    for (int m = 0; m < N; ++m) s = fma(G[(size_t)n * N + m], (double)odd_of(sk[c * N + m], L), s);
-                    quad = fma(xn, s, quad);
-                    lin = fma(xn, z[n], lin);
-                }
+                double quad, lin;
+                quad_lin_fp64(G, z, N, lane, [&](int n) { return (double)odd_of(sk[c * N + n], L); },
+                              quad, lin);
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
                     quad += __shfl_xor_sync(0xffffffffu, quad, o);

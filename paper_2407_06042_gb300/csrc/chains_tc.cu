@@ -649,15 +649,9 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             const double *G = A.G64 + d.mat_off;
             const double *z = A.z64 + d.vec_off;
             for (int c = x.warp; c < nC; c += blockDim.x >> 5) {
-                double quad = 0.0, lin = 0.0;
-                for (int n = x.lane; n < N; n += 32) {
-                    const double xn = odd_of(x.sfs[c * kMaxN + n], L);
-                    double sacc = 0.0;
-                    for (int m = 0; m < N; ++m)
-                        sacc = fma(G[(size_t)n * N + m], (double)odd_of(x.sfs[c * kMaxN + m], L), sacc);
-                    quad = fma(xn, sacc, quad);
-                    lin = fma(xn, z[n], lin);
-                }
+                double quad, lin;
+                quad_lin_fp64(G, z, N, x.lane,
+                              [&](int n) { return (double)odd_of(x.sfs[c * kMaxN + n], L); }, quad, lin);
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
                     quad += __shfl_xor_sync(0xffffffffu, quad, o);

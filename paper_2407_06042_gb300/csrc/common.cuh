@@ -112,4 +112,29 @@ __device__ __forceinline__ void set_status(unsigned *status, unsigned bit)
     atomicOr(status, bit);
 }
 
+// FP64 x^T G x and x^T z for one state (G symmetric N x N), this lane's share of a warp's work:
+// the lane takes row pairs (r, N - 1 - r), each row contributing x_n (G_nn x_n + 2 sum_{m>n}
+// G_nm x_m), so every lane does N - 1 products per pair, half of the full N^2. level(n) returns
+// the odd-integer value of dimension n. The caller sums quad and lin over the warp.
+template <typename Level>
+__device__ __forceinline__ void quad_lin_fp64(const double *G, const double *z, int N, int lane,
+                                              Level level, double &quad, double &lin)
+{
+    quad = 0.0;
+    lin = 0.0;
+    for (int r = lane; r < (N + 1) / 2; r += 32) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int n = h ? N - 1 - r : r;
+            if (h && n == r) break;
+            const double xn = level(n);
+            const double *g = G + (long long)n * N;
+            double s = 0.0;
+            for (int m = n + 1; m < N; ++m) s = fma(g[m], level(m), s);
+            quad = fma(xn, fma(2.0, s, g[n] * xn), quad);
+            lin = fma(xn, z[n], lin);
+        }
+    }
+}
+
 }  // namespace mcmcdet

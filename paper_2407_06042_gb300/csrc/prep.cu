@@ -303,17 +303,10 @@ __global__ void refresh_kernel(RefreshArgs a)
     const int8_t *k = a.states + d.state_off + (long long)c * N;
     const double *G = a.G64 + d.mat_off;
     const double *z = a.z64 + d.vec_off;
-    double quad = 0.0, lin = 0.0;
     bool bad = false;
-    for (int n = lane; n < N; n += 32) {
-        const int kn = k[n];
-        bad |= (kn < 0 || kn >= L);
-        const double xn = odd_of(kn, L);
-        double s = 0.0;
-        for (int m = 0; m < N; ++m) s = fma(G[(long long)n * N + m], (double)odd_of(k[m], L), s);
-        quad = fma(xn, s, quad);
-        lin = fma(xn, z[n], lin);
-    }
+    for (int n = lane; n < N; n += 32) bad |= (k[n] < 0 || k[n] >= L);
+    double quad, lin;
+    quad_lin_fp64(G, z, N, lane, [&](int n) { return (double)odd_of(k[n], L); }, quad, lin);
     for (int o = 16; o; o >>= 1) {
         quad += __shfl_xor_sync(0xffffffffu, quad, o);
         lin += __shfl_xor_sync(0xffffffffu, lin, o);
