@@ -2,24 +2,27 @@
 //
 // Each CTA owns a group of C chains of one channel (persistent over work items). Per transition
 // (Algorithm 1's loop body):
-//   1. every thread draws x'_n for its (dimension, 8 chains) from the cached drift slope of the
-//      current state (Eqs. (15)-(17) / (21)) and writes x' as BF16 (exact odd integers) into the
-//      shared-memory B operand [C chains x K];
+//   1. every thread draws x'_n for its (dimension, 4 chains) from the cached drift slope of the
+//      current state (Eqs. (15)-(17) / (21)), two chains per packed f32x2 instruction, and writes
+//      x' as BF16 (exact odd integers) into the shared-memory B operand [C chains x K];
 //   2. one thread issues D = A * X'^T on the tensor core: A = [Gt | P~ Gt] rows (split into
-//      `split_terms` BF16 terms, FP32 accumulation in TMEM), staged once per work item by a TMA
-//      bulk copy; completion is signalled through an mbarrier;
+//      `split_terms` BF16 terms, FP32 accumulation in TMEM); completion is signalled through an
+//      mbarrier, and the chains' acceptance uniforms are drawn meanwhile. For N <= 128 the A
+//      operand is staged once per work item by a bulk copy; beyond, it is streamed from L2 in
+//      128-row chunks through two buffers (full / empty mbarriers) every transition;
 //   3. every thread reads its TMEM lane (one row of A = one dimension of Gt or P~Gt) for its
-//      16 columns (chains), swaps halves with its partner lane, and evaluates the reverse factor
+//      8 columns (chains), swaps halves with its partner lane, and evaluates the reverse factor
 //      and the energy difference (Eqs. (3), (18));
 //   4. per chain the log acceptance ratio is reduced over dimensions (warp shuffles, then the
 //      four TMEM lane quadrants through shared memory) and the MH test is taken;
 //   5. accepted chains keep x', Gt x' and the drift slope of x'.
 // A-operand row layout (128 rows per tile t): row 32q + l holds dimension 64t + 16q + (l & 15) of
 // Gt (l < 16) or of P~ Gt (l >= 16), so each warp's TMEM quadrant carries both quantities of
-// 16 dimensions; each thread owns one dimension of 4 chains. Both operands are K-major, no swizzle, in 8 x 16-byte core matrices: K-adjacent
-// core matrices 128 B apart (LBO), 8-row groups (K/8)*128 B apart (SBO).
+// 16 dimensions; each thread owns one dimension of 4 chains per tile. Both operands are K-major,
+// no swizzle, in 8 x 16-byte core matrices: K-adjacent core matrices 128 B apart (LBO), 8-row
+// groups (K/8)*128 B apart (SBO).
 // Every wait is bounded: a wait that runs out sets the timeout status bit, the CTA stops issuing
-// work, frees its TMEM and returns.
+// work, waits (bounded) for its copies in flight, frees its TMEM and returns.
 #include "tc_plan.h"
 
 #include <cuda_bf16.h>

@@ -89,10 +89,12 @@ __device__ __forceinline__ uint32_t word_of(const U4 &v, int i)
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// Uniform in (0,1): (2 (w >> 9) + 1) * 2^-24, exactly representable in FP32 and FP64.
+// Uniform in (0,1): (2 (w >> 9) + 1) * 2^-24, exactly representable in FP32 and FP64. In FP32
+// it is formed without a conversion: 1 + m 2^-23 (m = w >> 9 in the mantissa of 1.0f) minus
+// (1 - 2^-24) is exact (Sterbenz) and equals (2m + 1) 2^-24.
 __device__ __forceinline__ float uniform_f(uint32_t w)
 {
-    return (float)(2u * (w >> 9) + 1u) * 5.9604644775390625e-8f;
+    return __fsub_rn(__uint_as_float(0x3F800000u | (w >> 9)), 0.99999994039535522f);
 }
 __device__ __forceinline__ double uniform_d(uint32_t w)
 {

@@ -34,11 +34,18 @@ __device__ __forceinline__ float lg2_approx(float x)
     return y;
 }
 
+// Round to nearest even by adding and removing 1.5 * 2^23 (exact for |x| < 2^22; beyond that the
+// callers' clamp to [0, L-1] gives what rintf would).
+__device__ __forceinline__ float round_even(float x)
+{
+    return __fadd_rn(__fadd_rn(x, 12582912.f), -12582912.f);
+}
+
 // Vertex level j* of the factor (a2, c2 in log2 units, k the current level, inv2c = 1/(2c2)).
 template <int L>
 __device__ __forceinline__ float vertex_level(float a2, float inv2c, float kf)
 {
-    float m = rintf(fmaf(a2, inv2c, kf));
+    float m = round_even(fmaf(a2, inv2c, kf));
     m = fminf(fmaxf(m, 0.f), (float)(L - 1));
     return m;
 }
@@ -203,8 +210,10 @@ __device__ __forceinline__ Poly2<L> rel_poly2(uint64_t a2, float c2, float inv2c
 {
     float v0, v1;
     f2_unpack(f2_fma(a2, f2_splat(inv2c), kf), v0, v1);
-    const float js0 = fminf(fmaxf(rintf(v0), 0.f), (float)(L - 1));
-    const float js1 = fminf(fmaxf(rintf(v1), 0.f), (float)(L - 1));
+    float r0, r1;
+    f2_unpack(f2_add(f2_add(f2_pack(v0, v1), f2_splat(12582912.f)), f2_splat(-12582912.f)), r0, r1);
+    const float js0 = fminf(fmaxf(r0, 0.f), (float)(L - 1));
+    const float js1 = fminf(fmaxf(r1, 0.f), (float)(L - 1));
     const uint64_t js = f2_pack(js0, js1);
     const uint64_t P = f2_fma(f2_splat(-c2), f2_fma(f2_splat(-2.f), kf, js), a2);
     return Poly2<L>{f2_fma(f2_splat(c2), js, P), f2_mul(f2_pack(-js0, -js1), P)};
