@@ -150,14 +150,17 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
  *  best_f   [n_channels]        f(x_best) = -||y - H x_best||^2 / sigma^2 (untempered, FP64)
  *  stats    host mcmc_stats*
  * best_idx/llr/best_f are device pointers when host_io == 0, host pointers when host_io == 1.
+ * best_f is an FP64 evaluation of the best state. The energies entering the LLRs are the tracked
+ * ones (FP64 in FP64 mode; FP32 steps since the last FP64 refresh otherwise, see refresh_period).
  * Synchronises the handle's stream and reports device-side faults. */
 mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr, double *best_f,
                                  mcmc_stats *stats, int32_t host_io);
 
 /* Chain state export: states [sum over channels Np*N_b] int8 level indices, channel-major, then
  * chain-major (chain c of channel b at offset Np*sum_{b'<b} N_b' + c*N_b); f [n_channels*Np]
- * tracked untempered energies of those states (FP64 in FP64 mode, FP64-accumulated FP32
- * differences otherwise). Host or device pointers per host_io. Synchronises. */
+ * untempered energies of those states, FP64 evaluations (FP32 and MIXED runs track them in FP32
+ * steps and they are recomputed in FP64 before they are handed out). Host or device pointers
+ * per host_io. Synchronises. */
 mcmc_status mcmc_detect_get_chains(mcmc_detector *d, int8_t *states, double *f, int32_t host_io);
 
 /* Chain state import (checkpoint restore, or any start point): same layout as get_chains; every

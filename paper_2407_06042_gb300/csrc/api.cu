@@ -79,6 +79,7 @@ struct mcmc_detector {
     long long tot_tc = 0;
     long long transitions = 0;
     bool f_valid = false;   // tracked energies hold the current states' values
+    bool f_exact = true;    // ... to FP64 accuracy (FP32 / MIXED runs track them in FP32 steps)
     bool d_valid = false;   // d_dexp holds Gt x of the current states
 
     // device workspace
@@ -173,7 +174,7 @@ cudaError_t h2d(mcmc_detector *d, void *dst, const void *src, size_t bytes, size
                            cudaMemcpyHostToDevice, d->stream);
 }
 
-mcmc_status ensure_energies(mcmc_detector *d);
+mcmc_status ensure_energies(mcmc_detector *d, bool exact = true);
 
 mcmc_status read_status(mcmc_detector *d)
 {
@@ -229,8 +230,29 @@ namespace {
 // FP64 energies of the current states (and a restart of the running best) when the tracked
 // energies are not valid yet: FP32 / MIXED handles read after preprocess or set_chains without a
 // run in between.
-mcmc_status ensure_energies(mcmc_detector *d)
+mcmc_status ensure_energies(mcmc_detector *d, bool exact)
 {
+    if (d->f_valid && !d->f_exact && exact) {
+        // energies handed out are FP64 evaluations of the current states; the running best
+        // (a state, re-evaluated in FP64 by the read-out) is kept
+        RefreshArgs ra{};
+        ra.desc = P<ChannelDesc>(d->d_desc);
+        ra.states = P<int8_t>(d->d_states);
+        ra.G64 = P<double>(d->d_G64);
+        ra.z64 = P<double>(d->d_z64);
+        ra.yy = P<double>(d->d_yy);
+        ra.f = P<double>(d->d_f);
+        ra.best_f = P<double>(d->d_best_f);
+        ra.best_states = P<int8_t>(d->d_best_states);
+        ra.status = status_ptr(d);
+        ra.n_channels = d->n_channels;
+        ra.chains = d->cfg.chains;
+        ra.reset_best = 0;
+        CK(launch_refresh(ra, d->stream), "energies");
+        d->launches++;
+        d->f_exact = true;
+        return MCMC_OK;
+    }
     if (d->f_valid) return MCMC_OK;
     RefreshArgs ra{};
     ra.desc = P<ChannelDesc>(d->d_desc);
@@ -248,6 +270,7 @@ mcmc_status ensure_energies(mcmc_detector *d)
     CK(launch_refresh(ra, d->stream), "energies");
     d->launches++;
     d->f_valid = true;
+    d->f_exact = true;
     return MCMC_OK;
 }
 
@@ -876,6 +899,7 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         }
     }
     d->f_valid = true;
+    d->f_exact = fp64;
     d->d_valid = !fp64;
     d->transitions += (long long)iterations * d->n_channels * d->cfg.chains;
     return MCMC_OK;
@@ -890,7 +914,7 @@ mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr,
     if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
     {
-        mcmc_status es = ensure_energies(d);
+        mcmc_status es = ensure_energies(d, false);
         if (es != MCMC_OK) return es;
     }
     int8_t *o_idx = best_idx;
@@ -998,6 +1022,7 @@ mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32
     CK(launch_refresh(ra, d->stream), "refresh energies");
     d->launches++;
     d->f_valid = true;
+    d->f_exact = true;
     d->d_valid = false;
     return read_status(d);
 }
@@ -1156,7 +1181,7 @@ mcmc_status mcmc_detect_mix_step(mcmc_detector *d, int64_t t)
     if (st != MCMC_OK) return st;
     if (!d->mlp) return fail(d, MCMC_ESTATE, "no network attached");
     if (t < 1 || t > 0xFFFFFFFFll) return fail(d, MCMC_EINVAL, "t out of range");
-    st = ensure_energies(d);
+    st = ensure_energies(d, false);
     if (st != MCMC_OK) return st;
     const long long rows = d->tot_states / 2;
     for (DevBuf *b : {&d->d_mx_gx, &d->d_mx_px, &d->d_mx_gxp, &d->d_mx_pxp, &d->d_mx_lqf})
@@ -1180,6 +1205,7 @@ mcmc_status mcmc_detect_mix_step(mcmc_detector *d, int64_t t)
     CK(launch_mix(1, a, d->n_channels, d->max_nt, d->stream), "mixture accept kernel");
     d->launches += 4;
     d->d_valid = false;
+    d->f_exact = false;
     long long moved = 0;
     for (const ChannelDesc &c : d->desc)
         if (c.L == L) moved += d->cfg.chains;

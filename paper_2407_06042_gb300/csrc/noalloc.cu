@@ -181,7 +181,9 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
         cudaGetLastError();
         return MCMC_ECUDA;
     }
-    const size_t gj_stage = (size_t)(2 * maxnt * maxnt) * 16;
+    // FP32 Gauss-Jordan block and the copies of its pivot row and column (always in shared
+    // memory, also when the block itself lives in global memory)
+    const size_t gj_stage = (size_t)(maxnt * maxnt + 2 * maxnt) * 8;
     const bool stage_gj = pre && gj_stage <= std::min<size_t>((size_t)optin, 160 * 1024);
     Carver cv{scratch};
     const long long ntc = mat / 4;
@@ -249,7 +251,7 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
     pa.stage_h = h_stage <= std::min<size_t>((size_t)optin, 128 * 1024);
     pa.stage_gj = stage_gj;
     pa.precond_fp32 = 1;
-    NA_CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : 0, pre, s));
+    NA_CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : (size_t)(2 * maxnt) * 8, pre, s));
 
     InitArgs ia{};
     ia.desc = d_desc;

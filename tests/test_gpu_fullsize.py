@@ -50,9 +50,10 @@ def test_full_size_run_properties(bench_batch):
     for ch in SAMPLED:
         t = tg[ch]
         # tracked energies of the final states (FP32 increments, no refresh at this workload)
+        # within the 1e-5 relative bar
         for c in range(0, 64, 7):
             fx = oracle.f_value(t.Hr, t.yr, t.sigma2, t.values(st[ch][c]))
-            assert abs(f[ch * 64 + c] - fx) <= 2e-4 * abs(fx) + 1e-2, (ch, c)
+            assert abs(f[ch * 64 + c] - fx) <= 1e-5 * abs(fx), (ch, c, f[ch * 64 + c], fx)
         # best sample: its FP64 energy is the reported best_f and no final state beats it
         lab = out["best_idx"][ch * 32:(ch + 1) * 32]
         kb = H.levels_from_labels(lab, 32, 8)
