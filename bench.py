@@ -161,33 +161,61 @@ def profiled_traffic(precision):
 
 
 def chain_roofline(precision, w, units, chain_ms, batch=None):
-    """Roofline of the chain loop (the dominant kernel). Its binding resource is the proposal
-    arithmetic: per chain-iteration the method evaluates, for every real dimension, two
-    categorical factors of L weights (one exponential each) and their two log-normalisers, plus
-    one log per MH test. Those transcendental operations run on the MUFU pipe, whose measured
-    ex2 rate is the peak. The Gram products (tensor pipe, MIXED) are reported beside it."""
+    """Roofline of the chain loop (the dominant kernel), from the method's algorithmic work per
+    chain-iteration (one MH transition of one chain; Algorithm 1 with the proposal of the
+    current state carried over, N real dimensions, L levels):
+      - MUFU: N L exponentials (the factor weights of x') + N log-normalisers + 1 log (MH test);
+      - FP32: about 5 N L + 4 N operations (per level: logit, running sum, search; per
+        dimension: slope, energy term, accumulations), plus the Gram products' N 2N FMAs when
+        they run on the CUDA cores (plain FP32 sampler);
+      - tensor: 2 N 2N Gram flops (D' = X'[Gt | P~Gt]; 2 N N without the preconditioner);
+      - HBM: the operand block and the states once per work item (no per-transition traffic).
+    Each pipe's time is its work over its measured peak on this GPU; the pipe with the largest
+    time is the bound, and the line reports that pipe's achieved rate over its peak. The other
+    pipes are reported beside it."""
+    pre = bool(w.get("preconditioned", True))
     if batch is not None and len(set(batch.nt.tolist())) > 1:
         Ns = 2 * batch.nt.astype(np.float64)
         Ls = np.sqrt(batch.qam.astype(np.float64))
         N, L = float(Ns.mean()), float(Ls.mean())
-        per_ci = float((Ns * (2 * Ls + 2) + 1).mean())
-        gemm = float((2 * Ns * 2 * Ns).mean())
+        mufu = float((Ns * (Ls + 1) + 1).mean())
+        fp32 = float((5 * Ns * Ls + 4 * Ns).mean())
+        gemm = float((2 * Ns * (2 if pre else 1) * Ns).mean())
     else:
         N = 2 * w["nt"]
         L = int(np.sqrt(w["qam"]))
-        per_ci = N * (2 * L + 2) + 1
-        gemm = 2 * N * (2 * N)
+        mufu = N * (L + 1) + 1
+        fp32 = 5 * N * L + 4 * N
+        gemm = 2 * N * (2 if pre else 1) * N
+    fp32_label = "5NL+4N"
+    if precision != "mixed":
+        fp32 += gemm / 2          # the Gram products as FMAs on the CUDA cores
+        fp32_label += " + Gram FMAs"
     peaks = pipe_peaks() or {}
     t = chain_ms * 1e-3
-    achieved = per_ci * units / t
-    peak = peaks.get("ex2")
-    out = {"bound": "alu", "achieved": achieved / 1e9,
-           "peak": (peak / 1e9) if peak else None, "unit": "Gop/s",
-           "frac": (achieved / peak) if peak else None,
-           "traffic": profiled_traffic(precision),
-           "pipe": "MUFU transcendental (ex2/lg2), measured ex2 rate of this GPU",
-           "per_unit": f"{per_ci:g} transcendental ops per chain-iteration (N(2L+2)+1, N={N:g}, L={L:g})",
-           "launch_ms": chain_ms, "peaks_measured": peaks}
+    pipes = {
+        "mufu": {"ops": mufu, "peak": peaks.get("ex2"),
+                 "per_unit": f"{mufu:g} transcendental ops per chain-iteration (N(L+1)+1, N={N:g}, L={L:g})",
+                 "pipe": "MUFU ex2/lg2, measured ex2 rate of this GPU"},
+        "fp32": {"ops": fp32, "peak": peaks.get("fma"),
+                 "per_unit": f"{fp32:g} FP32 ops per chain-iteration ({fp32_label}, N={N:g}, L={L:g})",
+                 "pipe": "FP32 lanes, measured FMA rate of this GPU"},
+    }
+    for v in pipes.values():
+        v["achieved"] = v["ops"] * units / t
+        v["frac"] = (v["achieved"] / v["peak"]) if v["peak"] else None
+    known = [k for k in pipes if pipes[k]["peak"]]
+    bind = max(known, key=lambda k: pipes[k]["ops"] / pipes[k]["peak"]) if known else "fp32"
+    pb = pipes[bind]
+    out = {"bound": "alu", "achieved": pb["achieved"] / 1e9,
+           "peak": (pb["peak"] / 1e9) if pb["peak"] else None, "unit": "Gop/s",
+           "frac": pb["frac"], "traffic": profiled_traffic(precision),
+           "pipe": pb["pipe"], "per_unit": pb["per_unit"], "launch_ms": chain_ms,
+           "other_pipes": {k: {"achieved_gops": v["achieved"] / 1e9,
+                               "peak_gops": (v["peak"] / 1e9) if v["peak"] else None,
+                               "frac": v["frac"], "per_unit": v["per_unit"]}
+                           for k, v in pipes.items() if k != bind},
+           "peaks_measured": peaks}
     if precision == "mixed":
         tf = gemm * units / t / 1e12
         out["tensor"] = {"achieved_tflops": tf, "peak_tflops": 1899.4, "frac": tf / 1899.4,

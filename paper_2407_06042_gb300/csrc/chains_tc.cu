@@ -2,9 +2,12 @@
 //
 // Each CTA owns a group of C chains of one channel (persistent over work items). Per transition
 // (Algorithm 1's loop body):
-//   1. every thread draws x'_n for its (dimension, 4 chains) from the cached drift slope of the
+//   1. every thread draws x'_n for its (dimension, 4 chains) from the proposal factors of the
 //      current state (Eqs. (15)-(17) / (21)), two chains per packed f32x2 instruction, and writes
-//      x' as BF16 (exact odd integers) into the shared-memory B operand [C chains x K];
+//      x' as BF16 (exact odd integers) into the shared-memory B operand [C chains x K]. The
+//      factors are carried from transition to transition in tensor memory (Algorithm 1 keeps
+//      q(.|x) while x stays); a warp rebuilds its tables from the drift slopes only after one of
+//      its chains moved;
 //   2. one thread issues D = A * X'^T on the tensor core: A = [Gt | P~ Gt] rows (split into
 //      `split_terms` BF16 terms, FP32 accumulation in TMEM); completion is signalled through an
 //      mbarrier, and the chains' acceptance uniforms are drawn meanwhile. For N <= 128 the A
@@ -299,6 +302,45 @@ __device__ __forceinline__ void tc_read_tile(const TcCtx &x, int t, float (&g)[4
     }
 }
 
+// Carried proposal factors in tensor memory (tiles of resident-operand kernels): per thread and
+// tile 48 columns past the accumulators, the cumulative weights of its two chain pairs at +0 and
+// +16 and their polynomial and log-normalisers at +32 and +40.
+__host__ __device__ constexpr int tc_table_cols(int MT, int C) { return tc_streamed(MT) ? 0 : 6 * MT * C; }
+
+template <int L>
+__device__ __forceinline__ void table_store(uint32_t ta, uint32_t te, const Table2<L> &tb)
+{
+    uint32_t s[2 * L], e[8];
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        s[j] = __float_as_uint(tb.S0[j]);
+        s[L + j] = __float_as_uint(tb.S1[j]);
+    }
+    float v[6];
+    f2_unpack(tb.B, v[0], v[1]);
+    f2_unpack(tb.C0, v[2], v[3]);
+    f2_unpack(tb.lgS, v[4], v[5]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) e[j] = __float_as_uint(v[j]);
+    e[6] = e[7] = 0u;
+    tmem_st_pair<2 * L>(ta, te, s, e);
+}
+
+template <int L>
+__device__ __forceinline__ void table_load(uint32_t ta, uint32_t te, Table2<L> &tb)
+{
+    uint32_t s[2 * L], e[8];
+    tmem_ld_pair<2 * L>(ta, te, s, e);
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        tb.S0[j] = __uint_as_float(s[j]);
+        tb.S1[j] = __uint_as_float(s[L + j]);
+    }
+    tb.B = f2_pack(__uint_as_float(e[0]), __uint_as_float(e[1]));
+    tb.C0 = f2_pack(__uint_as_float(e[2]), __uint_as_float(e[3]));
+    tb.lgS = f2_pack(__uint_as_float(e[4]), __uint_as_float(e[5]));
+}
+
 // One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
 // every chain column is live, so no per-(dimension, chain) validity test is needed. Levels are
 // held as exact small floats.
@@ -358,6 +400,14 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         k2[t][0] = f2_pack(kv[0], kv[1]);
         k2[t][1] = f2_pack(kv[2], kv[3]);
     }
+    // Algorithm 1 carries q(.|x) of the current state from one transition to the next: the
+    // resident-operand kernels keep every thread's factor tables in tensor memory and rebuild
+    // them (for the whole warp) only after one of its chains moved. Rebuilt tables equal the
+    // carried ones bit for bit, so the draws do not depend on where a table came from.
+    constexpr bool kCache = !tc_streamed(MT);
+    const uint32_t tcache =
+        x.tmem + ((32u * (uint32_t)x.q) << 16) + (uint32_t)(MT * C + 48 * MT * x.cgi);
+    bool stale = true;
     double fcur = 0.0, fbest = 0.0;
     unsigned cnt = 0;
     if (x.tid < nC) {
@@ -453,7 +503,9 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         const uint32_t t_it = (uint32_t)(A.t_offset + 1 + i);
         uint64_t part2[2] = {0ull, 0ull}, dpart2[2] = {0ull, 0ull};
         uint64_t kp2[MT][2];
-        // 1. proposal draw (log2 q(x'|x) accumulated with a minus sign)
+        // 1. proposal draw (log2 q(x'|x) accumulated with a minus sign) from the carried factors
+        const bool fresh = !kCache || __any_sync(0xffffffffu, stale);
+        stale = false;
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             const int n = nd[t];
@@ -463,9 +515,17 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                                   (uint32_t)((it.c0 + cbase) >> 2), A.key0, A.key1);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
+                Table2<L> tb;
+                const uint32_t ta = tcache + 48u * t + 16u * p, te = tcache + 48u * t + 32u + 8u * p;
+                if (fresh) {
+                    factor_table_f2<L>(sl2[t][p], c2, inv2c, k2[t][p], tb);
+                    if constexpr (kCache) table_store<L>(ta, te, tb);
+                } else {
+                    table_load<L>(ta, te, tb);
+                }
                 uint64_t sel, lq;
-                factor_draw_f2<L>(sl2[t][p], c2, inv2c, k2[t][p], uniform_f(word_of(w, 2 * p)),
-                                  uniform_f(word_of(w, 2 * p + 1)), sel, lq);
+                table_draw_f2<L>(tb, c2, uniform_f(word_of(w, 2 * p)), uniform_f(word_of(w, 2 * p + 1)),
+                                 sel, lq);
                 if (!FULL) {
                     float s[2], kk[2], q[2];
                     f2_unpack(sel, s[0], s[1]);
@@ -570,6 +630,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             for (int h = 0; h < 2; ++h) {
                 const int c = cbase + 2 * p + h;
                 fl[h] = (FULL || c < nC) ? x.sacc[c] : 0;
+                if (fl[h] & 1) stale = true;   // x' taken: its factors are not the carried ones
             }
             if constexpr (kReread) continue;
 #pragma unroll
@@ -905,7 +966,7 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
     plan->max_n = max_n;
     plan->split_terms = S;
     plan->threads = 16 * C;                   // 4 TMEM quadrants x C/8 column groups x 32
-    plan->tmem_cols = pow2_at_least(MT * C);
+    plan->tmem_cols = pow2_at_least(MT * C + tc_table_cols(MT, C));   // accumulators + carried factors
     // resident CTAs per SM: shared memory, threads, registers (the launch bounds allow 64 per
     // thread for one tile, 128 beyond), and TMEM
     const int regs = MT == 1 ? 65536 / (TC_MIN_BLOCKS * 512) : 128;

@@ -128,42 +128,6 @@ __device__ __forceinline__ float factor_log2q(float a2, float c2, float inv2c, i
     return rel_logit2(p, c2, (float)j_eval) - lg2_approx(S[L - 1]);
 }
 
-// Float-level forms (levels held as exact small floats, no integer conversions): draw returns the
-// level as a float.
-template <int L>
-__device__ __forceinline__ float factor_draw_f(float a2, float c2, float inv2c, float kf, float u,
-                                               float &log2q)
-{
-    float S[L];
-    const Poly p = factor_cumulative<L>(a2, c2, inv2c, kf, S);
-    const float target = u * S[L - 1];
-    float sel;
-    if constexpr (L == 2) {
-        sel = S[0] <= target ? 1.f : 0.f;
-    } else if constexpr (L == 4) {
-        const bool b1 = S[1] <= target;
-        const bool b0 = (b1 ? S[2] : S[0]) <= target;
-        sel = (b1 ? 2.f : 0.f) + (b0 ? 1.f : 0.f);
-    } else {
-        const bool b2 = S[3] <= target;
-        const bool b1 = (b2 ? S[5] : S[1]) <= target;
-        const float m = b2 ? (b1 ? S[6] : S[4]) : (b1 ? S[2] : S[0]);
-        const bool b0 = m <= target;
-        sel = (b2 ? 4.f : 0.f) + (b1 ? 2.f : 0.f) + (b0 ? 1.f : 0.f);
-    }
-    log2q = rel_logit2(p, c2, sel) - lg2_approx(S[L - 1]);
-    return sel;
-}
-
-template <int L>
-__device__ __forceinline__ float factor_log2q_f(float a2, float c2, float inv2c, float kf,
-                                                float jf)
-{
-    float S[L];
-    const Poly p = factor_cumulative<L>(a2, c2, inv2c, kf, S);
-    return rel_logit2(p, c2, jf) - lg2_approx(S[L - 1]);
-}
-
 // ------------------------------------------------------------------------------------------
 // Two chains per instruction: the same arithmetic on packed FP32 pairs (sm_100+ f32x2 add / mul
 // / fma, each lane rounded like its scalar counterpart), so a pair's results are bit-identical
@@ -225,38 +189,40 @@ __device__ __forceinline__ uint64_t rel_logit2_2(const Poly2<L> &p, uint64_t mc2
     return f2_fma(f2_fma(mc2, jf, p.B), jf, p.C0);
 }
 
-// Smallest level count evaluated in packed pairs (below it the two chains run the scalar code;
-// both give identical results).
-#ifndef TC_PAIR_MIN_L
-#define TC_PAIR_MIN_L 2
-#endif
-
-// factor_draw_f for two chains: levels (as floats) and log2 q of the drawn levels.
+// The proposal factor of two chains at their current levels, as Algorithm 1 carries it from one
+// transition to the next: the cumulative weights S_j of each chain, the relative-logit
+// polynomial and log2 of each total weight.
 template <int L>
-__device__ __forceinline__ void factor_draw_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
-                                               float u0, float u1, uint64_t &sel, uint64_t &log2q)
+struct Table2 {
+    float S0[L], S1[L];
+    uint64_t B, C0, lgS;
+};
+
+template <int L>
+__device__ __forceinline__ void factor_table_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
+                                                Table2<L> &tb)
 {
-    if constexpr (L < TC_PAIR_MIN_L) {
-        float a0, a1, k0, k1, q0, q1;
-        f2_unpack(a2, a0, a1);
-        f2_unpack(kf, k0, k1);
-        const float s0 = factor_draw_f<L>(a0, c2, inv2c, k0, u0, q0);
-        const float s1 = factor_draw_f<L>(a1, c2, inv2c, k1, u1, q1);
-        sel = f2_pack(s0, s1);
-        log2q = f2_pack(q0, q1);
-        return;
-    }
     const Poly2<L> p = rel_poly2<L>(a2, c2, inv2c, kf);
     const uint64_t mc2 = f2_splat(-c2);
-    float S0[L], S1[L];
     uint64_t acc = 0ull;   // (+0.f, +0.f)
 #pragma unroll
     for (int j = 0; j < L; ++j) {
         float l0, l1;
         f2_unpack(rel_logit2_2(p, mc2, f2_splat((float)j)), l0, l1);
         acc = f2_add(acc, f2_pack(ex2_approx(l0), ex2_approx(l1)));
-        f2_unpack(acc, S0[j], S1[j]);
+        f2_unpack(acc, tb.S0[j], tb.S1[j]);
     }
+    tb.B = p.B;
+    tb.C0 = p.C0;
+    tb.lgS = f2_pack(lg2_approx(tb.S0[L - 1]), lg2_approx(tb.S1[L - 1]));
+}
+
+// Draw from a table with uniforms (u0, u1): the levels (as floats) and log2 q of them.
+template <int L>
+__device__ __forceinline__ void table_draw_f2(const Table2<L> &tb, float c2, float u0, float u1,
+                                              uint64_t &sel, uint64_t &log2q)
+{
+    const float *S0 = tb.S0, *S1 = tb.S1;
     float t0, t1;
     f2_unpack(f2_mul(f2_pack(u0, u1), f2_pack(S0[L - 1], S1[L - 1])), t0, t1);
     float s0, s1;
@@ -278,23 +244,25 @@ __device__ __forceinline__ void factor_draw_f2(uint64_t a2, float c2, float inv2
         s1 = (b2b ? 4.f : 0.f) + (b1 ? 2.f : 0.f) + (b0 ? 1.f : 0.f);
     }
     sel = f2_pack(s0, s1);
-    float r0, r1;
-    f2_unpack(rel_logit2_2(p, mc2, sel), r0, r1);
-    log2q = f2_pack(r0 - lg2_approx(S0[L - 1]), r1 - lg2_approx(S1[L - 1]));
+    // log2 q = l2(sel) - log2 S_{L-1}, each lane rounded once as r - lg
+    log2q = f2_fma(f2_splat(-1.f), tb.lgS, rel_logit2_2(Poly2<L>{tb.B, tb.C0}, f2_splat(-c2), sel));
 }
 
-// factor_log2q_f for two chains: log2 q(j_eval | level k) of each.
+// factor_draw for two chains: levels (as exact small floats) and log2 q of the drawn levels.
+template <int L>
+__device__ __forceinline__ void factor_draw_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
+                                               float u0, float u1, uint64_t &sel, uint64_t &log2q)
+{
+    Table2<L> tb;
+    factor_table_f2<L>(a2, c2, inv2c, kf, tb);
+    table_draw_f2<L>(tb, c2, u0, u1, sel, log2q);
+}
+
+// factor_log2q for two chains: log2 q(j_eval | level k) of each (levels as floats).
 template <int L>
 __device__ __forceinline__ uint64_t factor_log2q_f2(uint64_t a2, float c2, float inv2c, uint64_t kf,
                                                     uint64_t jf)
 {
-    if constexpr (L < TC_PAIR_MIN_L) {
-        float a0, a1, k0, k1, j0, j1;
-        f2_unpack(a2, a0, a1);
-        f2_unpack(kf, k0, k1);
-        f2_unpack(jf, j0, j1);
-        return f2_pack(factor_log2q_f<L>(a0, c2, inv2c, k0, j0), factor_log2q_f<L>(a1, c2, inv2c, k1, j1));
-    }
     const Poly2<L> p = rel_poly2<L>(a2, c2, inv2c, kf);
     const uint64_t mc2 = f2_splat(-c2);
     uint64_t acc = 0ull;
