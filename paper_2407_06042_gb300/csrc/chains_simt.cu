@@ -290,8 +290,8 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
         // 1. proposal draw, four chains per Philox block
         for (int q = threadIdx.x; q < (nC / 4) * N; q += blockDim.x) {
             const int cq4 = q / N, n = q % N;
-            const U4 w = philox4x32_10(t, (uint32_t)n, (uint32_t)it.b,
-                                       (uint32_t)((it.c0 >> 2) + cq4), A.key0, A.key1);
+            const U4 w = philox4x32_10_rk(t, (uint32_t)n, (uint32_t)it.b,
+                                          (uint32_t)((it.c0 >> 2) + cq4), A.philox_rk);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int c = 4 * cq4 + j;
@@ -329,8 +329,8 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
             }
             if (lane == 0) {
                 const int cc = it.c0 + c;
-                const U4 w = philox4x32_10(t, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
-                                           A.key0, A.key1);
+                const U4 w = philox4x32_10_rk(t, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
+                                              A.philox_rk);
                 const T logr = s + cf * sd;
                 const T loga = logr < T(0) ? logr : T(0);
                 const T u = M<T>::uni(word_of(w, cc & 3));
@@ -418,9 +418,11 @@ size_t chain_smem_bytes_simt(int elem_size, int cg, int max_n, int max_nop, bool
     return make_layout(elem_size, cg, max_n, max_nop, bt_in_smem).total;
 }
 
-cudaError_t launch_chains_simt(const ChainArgs &a, bool fp64, size_t smem, cudaStream_t s)
+cudaError_t launch_chains_simt(const ChainArgs &a_in, bool fp64, size_t smem, cudaStream_t s)
 {
-    if (a.n_items <= 0) return cudaSuccess;
+    if (a_in.n_items <= 0) return cudaSuccess;
+    ChainArgs a = a_in;
+    philox_round_keys(a.key0, a.key1, a.philox_rk);
     cudaError_t e;
     if (fp64) {
         auto k = chains_simt_kernel<double, 4, 4>;

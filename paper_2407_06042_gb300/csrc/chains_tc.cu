@@ -37,7 +37,11 @@ namespace mcmcdet {
 
 namespace {
 
-// Resident CTAs per SM the register allocation is sized for (512 threads each).
+// Launch bounds of the one-tile kernel: at most TC_MAX_THREADS threads per CTA (16 per chain),
+// registers sized for TC_MIN_BLOCKS such CTAs per SM.
+#ifndef TC_MAX_THREADS
+#define TC_MAX_THREADS 512
+#endif
 #ifndef TC_MIN_BLOCKS
 #define TC_MIN_BLOCKS 2
 #endif
@@ -511,8 +515,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             const int n = nd[t];
             U4 w = {0, 0, 0, 0};
             if (FULL || live[t][0])
-                w = philox4x32_10(t_it, (uint32_t)n, (uint32_t)it.b,
-                                  (uint32_t)((it.c0 + cbase) >> 2), A.key0, A.key1);
+                w = philox4x32_10_rk(t_it, (uint32_t)n, (uint32_t)it.b,
+                                     (uint32_t)((it.c0 + cbase) >> 2), A.philox_rk);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 Table2<L> tb;
@@ -548,8 +552,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         float logu = 0.f;
         if (x.tid < nC) {
             const int cc = it.c0 + x.tid;
-            const U4 w = philox4x32_10(t_it, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
-                                       A.key0, A.key1);
+            const U4 w = philox4x32_10_rk(t_it, kMhStream, (uint32_t)it.b, (uint32_t)(cc >> 2),
+                                          A.philox_rk);
             logu = lg2_approx(uniform_f(word_of(w, cc & 3)));
         }
         const bool mma_ok = tc_gemm_wait<MT>(x, i + 1 < A.iterations);
@@ -765,7 +769,7 @@ __device__ __forceinline__ void tc_item_dispatch(const ChainArgs &A, TcCtx &x, c
 }
 
 template <int MT>
-__global__ void __launch_bounds__(512, MT == 1 ? TC_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
     chains_tc_kernel(const ChainArgs A, const int C, const int S, const int Kp)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -953,6 +957,7 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
     *plan = TcPlan{};
     if (max_n < 1 || max_n > kMaxN) return false;
     if (chains_per_cta < 16 || chains_per_cta > 32 || chains_per_cta % 16) return false;
+    if (16 * chains_per_cta > TC_MAX_THREADS) return false;
     const int MT = (max_n + 63) / 64;
     const int Kp = (max_n + 15) / 16 * 16;
     const int C = chains_per_cta;
@@ -967,9 +972,10 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
     plan->split_terms = S;
     plan->threads = 16 * C;                   // 4 TMEM quadrants x C/8 column groups x 32
     plan->tmem_cols = pow2_at_least(MT * C + tc_table_cols(MT, C));   // accumulators + carried factors
-    // resident CTAs per SM: shared memory, threads, registers (the launch bounds allow 64 per
-    // thread for one tile, 128 beyond), and TMEM
-    const int regs = MT == 1 ? 65536 / (TC_MIN_BLOCKS * 512) : 128;
+    // resident CTAs per SM: shared memory, threads, registers (as the launch bounds allow: 64
+    // per thread for one tile, 128 beyond, at the default bounds), and TMEM
+    const int regs = std::min(255, (MT == 1 ? 65536 / (TC_MIN_BLOCKS * TC_MAX_THREADS)
+                                            : 65536 / TC_MAX_THREADS) / 8 * 8);
     const int by_smem = (int)(228 * 1024 / (L.total + 1024));
     const int by_thr = std::min(2048 / plan->threads, 65536 / (plan->threads * regs));
     const int by_occ = std::min(by_smem, by_thr);
@@ -999,6 +1005,7 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
     if (a_in.n_items <= 0) return cudaSuccess;
     ChainArgs a = a_in;
     a.tc_tmem_cols = plan.tmem_cols;
+    philox_round_keys(a.key0, a.key1, a.philox_rk);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
