@@ -68,7 +68,7 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 
 // Shared-memory layout of the kernel (bytes).
 struct TcLayout {
-    uint32_t a, b, red, dred, acc, impr, ref, fref, kb, dg, bar, tmem, total;
+    uint32_t a, b, red, dred, acc, impr, ref, fst, cnt, fref, kb, dg, bar, tmem, total;
 };
 
 // The A operand stays resident for MT <= 2 (N <= 128). Beyond that it no longer fits one SM's
@@ -92,6 +92,8 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
     L.acc = take((uint32_t)C * 4, 16);
     L.impr = take((uint32_t)C * 4, 16);
     L.ref = take((uint32_t)C * 8, 16);       // FP64 refresh results per chain
+    L.fst = take((uint32_t)C * 16, 16);      // tracked and best energies per chain
+    L.cnt = take((uint32_t)C * 4, 16);       // accepted moves per chain
     L.fref = take((uint32_t)C * kMaxN, 16);  // states for the FP64 refresh
     L.kb = take((uint32_t)C * kMaxN, 16);    // best visited state of every chain
     // streamed kernels: Gt x of every thread's (tile, chain pair), [2 MT][threads] packed pairs
@@ -116,6 +118,8 @@ struct TcCtx {
     float *red, *dred;
     int *sacc, *simpr;
     double *sref;
+    double *sfc, *sfb;            // tracked and best energies of the CTA's chains
+    unsigned *scnt;
     int8_t *sfs;
     int8_t *skb;
     uint64_t *sdg;                // Gt x pairs in shared memory (streamed kernels)
@@ -412,12 +416,13 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     const uint32_t tcache =
         x.tmem + ((32u * (uint32_t)x.q) << 16) + (uint32_t)(MT * C + 48 * MT * x.cgi);
     bool stale = true;
-    double fcur = 0.0, fbest = 0.0;
-    unsigned cnt = 0;
+    // chain x.tid's tracked and best energies and accept count live in shared memory (read and
+    // written by that thread only)
     if (x.tid < nC) {
         const long long ci = (long long)it.b * A.chains + it.c0 + x.tid;
-        fcur = A.f[ci];
-        fbest = A.best_f[ci];
+        x.sfc[x.tid] = A.f[ci];
+        x.sfb[x.tid] = A.best_f[ci];
+        x.scnt[x.tid] = 0u;
     }
     const uint64_t two2 = f2_splat(2.f), mlm1 = f2_splat(-lm1), mone = f2_splat(-1.f);
     // x as BF16 into the B operand: bits of the exact float 2k - (L-1); dead slots write 0
@@ -497,8 +502,9 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             const int c = x.tid;
             const double l = (double)x.red[c] + x.red[C + c] + x.red[2 * C + c] + x.red[3 * C + c];
             const double qd = (double)x.dred[c] + x.dred[C + c] + x.dred[2 * C + c] + x.dred[3 * C + c];
-            fcur = -(A.yy[it.b] - 2.0 * l + qd) * d.inv_s2;
-            fbest = fcur;
+            const double f0 = -(A.yy[it.b] - 2.0 * l + qd) * d.inv_s2;
+            x.sfc[c] = f0;
+            x.sfb[c] = f0;
         }
         __syncthreads();
     }
@@ -619,9 +625,10 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             if (!isfinite(logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
             int im = 0;
             if (ok) {
-                fcur += d.inv_s2 * (double)sd;
-                cnt += 1;
-                if (fcur > fbest) { fbest = fcur; im = 1; }
+                const double fc = x.sfc[c] + d.inv_s2 * (double)sd;
+                x.sfc[c] = fc;
+                x.scnt[c] += 1u;
+                if (fc > x.sfb[c]) { x.sfb[c] = fc; im = 1; }
             }
             x.sacc[c] = ok | (im << 1);
         }
@@ -729,9 +736,9 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             }
             __syncthreads();
             if (x.tid < nC) {
-                const double dr = fabs(x.sref[x.tid] - fcur);
+                const double dr = fabs(x.sref[x.tid] - x.sfc[x.tid]);
                 atomicMax(A.drift_bits, (unsigned long long)__double_as_longlong(dr));
-                fcur = x.sref[x.tid];
+                x.sfc[x.tid] = x.sref[x.tid];
             }
         }
     }
@@ -754,9 +761,9 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     }
     if (x.tid < nC) {
         const long long ci = (long long)it.b * A.chains + it.c0 + x.tid;
-        A.f[ci] = fcur;
-        A.best_f[ci] = fbest;
-        A.accepts[ci] += cnt;
+        A.f[ci] = x.sfc[x.tid];
+        A.best_f[ci] = x.sfb[x.tid];
+        A.accepts[ci] += x.scnt[x.tid];
     }
 }
 
@@ -782,6 +789,9 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
     x.sacc = reinterpret_cast<int *>(smem + lay.acc);
     x.simpr = reinterpret_cast<int *>(smem + lay.impr);
     x.sref = reinterpret_cast<double *>(smem + lay.ref);
+    x.sfc = reinterpret_cast<double *>(smem + lay.fst);
+    x.sfb = x.sfc + C;
+    x.scnt = reinterpret_cast<unsigned *>(smem + lay.cnt);
     x.sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
     x.skb = reinterpret_cast<int8_t *>(smem + lay.kb);
     x.sdg = reinterpret_cast<uint64_t *>(smem + lay.dg);
