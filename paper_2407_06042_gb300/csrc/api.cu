@@ -72,6 +72,7 @@ struct mcmc_detector {
     std::vector<ChannelDesc> desc;
     std::vector<Choice> choice;     // per channel
     std::vector<Group> groups;
+    std::vector<DevBuf> spare_items;   // work-item buffers of earlier batches, reused
     cudaGraphExec_t graph = nullptr;
     int tuned_classes = 0;
     int max_n = 0, max_nop = 0, max_nt = 0, max_nr = 0;
@@ -87,6 +88,12 @@ struct mcmc_detector {
         d_w32, d_bt32, d_bt64, d_tc, d_states, d_best_states, d_f, d_best_f, d_accepts,
         d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp;
     HostBuf h_stage;
+    // pinned staging ring for the per-batch tables (descriptors, work items): a slot is rewritten
+    // only after the copy that last read it has completed
+    static constexpr int kUpSlots = 4;
+    HostBuf h_up[kUpSlots];
+    cudaEvent_t up_done[kUpSlots] = {};
+    int up_next = 0;
 
     // learned proposal (not owned network; scratch of the mixture move)
     mcmc_mlp *mlp = nullptr;
@@ -161,6 +168,27 @@ bool is_pinned_or_device(const void *p)
     }
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice ||
            at.type == cudaMemoryTypeManaged;
+}
+
+// Host-to-device copy of a host table built by the library (descriptors, work items) through the
+// pinned staging ring. A copy from pageable memory would first wait for all work queued on the
+// stream; this one waits, at most, for the copy issued kUpSlots uploads earlier.
+cudaError_t upload(mcmc_detector *d, void *dst, const void *src, size_t bytes)
+{
+    if (bytes == 0) return cudaSuccess;
+    const int k = d->up_next;
+    d->up_next = (k + 1) % mcmc_detector::kUpSlots;
+    cudaError_t e;
+    if (!d->up_done[k]) {
+        if ((e = cudaEventCreateWithFlags(&d->up_done[k], cudaEventDisableTiming)) != cudaSuccess) return e;
+    } else if ((e = cudaEventSynchronize(d->up_done[k])) != cudaSuccess) {
+        return e;
+    }
+    if ((e = ensure_host(d->h_up[k], bytes)) != cudaSuccess) return e;
+    std::memcpy(d->h_up[k].p, src, bytes);
+    if ((e = cudaMemcpyAsync(dst, d->h_up[k].p, bytes, cudaMemcpyHostToDevice, d->stream)) != cudaSuccess)
+        return e;
+    return cudaEventRecord(d->up_done[k], d->stream);
 }
 
 // Host-to-device copy: direct from pinned memory, else through the handle's pinned staging
@@ -322,15 +350,24 @@ Choice default_choice(const mcmc_detector *d, const ChannelDesc &c)
 mcmc_status build_groups(mcmc_detector *d)
 {
     const int Np = d->cfg.chains;
-    std::map<std::tuple<int, int, int>, std::vector<int>> by;   // (engine, tile, N-class) -> channels
+    using GroupKey = std::tuple<int, int, int>;   // (engine, tile, N-class)
+    std::map<GroupKey, std::vector<int>> by;
+    GroupKey last{-1, -1, -1};
+    std::vector<int> *last_v = nullptr;           // batches usually repeat one class for long runs
     for (int b = 0; b < d->n_channels; ++b) {
         const Choice ch = d->choice[b];
         const ChannelDesc &c = d->desc[b];
         const int cls = ch.engine == MCMC_ENGINE_TC ? (c.N + 15) / 16 * 16 : c.N;
-        by[{ch.engine, ch.tile, cls}].push_back(b);
+        const GroupKey key{ch.engine, ch.tile, cls};
+        if (!last_v || key != last) {
+            last = key;
+            last_v = &by[key];
+        }
+        last_v->push_back(b);
     }
+    // keep the work-item buffers: freeing device memory would synchronise the device
     for (auto &g : d->groups)
-        if (g.d_items.p) cudaFree(g.d_items.p);
+        if (g.d_items.p) d->spare_items.push_back(g.d_items);
     d->groups.clear();
     for (auto &kv : by) {
         Group g;
@@ -347,12 +384,16 @@ mcmc_status build_groups(mcmc_detector *d)
             if (g.tile <= 0 || !simt_fit(d, g.tile, g.max_n, g.max_nop, &g.bt_smem, &g.smem))
                 return fail(d, MCMC_EUNSUPPORTED, "channels of N = %d do not fit the CUDA-core kernel", g.max_n);
         }
+        g.items.reserve(kv.second.size() * (size_t)((Np + g.tile - 1) / g.tile));
         for (int b : kv.second)
             for (int c0 = 0; c0 < Np; c0 += g.tile)
                 g.items.push_back(WorkItem{b, c0, std::min(g.tile, Np - c0), 0});
+        if (!d->spare_items.empty()) {
+            g.d_items = d->spare_items.back();
+            d->spare_items.pop_back();
+        }
         CK(ensure(g.d_items, sizeof(WorkItem) * g.items.size()), "alloc items");
-        CK(cudaMemcpyAsync(g.d_items.p, g.items.data(), sizeof(WorkItem) * g.items.size(),
-                           cudaMemcpyHostToDevice, d->stream), "copy items");
+        CK(upload(d, g.d_items.p, g.items.data(), sizeof(WorkItem) * g.items.size()), "copy items");
         d->groups.push_back(std::move(g));
     }
     return MCMC_OK;
@@ -608,8 +649,14 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
         if (b->p) cudaFree(b->p);
     for (auto &g : d->groups)
         if (g.d_items.p) cudaFree(g.d_items.p);
+    for (auto &b : d->spare_items)
+        if (b.p) cudaFree(b.p);
     if (d->graph) cudaGraphExecDestroy(d->graph);
     if (d->h_stage.p) cudaFreeHost(d->h_stage.p);
+    for (int k = 0; k < mcmc_detector::kUpSlots; ++k) {
+        if (d->up_done[k]) cudaEventDestroy(d->up_done[k]);
+        if (d->h_up[k].p) cudaFreeHost(d->h_up[k].p);
+    }
     if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
     cudaGetLastError();
     delete d;
@@ -691,11 +738,18 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     d->choice.assign(n_channels, Choice{});
     {
         std::lock_guard<std::mutex> lk(g_tuned_mu);
+        int lastN = -1, lastL = -1;
+        Choice lastc{};
         for (int b = 0; b < n_channels; ++b) {
-            auto it = g_tuned.find(class_key(d, d->desc[b]));
-            d->choice[b] = (it != g_tuned.end() && (d->cfg.engine & 3) == MCMC_ENGINE_AUTO)
-                               ? it->second
-                               : default_choice(d, d->desc[b]);
+            const ChannelDesc &c = d->desc[b];
+            if (c.N != lastN || c.L != lastL) {   // the key varies with (N, L) only within a call
+                auto it = g_tuned.find(class_key(d, c));
+                lastc = (it != g_tuned.end() && (d->cfg.engine & 3) == MCMC_ENGINE_AUTO) ? it->second
+                                                                                        : default_choice(d, c);
+                lastN = c.N;
+                lastL = c.L;
+            }
+            d->choice[b] = lastc;
         }
     }
     long long tot_tc = 0;
@@ -762,8 +816,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
         yd = P<float2>(d->d_in_y);
         sd = P<float>(d->d_in_s2);
     }
-    CK(cudaMemcpyAsync(d->d_desc.p, d->desc.data(), sizeof(ChannelDesc) * n_channels,
-                       cudaMemcpyHostToDevice, d->stream), "copy desc");
+    CK(upload(d, d->d_desc.p, d->desc.data(), sizeof(ChannelDesc) * n_channels), "copy desc");
     CK(cudaMemsetAsync(d->d_misc.p, 0, 256, d->stream), "reset status");
     CK(cudaMemsetAsync(d->d_accepts.p, 0, 8 * (size_t)n_channels * Np, d->stream), "reset accepts");
     finalize_desc_kernel<<<(n_channels + 127) / 128, 128, 0, d->stream>>>(
