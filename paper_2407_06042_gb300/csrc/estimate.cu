@@ -3,9 +3,10 @@
 // One CTA per channel:
 //  * hard decision: the visited state with the largest f (smallest residual), ties to the lowest
 //    chain; its f is recomputed in FP64 and its levels are mapped to complex Gray labels;
-//  * soft output: IS-based LLR of Eq. (34) in the log-sum-exp form of Eqs. (35)-(36) with exact
-//    F(a) = log(1 + e^a), over the S = Np final states. For bit k on dimension n, x+ and x-
-//    differ from the sample in dimension n only (Sec. III-D), so
+//  * soft output: IS-based LLR of Eq. (34) in the log-sum-exp form of Eqs. (35)-(36) over the
+//    S = Np final states, with exact F(a) = log(1 + e^a) for the weights (F(gamma) taken as
+//    gamma + F(-gamma)) and a running maximum-and-scaled-sum for each log-sum-exp. For bit k on
+//    dimension n, x+ and x- differ from the sample in dimension n only (Sec. III-D), so
 //        f(x with level k') - f(x) = (1/sigma^2) (2 D (zt_n - (Gt xt)_n) - D^2 Gt_nn),
 //    D = 2 (k' - k), needs (Gt xt)_n of the sample only.
 #include "common.cuh"
@@ -21,12 +22,34 @@ template <> struct E<float> {
     {
         return a > 0.f ? a + log1pf(__expf(-a)) : log1pf(__expf(a));
     }
+    static __device__ __forceinline__ float ex(float a) { return __expf(a); }
+    static __device__ __forceinline__ float lg(float a) { return __logf(a); }
 };
 template <> struct E<double> {
     static __device__ __forceinline__ double softplus(double a)
     {
         return a > 0.0 ? a + log1p(exp(-a)) : log1p(exp(a));
     }
+    static __device__ __forceinline__ double ex(double a) { return exp(a); }
+    static __device__ __forceinline__ double lg(double a) { return log(a); }
+};
+
+// Running log-sum-exp of Eq. (36) as (m, s), value m + log s: one exponential per term, with the
+// sum rescaled whenever a term exceeds the running maximum.
+template <typename T>
+struct Lse {
+    T m = -INFINITY, s = T(0);
+    __device__ __forceinline__ void add(T a)
+    {
+        if (a == -INFINITY) return;
+        if (a <= m) {
+            s += E<T>::ex(a - m);
+        } else {
+            s = s * E<T>::ex(m - a) + T(1);   // exp(-inf) = 0 for the first term
+            m = a;
+        }
+    }
+    __device__ __forceinline__ T value() const { return s > T(0) ? m + E<T>::lg(s) : T(-INFINITY); }
 };
 
 // running log-sum-exp, Eq. (36)
@@ -81,14 +104,8 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
     if (threadIdx.x < 32) {
         const double *G64 = A.G64 + d.mat_off;
         const double *z64 = A.z64 + d.vec_off;
-        double quad = 0.0, lin = 0.0;
-        for (int n = threadIdx.x; n < N; n += 32) {
-            const double xn = odd_of(kb[n], L);
-            double s = 0.0;
-            for (int m = 0; m < N; ++m) s = fma(G64[(long long)n * N + m], (double)odd_of(kb[m], L), s);
-            quad = fma(xn, s, quad);
-            lin = fma(xn, z64[n], lin);
-        }
+        double quad, lin;
+        quad_lin_fp64(G64, z64, N, threadIdx.x, [&](int n) { return (double)odd_of(kb[n], L); }, quad, lin);
         for (int o = 16; o; o >>= 1) {
             quad += __shfl_xor_sync(0xffffffffu, quad, o);
             lin += __shfl_xor_sync(0xffffffffu, lin, o);
@@ -105,7 +122,7 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
     const int split = max(1, (int)blockDim.x / N);
     const int n = threadIdx.x % N, sp = threadIdx.x / N;
     const bool active = sp < split && (int)threadIdx.x < split * N;
-    T vp[3] = {-INFINITY, -INFINITY, -INFINITY}, vm[3] = {-INFINITY, -INFINITY, -INFINITY};
+    Lse<T> vp[3], vm[3];
     if (active) {
         const T gnn = G[(long long)n * gstride + n];
         const double fref = s_fref;
@@ -126,10 +143,9 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
                 const T dfp = inv_s2 * (T(2) * dp * r - dp * dp * gnn);
                 const T dfm = inv_s2 * (T(2) * dm * r - dm * dm * gnn);
                 const T gam = (dfp - dfm) / tau;
-                const T ap = w * (fs + dfp) - E<T>::softplus(-gam);
-                const T am = w * (fs + dfm) - E<T>::softplus(gam);
-                vp[p] = lse_push(vp[p], ap);
-                vm[p] = lse_push(vm[p], am);
+                const T fmg = E<T>::softplus(-gam);   // F(gam) = gam + F(-gam)
+                vp[p].add(w * (fs + dfp) - fmg);
+                vm[p].add(w * (fs + dfm) - (gam + fmg));
             }
         }
     }
@@ -139,8 +155,9 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
         if (active && sp == r) {
             for (int p = 0; p < B; ++p) {
                 T *slot = s_part + 2 * (p * kMaxN + n);
-                if (r == 0) { slot[0] = vp[p]; slot[1] = vm[p]; }
-                else { slot[0] = lse_push(slot[0], vp[p]); slot[1] = lse_push(slot[1], vm[p]); }
+                const T a = vp[p].value(), c = vm[p].value();
+                if (r == 0) { slot[0] = a; slot[1] = c; }
+                else { slot[0] = lse_push(slot[0], a); slot[1] = lse_push(slot[1], c); }
             }
         }
     }
