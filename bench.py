@@ -588,7 +588,9 @@ def main():
         det.run_chains(T)
         ev1.record(stream)
         det.estimate(o_idx, o_llr, o_bf, host_io=False)
-        return ev0, ev1
+        ev2 = torch.cuda.Event(enable_timing=True)
+        ev2.record(stream)
+        return ev0, ev1, ev2
 
     def timed(det, steps, warmup):
         for _ in range(warmup):
@@ -611,11 +613,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-        kms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+        kms = float(np.mean([a.elapsed_time(b) for a, b, _ in kev]))
+        ems = float(np.mean([b.elapsed_time(c) for _, b, c in kev]))
+        timed.readout_ms = ems
         return ms / steps, kms, det.kernel_launches() - l0, clk.summary()
 
     det = make(precision)
     ms_step, chain_ms, launches, clocks = timed(det, args.steps, args.warmup)
+    readout_ms = timed.readout_ms
     units_rank = B * Np * T
     value = whole_job_rate(units_rank, world, ms_step * 1e-3)
     det_per_s = B * world / (ms_step * 1e-3)
@@ -681,6 +686,7 @@ def main():
                                        "inputs larger than L2 (H = %d MB)" % (Hd.numel() * 4 // 2**20)),
                 "precision": precision, "graph": bool(args.graph), "engine": args.engine,
                 "detections_per_s": det_per_s, "chain_kernel_ms": chain_ms,
+                "readout_ms": readout_ms,
                 "ber": ber, "snr_points_at_ber_le_1e-3": ber_ok,
                 "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": cb}

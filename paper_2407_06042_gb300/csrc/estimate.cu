@@ -4,8 +4,9 @@
 //  * hard decision: the visited state with the largest f (smallest residual), ties to the lowest
 //    chain; its f is recomputed in FP64 and its levels are mapped to complex Gray labels;
 //  * soft output: IS-based LLR of Eq. (34) in the log-sum-exp form of Eqs. (35)-(36) over the
-//    S = Np final states, with exact F(a) = log(1 + e^a) for the weights (F(gamma) taken as
-//    gamma + F(-gamma)) and a running maximum-and-scaled-sum for each log-sum-exp. For bit k on
+//    S = Np final states, with F(a) = log(1 + e^a) for the weights (F(gamma) taken as
+//    gamma + F(-gamma); exact in FP64, within 6e-8 in FP32) and a running maximum-and-scaled-sum
+//    for each log-sum-exp. For bit k on
 //    dimension n, x+ and x- differ from the sample in dimension n only (Sec. III-D), so
 //        f(x with level k') - f(x) = (1/sigma^2) (2 D (zt_n - (Gt xt)_n) - D^2 Gt_nn),
 //    D = 2 (k' - k), needs (Gt xt)_n of the sample only.
@@ -18,9 +19,11 @@ namespace {
 
 template <typename T> struct E;
 template <> struct E<float> {
+    // F(a) = max(a, 0) + log(1 + e^-|a|); the log of 1 + e^-|a| drops terms below 2^-24
+    // (an absolute error under 6e-8, far inside the FP32 read-out's tolerance)
     static __device__ __forceinline__ float softplus(float a)
     {
-        return a > 0.f ? a + log1pf(__expf(-a)) : log1pf(__expf(a));
+        return fmaxf(a, 0.f) + __logf(1.f + __expf(-fabsf(a)));
     }
     static __device__ __forceinline__ float ex(float a) { return __expf(a); }
     static __device__ __forceinline__ float lg(float a) { return __logf(a); }
@@ -34,20 +37,18 @@ template <> struct E<double> {
     static __device__ __forceinline__ double lg(double a) { return log(a); }
 };
 
-// Running log-sum-exp of Eq. (36) as (m, s), value m + log s: one exponential per term, with the
-// sum rescaled whenever a term exceeds the running maximum.
+// Running log-sum-exp of Eq. (36) as (m, s), value m + log s, without branches: the running
+// maximum moves to max(m, a) and both the sum and the new term are scaled to it (one of the two
+// exponentials is exp(0) = 1; exp(-inf) = 0 for the first term).
 template <typename T>
 struct Lse {
     T m = -INFINITY, s = T(0);
     __device__ __forceinline__ void add(T a)
     {
         if (a == -INFINITY) return;
-        if (a <= m) {
-            s += E<T>::ex(a - m);
-        } else {
-            s = s * E<T>::ex(m - a) + T(1);   // exp(-inf) = 0 for the first term
-            m = a;
-        }
+        const T mn = m > a ? m : a;
+        s = s * E<T>::ex(m - mn) + E<T>::ex(a - mn);
+        m = mn;
     }
     __device__ __forceinline__ T value() const { return s > T(0) ? m + E<T>::lg(s) : T(-INFINITY); }
 };
@@ -63,6 +64,7 @@ __device__ __forceinline__ T lse_push(T v, T a)
     return m + E<T>::softplus(dlt);
 }
 
+// launched with 256 threads (8 warps)
 template <typename T>
 __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
 {
@@ -77,9 +79,11 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
     const T inv_s2 = (T)d.inv_s2;
     const T tau = (T)d.tau;
     const T w = (tau - T(1)) / tau;
+    const T inv_tau = T(1) / tau;
     __shared__ int s_best;
     __shared__ double s_fref;
     __shared__ T s_part[2 * 3 * kMaxN];      // partial LSEs (split 0 stored, others merged)
+    __shared__ T s_fs[1024];                 // f(x_s) - f_ref of every sample (FP64 difference)
 
     // hard decision and the reference energy of the soft output
     if (threadIdx.x < 32) {
@@ -100,17 +104,43 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
         if (threadIdx.x == 0) { s_best = bi; s_fref = fm; }
     }
     __syncthreads();
+    for (int c = threadIdx.x; c < Np; c += blockDim.x) s_fs[c] = (T)(f[c] - s_fref);
     const int8_t *kb = A.best_states + d.state_off + (long long)s_best * N;
-    if (threadIdx.x < 32) {
+    // FP64 energy of the best sample, x^T Gt x row by row: a warp takes every 8th row and its
+    // lanes the columns (coalesced rows), all rows in flight at once
+    __shared__ double s_x[kMaxN];
+    __shared__ double s_ql[2 * 8];
+    for (int n = threadIdx.x; n < N; n += blockDim.x) s_x[n] = (double)odd_of(kb[n], L);
+    __syncthreads();
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const double *G64 = A.G64 + d.mat_off;
         const double *z64 = A.z64 + d.vec_off;
-        double quad, lin;
-        quad_lin_fp64(G64, z64, N, threadIdx.x, [&](int n) { return (double)odd_of(kb[n], L); }, quad, lin);
+        double quad = 0.0, lin = 0.0;
+        for (int n = warp; n < N; n += 8) {
+            const double *g = G64 + (long long)n * N;
+            double sr = 0.0;
+            for (int m = lane; m < N; m += 32) sr = fma(g[m], s_x[m], sr);
+            quad = fma(s_x[n], sr, quad);
+        }
+        for (int n = threadIdx.x; n < N; n += blockDim.x) lin = fma(s_x[n], z64[n], lin);
         for (int o = 16; o; o >>= 1) {
             quad += __shfl_xor_sync(0xffffffffu, quad, o);
             lin += __shfl_xor_sync(0xffffffffu, lin, o);
         }
-        if (threadIdx.x == 0 && A.best_f_out) A.best_f_out[b] = -(A.yy[b] - 2.0 * lin + quad) * d.inv_s2;
+        if (lane == 0) {
+            s_ql[2 * warp] = quad;
+            s_ql[2 * warp + 1] = lin;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && A.best_f_out) {
+        double quad = 0.0, lin = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) {
+            quad += s_ql[2 * w8];
+            lin += s_ql[2 * w8 + 1];
+        }
+        A.best_f_out[b] = -(A.yy[b] - 2.0 * lin + quad) * d.inv_s2;
     }
     if (A.best_idx) {
         for (int i = threadIdx.x; i < nt; i += blockDim.x)
@@ -125,7 +155,6 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
     Lse<T> vp[3], vm[3];
     if (active) {
         const T gnn = G[(long long)n * gstride + n];
-        const double fref = s_fref;
         for (int s = sp; s < Np; s += split) {
             const int8_t *ks = S + (long long)s * N;
             T Dn = T(0);
@@ -134,7 +163,7 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
                 for (int m = 0; m < N; ++m) Dn = fma(G[(long long)n * gstride + m], (T)odd_of(ks[m], L), Dn);
             const int k = ks[n];
             const T r = z[n] - Dn;
-            const T fs = (T)(f[s] - fref);
+            const T fs = s_fs[s];
             const int g = gray_of(k);
             for (int p = 0; p < B; ++p) {
                 const int mask = 1 << (B - 1 - p);
@@ -142,7 +171,7 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
                 const T dp = T(2 * (kpl - k)), dm = T(2 * (kmi - k));
                 const T dfp = inv_s2 * (T(2) * dp * r - dp * dp * gnn);
                 const T dfm = inv_s2 * (T(2) * dm * r - dm * dm * gnn);
-                const T gam = (dfp - dfm) / tau;
+                const T gam = (dfp - dfm) * inv_tau;
                 const T fmg = E<T>::softplus(-gam);   // F(gam) = gam + F(-gam)
                 vp[p].add(w * (fs + dfp) - fmg);
                 vm[p].add(w * (fs + dfm) - (gam + fmg));
