@@ -846,6 +846,7 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     pa.stage_h = h_stage <= std::min<size_t>(d->smem_optin, 128 * 1024);
     pa.stage_gj = stage_gj;
     pa.precond_fp32 = fp64 ? 0 : 1;
+    pa.max_nt = maxnt;
     CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : 2 * maxnt * gj_elem, pre, d->stream),
        "prep kernels");
     d->launches += pre ? 3 : 2;

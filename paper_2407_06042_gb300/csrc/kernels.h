@@ -26,7 +26,8 @@ struct PrepArgs {
     unsigned *status;
     int stage_h;            // stage H and y in shared memory
     int stage_gj;           // factorise the preconditioner in shared memory
-    int precond_fp32;       // FP32 Cholesky (FP32 / MIXED modes) instead of FP64
+    int precond_fp32;       // FP32 Gauss-Jordan (FP32 / MIXED modes) instead of FP64
+    int max_nt;             // largest Nt of the batch (0: unknown)
 };
 
 struct InitArgs {

@@ -131,6 +131,79 @@ template <> struct CT<double> { using type = cd; };
 //     A_kk <- 1/p,  A_kj <- A_kj / p,  A_ik <- -A_ik / p,  A_ij <- A_ij - A_ik A_kj / p.
 // The matrix lives in shared memory when it fits, else in the channel's global scratch block.
 // ------------------------------------------------------------------------------------------
+// Register-tiled form for nt <= 16 T (FP32, 256 threads): thread (ti, tj) of a 16 x 16 grid
+// holds rows [T ti, T ti + T) x columns [T tj, T tj + T) of A in registers. At step k the owners
+// of row k and column k publish their old values (double-buffered, so one barrier per step
+// suffices: a buffer is rewritten two steps later, after every reader has passed the barrier
+// between), then every thread updates its tile with the same four rules.
+template <int T>
+__device__ __forceinline__ void precond_regs(const PrepArgs &a, const ChannelDesc &d, int nt,
+                                             double gamma)
+{
+    using C2 = CT<float>::type;
+    __shared__ C2 srow[2][64], scol[2][64];
+    const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+    const int i0 = T * ti, j0 = T * tj;
+    const cd *G = reinterpret_cast<const cd *>(a.Gc) + d.mat_off / 4;
+    C2 A[T][T];
+#pragma unroll
+    for (int r = 0; r < T; ++r)
+#pragma unroll
+        for (int c = 0; c < T; ++c) {
+            const int i = i0 + r, j = j0 + c;
+            A[r][c] = {0.f, 0.f};
+            if (i < nt && j < nt) {
+                const cd g = G[i * nt + j];
+                A[r][c] = {(float)(g.x + (i == j ? gamma : 0.0)), (float)g.y};
+            }
+        }
+    for (int k = 0; k < nt; ++k) {
+        const int buf = k & 1;
+#pragma unroll
+        for (int r = 0; r < T; ++r)
+            if (i0 + r == k)
+#pragma unroll
+                for (int c = 0; c < T; ++c) srow[buf][j0 + c] = A[r][c];
+#pragma unroll
+        for (int c = 0; c < T; ++c)
+            if (j0 + c == k)
+#pragma unroll
+                for (int r = 0; r < T; ++r) scol[buf][i0 + r] = A[r][c];
+        __syncthreads();
+        const C2 piv = srow[buf][k];
+        if (threadIdx.x == 0 && !(piv.x > 0.f)) set_status(a.status, kStatusNumeric);
+        const float den = piv.x * piv.x + piv.y * piv.y;
+        const C2 pinv = {piv.x / den, -piv.y / den};
+        C2 rk[T], ck[T];
+#pragma unroll
+        for (int c = 0; c < T; ++c) {
+            const C2 r = srow[buf][j0 + c];
+            rk[c] = {r.x * pinv.x - r.y * pinv.y, r.x * pinv.y + r.y * pinv.x};
+        }
+#pragma unroll
+        for (int r = 0; r < T; ++r) ck[r] = scol[buf][i0 + r];
+#pragma unroll
+        for (int r = 0; r < T; ++r)
+#pragma unroll
+            for (int c = 0; c < T; ++c) {
+                const bool ik = i0 + r == k, jk = j0 + c == k;
+                const C2 cc = ck[r], rr = rk[c], o = A[r][c];
+                C2 v = {o.x - (cc.x * rr.x - cc.y * rr.y), o.y - (cc.x * rr.y + cc.y * rr.x)};
+                if (jk) v = {-(cc.x * pinv.x - cc.y * pinv.y), -(cc.x * pinv.y + cc.y * pinv.x)};
+                if (ik) v = jk ? pinv : rr;
+                A[r][c] = v;
+            }
+    }
+    cd *M = reinterpret_cast<cd *>(a.Mc) + d.mat_off / 4;
+#pragma unroll
+    for (int r = 0; r < T; ++r)
+#pragma unroll
+        for (int c = 0; c < T; ++c) {
+            const int i = i0 + r, j = j0 + c;
+            if (i < nt && j < nt) M[i * nt + j] = {(double)A[r][c].x, (double)A[r][c].y};
+        }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
 {
@@ -138,6 +211,10 @@ __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
     const ChannelDesc d = a.desc[b];
     const int nt = d.Nt;
     const double gamma = d.gamma_t / (d.dmin * d.dmin);   // gamma in the unscaled model
+    if constexpr (sizeof(R) == 4) {
+        if (nt <= 32) { precond_regs<2>(a, d, nt, gamma); return; }
+        if (nt <= 64) { precond_regs<4>(a, d, nt, gamma); return; }
+    }
     using C2 = typename CT<R>::type;
     extern __shared__ double shd[];
     C2 *rowk = reinterpret_cast<C2 *>(shd);               // A_kj / p
@@ -343,6 +420,8 @@ cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (preconditioned) {
         auto k = a.precond_fp32 ? precond_kernel<float> : precond_kernel<double>;
+        // the FP32 kernel keeps matrices of up to 64 x 64 in registers (no dynamic shared memory)
+        if (a.precond_fp32 && a.max_nt > 0 && a.max_nt <= 64) gj_stage_bytes = 0;
         if (gj_stage_bytes > 48 * 1024) {
             e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)gj_stage_bytes);
