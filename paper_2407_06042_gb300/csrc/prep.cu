@@ -137,9 +137,11 @@ template <> struct CT<double> { using type = cd; };
 // suffices: a buffer is rewritten two steps later, after every reader has passed the barrier
 // between), then every thread updates its tile with the same four rules.
 template <int T>
-__device__ __forceinline__ void precond_regs(const PrepArgs &a, const ChannelDesc &d, int nt,
-                                             double gamma)
+__global__ void __launch_bounds__(256, T == 4 ? 3 : 6) precond_regs_kernel(PrepArgs a)
 {
+    const ChannelDesc d = a.desc[blockIdx.x];
+    const int nt = d.Nt;
+    const double gamma = d.gamma_t / (d.dmin * d.dmin);   // gamma in the unscaled model
     using C2 = CT<float>::type;
     __shared__ C2 srow[2][64], scol[2][64];
     const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
@@ -211,10 +213,6 @@ __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
     const ChannelDesc d = a.desc[b];
     const int nt = d.Nt;
     const double gamma = d.gamma_t / (d.dmin * d.dmin);   // gamma in the unscaled model
-    if constexpr (sizeof(R) == 4) {
-        if (nt <= 32) { precond_regs<2>(a, d, nt, gamma); return; }
-        if (nt <= 64) { precond_regs<4>(a, d, nt, gamma); return; }
-    }
     using C2 = typename CT<R>::type;
     extern __shared__ double shd[];
     C2 *rowk = reinterpret_cast<C2 *>(shd);               // A_kj / p
@@ -420,8 +418,11 @@ cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (preconditioned) {
         auto k = a.precond_fp32 ? precond_kernel<float> : precond_kernel<double>;
-        // the FP32 kernel keeps matrices of up to 64 x 64 in registers (no dynamic shared memory)
-        if (a.precond_fp32 && a.max_nt > 0 && a.max_nt <= 64) gj_stage_bytes = 0;
+        // FP32 batches of Nt <= 64: the matrix in registers (no dynamic shared memory)
+        if (a.precond_fp32 && a.max_nt > 0 && a.max_nt <= 64) {
+            k = a.max_nt <= 32 ? precond_regs_kernel<2> : precond_regs_kernel<4>;
+            gj_stage_bytes = 0;
+        }
         if (gj_stage_bytes > 48 * 1024) {
             e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)gj_stage_bytes);
