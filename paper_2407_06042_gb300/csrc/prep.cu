@@ -39,7 +39,7 @@ struct FF {
 // K1: complex Gram matrix, matched filter, ||y||^2 (FP64 accumulation of FP32 inputs: every
 // product of two FP32 values is exact in FP64).
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) gram_kernel(PrepArgs a)
+__global__ void __launch_bounds__(512) gram_kernel(PrepArgs a)
 {
     const int b = blockIdx.x;
     const ChannelDesc d = a.desc[b];
@@ -404,6 +404,23 @@ __global__ void refresh_kernel(RefreshArgs a)
 // ------------------------------------------------------------------------------------------
 // Host launchers
 // ------------------------------------------------------------------------------------------
+// Threads of the Gram kernel: its work items are the nb (nb + 1) / 2 upper-triangle 2 x 2 blocks
+// (nb = ceil(Nt / 2)) of equal cost; pick the warp multiple in [128, 512] that wastes the fewest
+// thread-slots over the rounds (ties to more threads). 256 when the batch's Nt is unknown.
+int gram_threads(int max_nt)
+{
+    if (max_nt <= 0) return 256;
+    const int nb = (max_nt + 1) / 2, nblk = nb * (nb + 1) / 2;
+    int best = 256;
+    double best_eff = -1.0;
+    for (int t = 128; t <= 512; t += 32) {
+        const int rounds = (nblk + t - 1) / t;
+        const double eff = (double)nblk / ((double)rounds * t);
+        if (eff >= best_eff) { best_eff = eff; best = t; }
+    }
+    return best;
+}
+
 cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
                         size_t gj_stage_bytes, bool preconditioned, cudaStream_t s)
 {
@@ -414,7 +431,7 @@ cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
                                  (int)h_stage_bytes);
         if (e != cudaSuccess) return e;
     }
-    gram_kernel<<<n_channels, 256, a.stage_h ? h_stage_bytes : 0, s>>>(a);
+    gram_kernel<<<n_channels, gram_threads(a.max_nt), a.stage_h ? h_stage_bytes : 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (preconditioned) {
         auto k = a.precond_fp32 ? precond_kernel<float> : precond_kernel<double>;
