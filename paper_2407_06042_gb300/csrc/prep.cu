@@ -265,78 +265,85 @@ __global__ void __launch_bounds__(256) precond_kernel(PrepArgs a)
 //   zt = d [Re z; Im z],  wt = P~ zt = [Re(M z); Im(M z)] / d
 //   Bt (N x NOp, the CUDA-core GEMM operand): row m = [Gt row m | GMt row m | 0 pad]
 // ------------------------------------------------------------------------------------------
-// Entry (r, c) of real([(G + gamma I)^{-1} G]) = real(I - gamma M) (the stacked embedding).
-__device__ __forceinline__ double gm_entry(const cd *M, int nt, double gamma, int r, int c)
-{
-    const cd m = M[(r % nt) * nt + (c % nt)];
-    const int q = (r >= nt) * 2 + (c >= nt);
-    const double v = (q == 0 || q == 3) ? m.x : (q == 1 ? -m.y : m.y);
-    return -gamma * v + (r == c ? 1.0 : 0.0);
-}
-
-template <typename T>
-__device__ void emit_bt(const PrepArgs &a, const ChannelDesc &d, T *bt)
-{
-    const int N = d.N, nt = d.Nt;
-    const cd *M = reinterpret_cast<const cd *>(a.Mc) + d.mat_off / 4;
-    const double gamma = d.gamma_t / (d.dmin * d.dmin);
-    for (int e = threadIdx.x; e < N * d.NOp; e += blockDim.x) {
-        const int m = e / d.NOp, o = e % d.NOp;
-        double v = 0.0;
-        if (o < N) v = a.G64[d.mat_off + (long long)m * N + o];
-        else if (o < d.NO) v = gm_entry(M, nt, gamma, m, o - N);
-        bt[e] = (T)v;
-    }
-}
-
 __global__ void __launch_bounds__(256) emit_kernel(PrepArgs a)
 {
     const int b = blockIdx.x;
     const ChannelDesc d = a.desc[b];
-    const int nt = d.Nt, N = d.N;
+    const int nt = d.Nt, N = d.N, NO = d.NO, NOp = d.NOp;
     const double d2 = d.dmin * d.dmin;
-    const cd *G = reinterpret_cast<const cd *>(a.Gc) + d.mat_off / 4;
-    const cd *z = reinterpret_cast<const cd *>(a.zc) + d.vec_off / 2;
-    double *G64 = a.G64 + d.mat_off;
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int r = e / N, c = e % N;
-        const cd g = G[(r % nt) * nt + (c % nt)];
-        const int q = (r >= nt) * 2 + (c >= nt);
-        const double v = (q == 0 || q == 3) ? g.x : (q == 1 ? -g.y : g.y);
-        G64[e] = d2 * v;
-    }
-    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-        a.z64[d.vec_off + i] = d.dmin * z[i].x;
-        a.z64[d.vec_off + nt + i] = d.dmin * z[i].y;
-    }
-    const bool pre = d.NO > N;
-    if (pre) {
-        const cd *M = reinterpret_cast<const cd *>(a.Mc) + d.mat_off / 4;
-        const double gamma = d.gamma_t / d2;
-        if (a.GM64) {
-            double *GM = a.GM64 + d.mat_off;
-            for (int e = threadIdx.x; e < N * N; e += blockDim.x)
-                GM[e] = gm_entry(M, nt, gamma, e / N, e % N);
+    const bool pre = NO > N;
+    const double gamma = d.gamma_t / d2;
+    const cd *__restrict__ G = reinterpret_cast<const cd *>(a.Gc) + d.mat_off / 4;
+    const cd *__restrict__ M = reinterpret_cast<const cd *>(a.Mc) + d.mat_off / 4;
+    const cd *__restrict__ z = reinterpret_cast<const cd *>(a.zc) + d.vec_off / 2;
+    double *__restrict__ G64 = a.G64 + d.mat_off;
+    double *__restrict__ GM = (pre && a.GM64) ? a.GM64 + d.mat_off : nullptr;
+    double *__restrict__ bt64 = a.bt64 ? a.bt64 + d.bt_off : nullptr;
+    float *__restrict__ bt32 = a.bt32 ? a.bt32 + d.bt_off : nullptr;
+    // Every element (r, c) of the N x NOp operand [Gt | GMt | 0], one pass: consecutive threads
+    // take consecutive elements, and (r, c) advance by (blockDim / NOp, blockDim % NOp) without
+    // divisions. In the stacked embedding, entry (r, c) of Gt (or of GMt) takes the complex entry
+    // (r mod nt, c mod nt) of G (or M): Re on the diagonal blocks, -Im above, +Im below.
+    const int dr = blockDim.x / NOp, dc = blockDim.x % NOp;
+    int r = threadIdx.x / NOp, c = threadIdx.x % NOp;
+    for (int e = threadIdx.x; e < N * NOp; e += blockDim.x) {
+        double v = 0.0;
+        if (c < NO) {
+            const bool gpart = c < N;
+            const int cc = gpart ? c : c - N;
+            const int ri = r < nt ? r : r - nt, ci = cc < nt ? cc : cc - nt;
+            const bool rlo = r >= nt, clo = cc >= nt;
+            const cd g = (gpart ? G : M)[ri * nt + ci];
+            const double q = rlo == clo ? g.x : (clo ? -g.y : g.y);
+            if (gpart) {
+                v = d2 * q;
+                G64[r * N + c] = v;
+            } else {
+                v = -gamma * q + (r == cc ? 1.0 : 0.0);   // real(I - gamma M)
+                if (GM) GM[r * N + cc] = v;
+            }
         }
-        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-            double re = 0.0, im = 0.0;
+        if (bt64) bt64[e] = v;
+        else if (bt32) bt32[e] = (float)v;
+        c += dc;
+        r += dr;
+        if (c >= NOp) {
+            c -= NOp;
+            ++r;
+        }
+    }
+    // zt = d [Re z; Im z] and wt = [Re(M z); Im(M z)] / d (zero without the preconditioner); wt
+    // in FP32 when M came from the FP32 factorisation (FP64 would add no accuracy there)
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        const double zr = d.dmin * z[i].x, zi = d.dmin * z[i].y;
+        double re = 0.0, im = 0.0;
+        if (pre && a.precond_fp32) {
+            float fr = 0.f, fi = 0.f;
+            for (int j = 0; j < nt; ++j) {
+                const cd m = M[i * nt + j], v = z[j];
+                const float mr = (float)m.x, mi = (float)m.y, vr = (float)v.x, vi = (float)v.y;
+                fr = fmaf(mr, vr, fmaf(-mi, vi, fr));
+                fi = fmaf(mr, vi, fmaf(mi, vr, fi));
+            }
+            re = fr;
+            im = fi;
+        } else if (pre) {
             for (int j = 0; j < nt; ++j) {
                 const cd p = cmul(M[i * nt + j], z[j]);
-                re += p.x; im += p.y;
+                re += p.x;
+                im += p.y;
             }
-            a.w64[d.vec_off + i] = re / d.dmin;
-            a.w64[d.vec_off + nt + i] = im / d.dmin;
         }
-    } else {
-        for (int i = threadIdx.x; i < N; i += blockDim.x) a.w64[d.vec_off + i] = 0.0;
+        const double wr = re / d.dmin, wi = im / d.dmin;
+        a.z64[d.vec_off + i] = zr;
+        a.z64[d.vec_off + nt + i] = zi;
+        a.z32[d.vec_off + i] = (float)zr;
+        a.z32[d.vec_off + nt + i] = (float)zi;
+        a.w64[d.vec_off + i] = wr;
+        a.w64[d.vec_off + nt + i] = wi;
+        a.w32[d.vec_off + i] = (float)wr;
+        a.w32[d.vec_off + nt + i] = (float)wi;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        a.z32[d.vec_off + i] = (float)a.z64[d.vec_off + i];
-        a.w32[d.vec_off + i] = (float)a.w64[d.vec_off + i];
-    }
-    if (a.bt64) emit_bt<double>(a, d, a.bt64 + d.bt_off);
-    if (a.bt32) emit_bt<float>(a, d, a.bt32 + d.bt_off);
 }
 
 // ------------------------------------------------------------------------------------------
