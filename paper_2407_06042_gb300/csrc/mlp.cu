@@ -5,13 +5,15 @@
 // cross-entropy, Adam. Every reduction has a fixed order (split-K partials summed by a second
 // kernel, column sums by fixed row groups), so training is deterministic.
 //
-// Tensor-core inference (one CTA of 128 threads per SM, persistent over 128-row tiles):
-//   1. each thread computes its row's first layer on the CUDA cores (K = 6) and stores the BF16
-//      activations into the A operand (K-major core matrices, 128 x 256);
+// Tensor-core inference (one CTA of 256 threads per SM, persistent over 128-row tiles; two
+// threads per row, each taking half of the hidden units and logits):
+//   1. each thread computes its half of its row's first layer on the CUDA cores (K = 6) and
+//      stores the BF16 activations into the A operand (K-major core matrices, 128 x 256);
 //   2. one thread issues 16 MMAs (M = 128, N = 256, K = 16) against W2 (BF16, staged once per
 //      CTA by a bulk copy) into tensor memory columns 0..255;
-//   3. each warp reads its 32 lanes back (tcgen05.ld), adds b2, applies ReLU, rounds to BF16 and
-//      overwrites the A operand with the second hidden layer;
+//   3. each warp reads its 32 lanes back (tcgen05.ld; warps w and w + 4 share lane quadrant
+//      w % 4 and split the columns), adds b2, applies ReLU, rounds to BF16 and overwrites the A
+//      operand with the second hidden layer;
 //   4. 16 MMAs against W3 (N = Qc padded to 16) into columns 256.., then bias and store.
 // Every mbarrier wait is bounded; one that runs out sets the timeout status bit and the CTA
 // frees its tensor memory and returns.
