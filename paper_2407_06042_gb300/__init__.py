@@ -21,7 +21,7 @@ __all__ = [
     "Detector", "Config", "Stats", "lib", "load", "MCMC_PREC_FP64", "MCMC_PREC_FP32",
     "MCMC_PREC_MIXED", "MCMC_ENGINE_AUTO", "MCMC_ENGINE_SIMT", "MCMC_ENGINE_TC",
     "MCMC_ENGINE_GRAPH", "McmcError", "Mlp",
-    "ABI_FUNCTIONS", "ABI_FUNCTIONS_LEARNED",
+    "ABI_FUNCTIONS", "ABI_FUNCTIONS_LEARNED", "ABI_FUNCTIONS_DIAG", "transition_diagnostics",
 ]
 
 MCMC_PREC_FP64, MCMC_PREC_FP32, MCMC_PREC_MIXED = 0, 1, 2
@@ -46,6 +46,10 @@ ABI_FUNCTIONS_LEARNED = [
     "mcmc_mlp_train_step", "mcmc_detect_features", "mcmc_detect_set_model",
     "mcmc_detect_init_learned", "mcmc_detect_mix_step",
 ]
+
+
+# Every entry point of include/mcmcdet_diag.h.
+ABI_FUNCTIONS_DIAG = ["mcmc_diag_transition"]
 
 
 class McmcError(RuntimeError):
@@ -130,6 +134,9 @@ def load(path: Optional[str] = None):
     for n in ABI_FUNCTIONS_LEARNED:
         if n not in ("mcmc_mlp_param_count", "mcmc_mlp_last_error"):
             getattr(l, n).restype = ctypes.c_int
+    l.mcmc_diag_transition.argtypes = [i32, i32, i32, i32, vp, vp, vp, i32, ctypes.c_float,
+                                       ctypes.c_float, vp, vp, vp, i32, vp, vp]
+    l.mcmc_diag_transition.restype = ctypes.c_int
     if path is None:
         _lib = l
     return l
@@ -404,3 +411,37 @@ class Mlp:
             self.destroy()
         except Exception:
             pass
+
+
+def transition_diagnostics(H, y, noise_var, nt: int, nr: int, qam: int, *, preconditioned=True,
+                           alpha_scale: float = 1.0, tau: float = 2.0, tv_steps: int = 0,
+                           eigenvalues: bool = False, stream=None):
+    """Exact transition kernels of a batch of small channels of one shape, on the GPU (see
+    include/mcmcdet_diag.h). H, y: device float32 tensors with the complex entries interleaved
+    (channel b at H[b * nr * nt * 2:], column-major nr x nt; y[b * nr * 2:]); noise_var: device
+    float32 [n_channels]. Returns device float64 tensors: P [B, S, S], pi [B, S], and, when
+    asked for, eig [B, S] (descending) and tv [B, tv_steps + 1]."""
+    import torch
+    n = int(noise_var.numel())
+    L = {4: 2, 16: 4, 64: 8}.get(int(qam), 0)
+    S = L ** (2 * int(nt)) if L else 0
+    if not S or S > 256 or n < 1:
+        raise McmcError(1, "shape outside the diagnostics' range")
+    dev = noise_var.device
+    P = torch.empty((n, S, S), dtype=torch.float64, device=dev)
+    pi = torch.empty((n, S), dtype=torch.float64, device=dev)
+    eig = torch.empty((n, S), dtype=torch.float64, device=dev) if eigenvalues else None
+    tv = torch.empty((n, tv_steps + 1), dtype=torch.float64, device=dev) if tv_steps > 0 else None
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    rc = load().mcmc_diag_transition(n, int(nt), int(nr), int(qam), _ptr(H), _ptr(y),
+                                     _ptr(noise_var), int(bool(preconditioned)),
+                                     float(alpha_scale), float(tau), _ptr(P), _ptr(pi), _ptr(eig),
+                                     int(tv_steps), _ptr(tv), ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise McmcError(rc, "mcmc_diag_transition")
+    out = {"P": P, "pi": pi}
+    if eig is not None:
+        out["eig"] = eig
+    if tv is not None:
+        out["tv"] = tv
+    return out

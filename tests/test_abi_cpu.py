@@ -1,6 +1,6 @@
 """CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports every entry point
-that include/mcmcdet.h and include/mcmcdet_learned.h declare. Only host-only entry points are
-called (no GPU here)."""
+that include/mcmcdet.h, include/mcmcdet_learned.h and include/mcmcdet_diag.h declare. Only
+host-only entry points and host-side argument checks are called (no GPU here)."""
 import ctypes
 import os
 import re
@@ -17,7 +17,8 @@ def _header_functions(name="mcmcdet.h"):
 
 
 @pytest.mark.parametrize("header,attr", [("mcmcdet.h", "ABI_FUNCTIONS"),
-                                         ("mcmcdet_learned.h", "ABI_FUNCTIONS_LEARNED")])
+                                         ("mcmcdet_learned.h", "ABI_FUNCTIONS_LEARNED"),
+                                         ("mcmcdet_diag.h", "ABI_FUNCTIONS_DIAG")])
 def test_library_builds_and_exports_every_declared_symbol(header, attr):
     import paper_2407_06042_gb300 as pkg
     lib = pkg.load()
@@ -67,3 +68,27 @@ def test_config_struct_matches_header():
     # int32 x 10 + uint64 + pointer
     assert ctypes.sizeof(pkg.Config) == 10 * 4 + 8 + 8
     assert ctypes.sizeof(pkg.Stats) == 8 + 8 + 4 + 4 + 8
+
+
+def test_diag_argument_checks_on_the_host():
+    """Arguments outside the diagnostics' range are rejected before any device call."""
+    import paper_2407_06042_gb300 as pkg
+    lib = pkg.load()
+    d = ctypes.c_void_p(16)          # never dereferenced: every call below fails its checks
+    call = lib.mcmc_diag_transition
+    bad = [
+        (0, 2, 2, 4, d, d, d, 1, 1.0, 2.0, d, None, None, 0, None, None),    # no channels
+        (1, 3, 3, 16, d, d, d, 1, 1.0, 2.0, d, None, None, 0, None, None),   # S = 4^6 > 256
+        (1, 5, 5, 4, d, d, d, 1, 1.0, 2.0, d, None, None, 0, None, None),    # N = 10 > 8
+        (1, 2, 2, 16, d, d, d, 1, 1.0, 2.0, d, None, d, 0, None, None),      # spectrum of S = 256
+        (1, 1, 33, 4, d, d, d, 1, 1.0, 2.0, d, None, None, 0, None, None),   # nr > 32
+        (1, 1, 1, 8, d, d, d, 1, 1.0, 2.0, d, None, None, 0, None, None),    # qam
+        (1, 1, 1, 4, d, d, d, 2, 1.0, 2.0, d, None, None, 0, None, None),    # flag
+        (1, 1, 1, 4, d, d, d, 1, 0.0, 2.0, d, None, None, 0, None, None),    # alpha_scale
+        (1, 1, 1, 4, d, d, d, 1, 1.0, 0.5, d, None, None, 0, None, None),    # tau < 1
+        (1, 1, 1, 4, d, d, d, 1, 1.0, 2.0, None, None, None, 0, None, None),  # no P
+        (1, 1, 1, 4, None, d, d, 1, 1.0, 2.0, d, None, None, 0, None, None),  # no H
+        (1, 1, 1, 4, d, d, d, 1, 1.0, 2.0, d, None, None, -1, d, None),      # tv_steps
+    ]
+    for args in bad:
+        assert call(*args) == 1, args
