@@ -232,7 +232,7 @@ def chain_roofline(precision, w, units, chain_ms, batch=None):
 def load_batch(scale: float, rank: int, name: str = WORKLOAD):
     w = dict(workload.WORKLOADS[name])
     w["seed"] = rank_seed(w["seed"], rank)
-    if w["kind"] == "rayleigh":
+    if w["kind"] in ("rayleigh", "convergence"):
         n = max(1, int(round(w["per_snr"] * scale)))
         b = workload.rayleigh_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["seed"])
     elif w["kind"] == "kronecker":
@@ -501,6 +501,114 @@ def run_learned(args, w, batch, rank, world, dist, dev, pkg, torch):
     return 0
 
 
+def run_convergence(args, w, batch, rank, world, dist, dev, pkg, torch):
+    """Convergence diagnostics (Sec. III-B, Figs. 2-3): for every channel the exact transition
+    kernel of the plain and of the preconditioned proposal, its spectrum (rate r = second
+    eigenvalue) and the total-variation curve from the uniform start. One step = both proposals
+    over the whole batch; value = transition kernels per second. The kernel is FP64 and latency
+    bound (one CTA per 16-state problem): its roofline is quoted against the measured DFMA rate
+    with the method's minimal FP64 work per kernel (S^2 (2N + 1) for P, (4/3) S^3 for the
+    eigenvalues, 2 T S^2 for T transitions of the TV curve)."""
+    import oracle
+    import oracle.diag as od
+    T = w["iterations"]
+    B = batch.n_channels
+    nt, nr, qam = w["nt"], w["nr"], w["qam"]
+    S = int(round(np.sqrt(qam))) ** (2 * nt)
+    Hh = torch.from_numpy(np.ascontiguousarray(batch.H).view(np.float32).copy()).pin_memory()
+    yh = torch.from_numpy(np.ascontiguousarray(batch.y).view(np.float32).copy()).pin_memory()
+    sh = torch.from_numpy(np.ascontiguousarray(batch.sigma2, np.float32)).pin_memory()
+    Hd, yd, sd = Hh.to(dev), yh.to(dev), sh.to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step(Hx, yx, sx):
+        return [pkg.transition_diagnostics(Hx, yx, sx, nt, nr, qam, preconditioned=pc, tv_steps=T,
+                                           eigenvalues=True) for pc in (False, True)]
+
+    for _ in range(args.warmup):
+        step(Hd, yd, sd)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    tot = 0.0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                 # L2 flushed between timed steps, outside the events
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs = step(Hd, yd, sd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(tot, dist, dev) / args.steps
+    value = whole_job_rate(2 * B, world, ms * 1e-3)
+    # end to end: pinned inputs up, spectra and TV curves down, every step
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o = step(Hh.to(dev, non_blocking=True), yh.to(dev, non_blocking=True),
+                 sh.to(dev, non_blocking=True))
+        host = [(x["eig"].cpu(), x["tv"].cpu()) for x in o]
+    torch.cuda.synchronize()
+    dt = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, dev)
+    e2e = {"value": whole_job_rate(2 * B, world, dt), "unit": "transition kernels/s",
+           "h2d_bytes_per_step": 2 * int(Hh.numel() * 4 + yh.numel() * 4 + sh.numel() * 4),
+           "d2h_bytes_per_step": int(sum(a.numel() * 8 + b.numel() * 8 for a, b in host))}
+    N = 2 * nt
+    per = S * S * (2 * N + 1) + (4.0 / 3.0) * S ** 3 + 2 * T * S * S
+    peaks = pipe_peaks() or {}
+    dfma = peaks.get("dfma")
+    ach = per * 2 * B / (ms * 1e-3)
+    roof = {"bound": "alu", "achieved": ach / 1e9, "peak": 2 * dfma / 1e9 if dfma else None,
+            "unit": "GFLOP/s", "frac": ach / (2 * dfma) if dfma else None, "traffic": None,
+            "pipe": "FP64 (2 flops per DFMA at the measured DFMA rate); latency bound",
+            "per_unit": f"{per:g} FP64 flops per transition kernel (S={S}, N={N}, T={T})"}
+    # Fig. 3 boxplot data and median TV curves per SNR point
+    figs = {}
+    snr = batch.snr_db
+    for pc, o in zip(("plain", "preconditioned"), outs):
+        eig = o["eig"].cpu().numpy()
+        tv = o["tv"].cpu().numpy()
+        figs[pc] = {}
+        for s in sorted(set(snr.tolist())):
+            m = snr == s
+            r = eig[m, 1]
+            figs[pc][f"{s:g}"] = {
+                "rate_quartiles": [float(v) for v in np.percentile(r, [0, 25, 50, 75, 100])],
+                "tv_median": {str(t): float(np.median(tv[m, t])) for t in (0, 5, 10, 20, T)}}
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        idx = list(range(0, B, max(1, B // 40)))
+        t0 = time.perf_counter()
+        for ch in idx:
+            Hc, yc, s2 = batch.channel(ch)
+            for pc in (False, True):
+                t = oracle.Target.from_channel(Hc, yc, s2, qam, preconditioned=pc, tau=2.0)
+                P = t.transition_matrix()
+                pi = od.stationary(t.all_f() / 2.0)
+                od.spectrum(P, pi)
+                od.tv_curve(P, pi, T)
+        dtc = time.perf_counter() - t0
+        cb = {"value": 2 * len(idx) / dtc, "unit": "transition kernels/s", "cores": 1,
+              "kind": "oracle", "sample": f"{len(idx)} channels x 2 proposals: C transition matrix, "
+              "numpy spectrum and TV curve, one thread", "seconds": dtc}
+    if rank == 0:
+        line = {"metric": "transition kernels/s (exact P, spectrum, TV curve)", "value": value,
+                "unit": "transition kernels/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "nt": nt, "nr": nr, "qam": qam,
+                           "snr_db": w["snr_db"], "channels": B * world, "states": S,
+                           "tv_steps": T, "parallelism": f"replicas x{world}",
+                           "l2": "L2 flushed between timed steps (256 MB write outside the events)"},
+                "clocks": clk.summary(), "gpu_launches": 2 * args.steps,
+                "roofline": roof, "e2e": e2e, "cpu_baseline": cb, "fig3": figs}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,6 +648,8 @@ def main():
     batch, w = load_batch(args.scale, rank, args.workload)
     if w["kind"] == "learned":
         return run_learned(args, w, batch, rank, world, dist, dev, pkg, torch)
+    if w["kind"] == "convergence":
+        return run_convergence(args, w, batch, rank, world, dist, dev, pkg, torch)
     T, Np = w["iterations"], w["chains"]
     B = batch.n_channels
     refresh = args.refresh if args.refresh is not None else (50 if w["kind"] == "kronecker" else 0)

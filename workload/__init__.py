@@ -227,6 +227,12 @@ WORKLOADS = {
     # 64 chains, the plain sampler's reference at 40 iterations; the network is trained on plain-
     # sampler samples of 32x32 16-QAM Rayleigh at SNR U[12,24] dB (512 channels x 16 chains,
     # features at 7 points of each chain: ~1.8M rows).
+    # Convergence diagnostics of Figs. 2-3 (Sec. III-B): 2x2 QPSK Rayleigh (16 states), 100
+    # channel realisations at each of 4, 6, 8, 10 dB; exact transition kernels of both proposals,
+    # their spectra and total-variation curves over 50 transitions.
+    "convergence_2x2_qpsk": dict(kind="convergence", nt=2, nr=2, qam=4,
+                                 snr_db=[4.0, 6.0, 8.0, 10.0], per_snr=100, chains=1,
+                                 iterations=50, seed=1006),
     "learned_64x64_16qam": dict(kind="learned", nt=64, nr=64, qam=16, snr_range=(12.0, 24.0),
                                 count=8192, chains=64, iterations=40, seed=1005,
                                 checkpoints=[1, 2, 5, 10, 20, 40],
@@ -239,7 +245,7 @@ WORKLOADS = {
 def workload(name: str, scale: float = 1.0) -> Batch:
     """Materialise a named workload; ``scale`` < 1 keeps that fraction of the channels."""
     w = WORKLOADS[name]
-    if w["kind"] == "rayleigh":
+    if w["kind"] in ("rayleigh", "convergence"):
         n = max(1, int(round(w["per_snr"] * scale)))
         return rayleigh_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], n, w["seed"])
     if w["kind"] == "kronecker":
