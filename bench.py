@@ -241,6 +241,10 @@ def load_batch(scale: float, rank: int, name: str = WORKLOAD):
     elif w["kind"] == "learned":
         n = max(1, int(round(w["count"] * scale)))
         b = workload.learned_eval_batch(w, n, rank_seed(0, rank))
+    elif w["kind"] == "csi":
+        n = max(1, int(round(w["per_point"] * scale)))
+        b = workload.csi_batch(w["nt"], w["nr"], w["qam"], w["snr_db"][0], w["nmse_db"], n,
+                               w["seed"])
     else:
         n = max(1, int(round(w["count"] * scale)))
         b = workload.uneven_batch(n, w["seed"])
@@ -251,7 +255,8 @@ def load_batch(scale: float, rank: int, name: str = WORKLOAD):
 
 
 def ber_of(batch, llr, best_idx):
-    """Uncoded BER of sign(LLR) and of the hard decision, per SNR point."""
+    """Uncoded BER of sign(LLR) and of the hard decision, per SNR point (per channel-estimate
+    NMSE point for imperfect-CSI batches, keyed "nmse<dB>")."""
     bits = batch.tx_bits.astype(np.int64)
     hard = (llr < 0).astype(np.int64)
     errs_soft = hard != bits
@@ -269,14 +274,17 @@ def ber_of(batch, llr, best_idx):
     nb = batch.nt.astype(np.int64) * np.log2(batch.qam).astype(np.int64)
     off = 0
     for b in range(batch.n_channels):
-        s = float(batch.snr_db[b]) if uniform else float(5 * round(batch.snr_db[b] / 5))
+        if batch.nmse_db is not None:
+            s = f"nmse{float(batch.nmse_db[b]):g}"
+        else:
+            s = f"{float(batch.snr_db[b]) if uniform else float(5 * round(batch.snr_db[b] / 5)):g}"
         e = per.setdefault(s, [0, 0, 0])
         e[0] += int(errs_soft[off: off + nb[b]].sum())
         e[1] += int(errs_hard[off: off + nb[b]].sum())
         e[2] += int(nb[b])
         off += nb[b]
-    return {f"{k:g}": {"ber_llr": v[0] / v[2], "ber_best": v[1] / v[2], "bits": v[2]}
-            for k, v in sorted(per.items())}
+    return {k: {"ber_llr": v[0] / v[2], "ber_best": v[1] / v[2], "bits": v[2]}
+            for k, v in per.items()}
 
 
 def cpu_baseline(batch, w, budget_s: float, rank: int):
@@ -314,6 +322,10 @@ def bench_config(args, w, n_channels, world, refresh, l2_note=None):
            "snr_db": snr, "channels": n_channels * world,
            "chains": w["chains"], "iterations": w["iterations"], "preconditioned": True,
            "refresh_period": refresh, "parallelism": f"replicas x{world}"}
+    if "nmse_db" in w:
+        cfg["nmse_db"] = w["nmse_db"]
+    if "rho" in w:
+        cfg["rho"] = w["rho"]
     if getattr(args, "engine", "auto") != "auto":
         cfg["engine"] = args.engine
         cfg["tile"] = getattr(args, "tile", 0) or "default"

@@ -12,7 +12,10 @@ the channel models), none of the detector's arithmetic:
 * channel: iid Rayleigh with entries CN(0, 1/Nr), or Kronecker ``R_r^{1/2} G R_t^{1/2}`` with the
   exponential correlation ``[R]_ij = rho^|i-j|`` (Sec. IV-D, Eq. (37)), square roots by eigendecomposition;
 * noise: CN(0, sigma^2) per receive antenna with ``sigma^2 = Nt / (Nr * 10^(SNR/10))``, which is
-  the paper's SNR definition ``E||Hx||^2 / E||n||^2`` (footnote of Sec. III-B) for these channels.
+  the paper's SNR definition ``E||Hx||^2 / E||n||^2`` (footnote of Sec. III-B) for these channels;
+* imperfect CSI (Sec. IV-F): the receiver's estimate ``H^ = H + E`` with E entries
+  CN(0, sigma_e^2); for CN(0, 1/Nr) channels the NMSE ``E||E||_F^2 / E||H||_F^2`` equals
+  ``Nr sigma_e^2``. y is generated with the true H; the batch carries H^, the detector's view.
 
 H, y and sigma^2 are rounded to single precision once, here, so that every consumer (the FP64
 oracle and the FP32 device path) detects exactly the same problem.
@@ -25,7 +28,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = [
-    "Batch", "generate", "rayleigh_batch", "kronecker_batch", "uneven_batch",
+    "Batch", "generate", "rayleigh_batch", "kronecker_batch", "uneven_batch", "csi_batch",
     "WORKLOADS", "workload",
 ]
 
@@ -52,6 +55,7 @@ class Batch:
     lev_off: np.ndarray     # int64 [B]
     tx_bits: np.ndarray     # uint8 packed, per channel Nt*log2(Qc) bits
     bit_off: np.ndarray     # int64 [B]
+    nmse_db: Optional[np.ndarray] = None   # float64 [B] NMSE of the channel estimate (imperfect CSI)
 
     @property
     def n_channels(self) -> int:
@@ -75,12 +79,15 @@ class Batch:
     def subset(self, idx: Sequence[int]) -> "Batch":
         """A new packed batch holding the channels ``idx`` in that order."""
         parts = [(self.channel(int(b)), int(b)) for b in idx]
-        return _pack(
+        out = _pack(
             [self.nt[b] for _, b in parts], [self.nr[b] for _, b in parts],
             [self.qam[b] for _, b in parts], [self.snr_db[b] for _, b in parts],
             [self.sigma2[b] for _, b in parts], [p[0] for p, _ in parts],
             [p[1] for p, _ in parts], [self.levels(b) for _, b in parts],
         )
+        if self.nmse_db is not None:
+            out.nmse_db = np.asarray([self.nmse_db[b] for _, b in parts], np.float64)
+        return out
 
 
 def _gray_bits(levels: np.ndarray, nbits: int) -> np.ndarray:
@@ -195,6 +202,23 @@ def kronecker_batch(nt: int, nr: int, qam: int, snr_db: Sequence[float], total: 
     return generate(shapes, seed, rho=rho)
 
 
+def csi_batch(nt: int, nr: int, qam: int, snr_db: float, nmse_db: Sequence[float],
+              per_point: int, seed: int) -> Batch:
+    """``per_point`` Rayleigh channels at each NMSE point (point-major order) seen through an
+    imperfect estimate H^ = H + E, E entries CN(0, 10^(NMSE/10) / Nr). The true channels, symbols
+    and noise are those of ``generate`` with the same seed; E comes from its own stream."""
+    pts = [float(v) for v in nmse_db]
+    b = generate([(nt, nr, qam, snr_db)] * (per_point * len(pts)), seed)
+    nm = np.repeat(np.asarray(pts, np.float64), per_point)
+    rng = np.random.default_rng(seed + 104729)
+    n = nt * nr
+    E = rng.standard_normal((b.n_channels, n, 2))
+    se = np.sqrt(10.0 ** (nm / 10.0) / nr / 2.0)
+    E = (E[..., 0] + 1j * E[..., 1]) * se[:, None]
+    Hh = b.H.astype(np.complex128).reshape(b.n_channels, n) + E
+    return dataclasses.replace(b, H=Hh.astype(np.complex64).reshape(-1), nmse_db=nm)
+
+
 def uneven_batch(count: int, seed: int, nts=(8, 16, 32, 64), qams=(4, 16, 64),
                  snr_range=(10.0, 30.0)) -> Batch:
     """Mixed-shape batch: Nt ~ U(nts), Nr ~ U{Nt, 2Nt}, Qc ~ U(qams), SNR ~ U[snr_range]."""
@@ -233,6 +257,23 @@ WORKLOADS = {
     "convergence_2x2_qpsk": dict(kind="convergence", nt=2, nr=2, qam=4,
                                  snr_db=[4.0, 6.0, 8.0, 10.0], per_snr=100, chains=1,
                                  iterations=50, seed=1006),
+    # Large MIMO of Figs. 7-8 (Sec. IV-C): 16x16 and 24x24 16-QAM Rayleigh, 128 chains, T = 100
+    # (the paper's default, Sec. IV-A).
+    "rayleigh_16x16_16qam": dict(kind="rayleigh", nt=16, nr=16, qam=16,
+                                 snr_db=[10.0, 12.0, 14.0, 16.0, 18.0], per_snr=2048, chains=128,
+                                 iterations=100, seed=1007),
+    "rayleigh_24x24_16qam": dict(kind="rayleigh", nt=24, nr=24, qam=16,
+                                 snr_db=[12.0, 14.0, 16.0, 18.0, 20.0], per_snr=1024, chains=128,
+                                 iterations=100, seed=1008),
+    # Correlated channels of Fig. 9 (Sec. IV-D): 16x16 16-QAM Kronecker, rho = 0.5.
+    "kronecker_16x16_16qam": dict(kind="kronecker", nt=16, nr=16, qam=16,
+                                  snr_db=[14.0, 16.0, 18.0, 20.0, 22.0], total=5120, rho=0.5,
+                                  chains=128, iterations=100, seed=1009),
+    # Imperfect CSI of Fig. 11 (Sec. IV-F): 16x16 16-QAM Rayleigh at 16.5 dB, channel-estimate
+    # NMSE -30..-15 dB.
+    "csi_16x16_16qam": dict(kind="csi", nt=16, nr=16, qam=16, snr_db=[16.5],
+                            nmse_db=[-30.0, -25.0, -20.0, -15.0], per_point=1024, chains=128,
+                            iterations=100, seed=1010),
     "learned_64x64_16qam": dict(kind="learned", nt=64, nr=64, qam=16, snr_range=(12.0, 24.0),
                                 count=8192, chains=64, iterations=40, seed=1005,
                                 checkpoints=[1, 2, 5, 10, 20, 40],
@@ -254,6 +295,9 @@ def workload(name: str, scale: float = 1.0) -> Batch:
     if w["kind"] == "uneven":
         n = max(1, int(round(w["count"] * scale)))
         return uneven_batch(n, w["seed"])
+    if w["kind"] == "csi":
+        n = max(1, int(round(w["per_point"] * scale)))
+        return csi_batch(w["nt"], w["nr"], w["qam"], w["snr_db"][0], w["nmse_db"], n, w["seed"])
     if w["kind"] == "learned":
         n = max(1, int(round(w["count"] * scale)))
         return learned_eval_batch(w, n)
