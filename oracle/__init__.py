@@ -119,6 +119,7 @@ def lib():
             l.oracle_all_f.argtypes = [pp, _dp]
             l.oracle_exact_llr.argtypes = [pp, _dp]
             l.oracle_transition_matrix.argtypes = [pp, _dp]
+            l.oracle_llr_list.argtypes = [pp, ctypes.c_int, _ip, ctypes.c_double, _dp]
             l.oracle_detect.restype = ctypes.c_int
             l.oracle_detect.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                         ctypes.c_double, ctypes.POINTER(DetectCfg), _ip, _dp, _ip,
@@ -313,6 +314,14 @@ class Target:
         B = int(np.log2(self.L))
         out = np.zeros(self.N * B)
         lib().oracle_llr_is(self.ptr, s.shape[0], _i(s), _d(out))
+        return out
+
+    def llr_list(self, samples, clip: float) -> np.ndarray:
+        """List-based LLR of Eq. (31) over the distinct samples, clipped to [-clip, clip]."""
+        s = np.ascontiguousarray(samples, np.int32)
+        B = int(np.log2(self.L))
+        out = np.zeros(self.N * B)
+        lib().oracle_llr_list(self.ptr, s.shape[0], _i(s), float(clip), _d(out))
         return out
 
     def n_states(self) -> int:

@@ -557,6 +557,52 @@ void oracle_llr_is(const oracle_problem *p, int S, const int *samples, double *l
     }
 }
 
+/* List-based LLR, Eq. (31): the sample list stands in for the whole state space,
+ * L_k = log sum_{x in list, bit k of x = 0} exp(f(x)) - log sum_{x in list, bit k = 1} exp(f(x)),
+ * over the distinct vectors of the list (the two sums run over sets). The paper leaves a side
+ * with no vector unspecified: it gives +clip (no vector with bit 1) or -clip (none with bit 0),
+ * and every value is clipped to [-clip, clip]. f is untempered (Eq. (3)). */
+void oracle_llr_list(const oracle_problem *p, int S, const int *samples, double clip, double *llr)
+{
+    int N = p->N, B = log2_levels(p->L);
+    double *f = (double *)malloc(sizeof(double) * (size_t)S);
+    int *keep = (int *)malloc(sizeof(int) * (size_t)S);
+    if (!f || !keep) { free(f); free(keep); return; }
+    double x[ORACLE_MAX_N];
+    for (int s = 0; s < S; ++s) {
+        const int *ks = samples + (size_t)s * (size_t)N;
+        keep[s] = 1;
+        for (int r = 0; r < s && keep[s]; ++r) {
+            const int *kr = samples + (size_t)r * (size_t)N;
+            int same = 1;
+            for (int n = 0; n < N; ++n) same &= ks[n] == kr[n];
+            if (same) keep[s] = 0;
+        }
+        if (keep[s]) {
+            levels_to_x(p, ks, x);
+            f[s] = oracle_f(p->H, p->y, p->M, N, p->sigma2, x);
+        }
+    }
+    for (int kb = 0; kb < N * B; ++kb) {
+        int n, pos;
+        bit_position(N, B, kb, &n, &pos);
+        int mask = 1 << (B - 1 - pos);
+        double vp = -INFINITY, vm = -INFINITY;
+        for (int s = 0; s < S; ++s) {
+            if (!keep[s]) continue;
+            double a = f[s];
+            if (gray_of(samples[(size_t)s * (size_t)N + n]) & mask)
+                vm = (vm > a ? vm : a) + softplus(-fabs(vm - a));
+            else
+                vp = (vp > a ? vp : a) + softplus(-fabs(vp - a));
+        }
+        double v = vp == -INFINITY ? -clip : vm == -INFINITY ? clip : vp - vm;
+        llr[kb] = v > clip ? clip : v < -clip ? -clip : v;
+    }
+    free(f);
+    free(keep);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Exact companions for enumerable systems (L^N states).                                       */
 /* ------------------------------------------------------------------------------------------ */
