@@ -156,6 +156,15 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
 mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr, double *best_f,
                                  mcmc_stats *stats, int32_t host_io);
 
+/* List-based soft output, Eq. (31): the conventional alternative to the IS-LLR of
+ * mcmc_detect_estimate. The Np current states of each channel form the sample list, and
+ *   llr_k = log sum_{x, bit k of x = 0} exp(f(x)) - log sum_{x, bit k of x = 1} exp(f(x))
+ * over its distinct vectors, with f the FP64 energy of each state (Eq. (3)). The paper does not
+ * say what an empty side gives: here -clip (no state with bit k = 0) or +clip, and every value
+ * is clipped to [-clip, clip]. clip > 0 and finite. llr [sum over channels Nt_b log2 Qc_b]:
+ * device or host per host_io, in the bit order of mcmc_detect_estimate. Synchronises. */
+mcmc_status mcmc_detect_llr_list(mcmc_detector *d, float *llr, float clip, int32_t host_io);
+
 /* Chain state export: states [sum over channels Np*N_b] int8 level indices, channel-major, then
  * chain-major (chain c of channel b at offset Np*sum_{b'<b} N_b' + c*N_b); f [n_channels*Np]
  * untempered energies of those states, FP64 evaluations (FP32 and MIXED runs track them in FP32

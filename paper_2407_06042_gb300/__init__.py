@@ -36,7 +36,7 @@ ABI_FUNCTIONS = [
     "mcmc_detect_run_chains", "mcmc_detect_estimate", "mcmc_detect_get_chains",
     "mcmc_detect_set_chains", "mcmc_detect_synchronize", "mcmc_detect_destroy",
     "mcmc_status_string", "mcmc_detect_last_error", "mcmc_detect_kernel_launches",
-    "mcmc_detect_noalloc",
+    "mcmc_detect_noalloc", "mcmc_detect_llr_list",
 ]
 
 # Every entry point of include/mcmcdet_learned.h.
@@ -99,6 +99,8 @@ def load(path: Optional[str] = None):
     l.mcmc_detect_estimate.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Stats), i32]
     l.mcmc_detect_estimate.restype = ctypes.c_int
     l.mcmc_detect_get_chains.argtypes = [vp, vp, vp, i32]
+    l.mcmc_detect_llr_list.argtypes = [vp, vp, ctypes.c_float, i32]
+    l.mcmc_detect_llr_list.restype = ctypes.c_int
     l.mcmc_detect_get_chains.restype = ctypes.c_int
     l.mcmc_detect_set_chains.argtypes = [vp, vp, i32]
     l.mcmc_detect_set_chains.restype = ctypes.c_int
@@ -260,6 +262,17 @@ class Detector:
             out["stats"] = dict(transitions=s.transitions, accepts=s.accepts,
                                 refresh_drift=s.refresh_drift)
         return out
+
+    def llr_list(self, clip: float, llr=None, *, host_io: Optional[bool] = None):
+        """List-based LLRs (Eq. (31)) of the current states, clipped to [-clip, clip]; with no
+        buffer, returns a new host numpy array."""
+        if llr is None:
+            _, n_bits, _ = self.sizes()
+            llr = np.zeros(n_bits, np.float32)
+        if host_io is None:
+            host_io = _is_host(llr)
+        self._check(self._l.mcmc_detect_llr_list(self._h, _ptr(llr), float(clip), int(host_io)))
+        return llr
 
     def get_chains(self, states=None, f=None, *, host_io: Optional[bool] = None):
         if states is None and f is None:

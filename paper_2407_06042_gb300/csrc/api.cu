@@ -1023,6 +1023,38 @@ mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr,
     return s;
 }
 
+mcmc_status mcmc_detect_llr_list(mcmc_detector *d, float *llr, float clip, int32_t host_io)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "llr_list before preprocess");
+    if (!llr) return fail(d, MCMC_EINVAL, "null llr");
+    if (!(clip > 0.f) || !std::isfinite(clip)) return fail(d, MCMC_EINVAL, "clip must be > 0 and finite");
+    if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    {
+        mcmc_status es = ensure_energies(d, true);   // FP64 energies of the current states
+        if (es != MCMC_OK) return es;
+    }
+    float *o_llr = llr;
+    if (host_io) {
+        CK(ensure(d->d_out_llr, 4 * d->tot_bits), "alloc out");
+        o_llr = P<float>(d->d_out_llr);
+    }
+    ListLlrArgs la{};
+    la.desc = P<ChannelDesc>(d->d_desc);
+    la.states = P<int8_t>(d->d_states);
+    la.f = P<double>(d->d_f);
+    la.n_channels = d->n_channels;
+    la.chains = d->cfg.chains;
+    la.clip = clip;
+    la.llr = o_llr;
+    la.status = status_ptr(d);
+    CK(launch_list_llr(la, d->cfg.precision == MCMC_PREC_FP64, d->stream), "list LLR kernel");
+    d->launches++;
+    if (host_io) CK(cudaMemcpyAsync(llr, o_llr, 4 * d->tot_bits, cudaMemcpyDeviceToHost, d->stream), "copy out");
+    return read_status(d);
+}
+
 mcmc_status mcmc_detect_get_chains(mcmc_detector *d, int8_t *states, double *f, int32_t host_io)
 {
     if (!d) return MCMC_EINVAL;

@@ -201,7 +201,80 @@ __global__ void __launch_bounds__(256) estimate_kernel(const EstimateArgs A)
     }
 }
 
+// List-based soft output, Eq. (31): the sample list (the Np final states) stands in for the whole
+// state space, over its distinct vectors. One CTA per channel: a 64-bit FNV-1a hash of every
+// chain's levels, a chain kept unless an earlier one holds the same levels (hash match, then a
+// full comparison), the FP64 energies relative to the largest kept one, then per bit a running
+// log-sum-exp over the kept states on each side. A side with no state gives -clip or +clip, and
+// every value is clipped to [-clip, clip] (the paper leaves empty sides open).
+template <typename T>
+__global__ void __launch_bounds__(256) list_llr_kernel(const ListLlrArgs A)
+{
+    const int b = blockIdx.x;
+    const ChannelDesc d = A.desc[b];
+    const int N = d.N, B = d.log2L, Np = A.chains, nt = d.Nt;
+    const int8_t *S = A.states + d.state_off;
+    const double *f = A.f + (long long)b * Np;
+    __shared__ unsigned long long s_h[1024];
+    __shared__ unsigned char s_keep[1024];
+    __shared__ T s_fs[1024];
+    __shared__ double s_red[8];
+    const int tid = threadIdx.x;
+    for (int c = tid; c < Np; c += blockDim.x) {
+        unsigned long long h = 14695981039346656037ull;
+        for (int n = 0; n < N; ++n) {
+            h ^= (unsigned char)S[(long long)c * N + n];
+            h *= 1099511628211ull;
+        }
+        s_h[c] = h;
+    }
+    __syncthreads();
+    double fm = -INFINITY;
+    for (int c = tid; c < Np; c += blockDim.x) {
+        bool keep = true;
+        for (int r = 0; r < c && keep; ++r) {
+            if (s_h[r] != s_h[c]) continue;
+            bool same = true;
+            for (int n = 0; n < N && same; ++n) same = S[(long long)r * N + n] == S[(long long)c * N + n];
+            keep = !same;
+        }
+        s_keep[c] = keep;
+        if (keep) fm = fmax(fm, f[c]);
+    }
+    for (int o = 16; o; o >>= 1) fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = fm;
+    __syncthreads();
+    fm = s_red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) fm = fmax(fm, s_red[w]);
+    for (int c = tid; c < Np; c += blockDim.x) s_fs[c] = (T)(f[c] - fm);
+    __syncthreads();
+    const T clip = (T)A.clip;
+    for (int kb = tid; kb < N * B; kb += blockDim.x) {
+        const int ant = kb / (2 * B), r = kb % (2 * B);
+        const int n = r < B ? ant : nt + ant, pos = r < B ? r : r - B;
+        const int mask = 1 << (B - 1 - pos);
+        Lse<T> vp, vm;
+        for (int c = 0; c < Np; ++c) {
+            if (!s_keep[c]) continue;
+            if (gray_of(S[(long long)c * N + n]) & mask) vm.add(s_fs[c]);
+            else vp.add(s_fs[c]);
+        }
+        T v = !(vp.s > T(0)) ? -clip : !(vm.s > T(0)) ? clip : vp.value() - vm.value();
+        if (!isfinite((double)v)) set_status(A.status, kStatusNumeric);
+        v = v > clip ? clip : (v < -clip ? -clip : v);
+        A.llr[d.bit_off + kb] = (float)v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_list_llr(const ListLlrArgs &a, bool fp64, cudaStream_t s)
+{
+    if (a.n_channels <= 0) return cudaSuccess;
+    if (fp64) list_llr_kernel<double><<<a.n_channels, 256, 0, s>>>(a);
+    else list_llr_kernel<float><<<a.n_channels, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_estimate(const EstimateArgs &a, bool fp64, cudaStream_t s)
 {

@@ -98,6 +98,17 @@ struct ChainArgs {
     uint32_t philox_rk[2 * kPhiloxRounds];   // round keys of (key0, key1), set at launch
 };
 
+struct ListLlrArgs {
+    const ChannelDesc *desc;
+    const int8_t *states;
+    const double *f;        // FP64 energies of the states
+    int n_channels;
+    int chains;
+    float clip;
+    float *llr;
+    unsigned *status;
+};
+
 struct EstimateArgs {
     const ChannelDesc *desc;
     const int8_t *states;
@@ -167,5 +178,6 @@ cudaError_t launch_init_states(const InitArgs &a, cudaStream_t s);
 cudaError_t launch_refresh(const RefreshArgs &a, cudaStream_t s);
 cudaError_t launch_chains_simt(const ChainArgs &a, bool fp64, size_t smem, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateArgs &a, bool fp64, cudaStream_t s);
+cudaError_t launch_list_llr(const ListLlrArgs &a, bool fp64, cudaStream_t s);
 
 }  // namespace mcmcdet

@@ -59,6 +59,7 @@ def test_host_only_entry_points():
     assert lib.mcmc_detect_destroy(None) == 0
     assert lib.mcmc_detect_kernel_launches(None) == 0
     assert lib.mcmc_detect_last_error(None) == b"null handle"
+    assert lib.mcmc_detect_llr_list(None, None, 1.0, 0) == 1
     assert lib.mcmc_detect_run_chains(None, 1, 0) == 1
     assert lib.mcmc_detect_create(None, None) == 1
 
