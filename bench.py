@@ -633,6 +633,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--compare-fp32", action="store_true", help="also time the plain FP32 sampler")
+    ap.add_argument("--compare-llr", type=float, default=0.0, metavar="CLIP",
+                    help="also time the list-based LLR (Eq. (31), clipped at CLIP) on the final "
+                         "states and report its BER beside the IS-LLR's")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workload.WORKLOADS),
                     help="bench a parity-test configuration instead of the headline one")
     ap.add_argument("--graph", action="store_true", help="replay run_chains from a CUDA graph")
@@ -782,6 +785,23 @@ def main():
                "d2h_bytes_per_step": int(hi.numel() + hl.numel() * 4 + hb.numel() * 8),
                "detections_per_s": B * world / dt}
 
+    llr_line = None
+    if args.compare_llr > 0:
+        # the timed run's final states: the list read-out on the same samples as the IS-LLR
+        o_list = torch.empty_like(o_llr)
+        for _ in range(2):
+            det.llr_list(args.compare_llr, o_list, host_io=False)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        det.llr_list(args.compare_llr, o_list, host_io=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        bl = ber_of(batch, o_list.cpu().numpy(), o_idx.cpu().numpy())
+        llr_line = {"clip": args.compare_llr, "readout_ms": ev0.elapsed_time(ev1),
+                    "ber_list": {k: v["ber_llr"] for k, v in bl.items()},
+                    "ber_is": {k: v["ber_llr"] for k, v in ber.items()}}
+
     fp32_line = None
     if args.compare_fp32 and precision != "fp32":
         d32 = make("fp32")
@@ -814,6 +834,8 @@ def main():
                 "e2e": e2e, "cpu_baseline": cb}
         if fp32_line:
             line["plain_fp32"] = fp32_line
+        if llr_line:
+            line["list_llr"] = llr_line
         print(json.dumps(line), flush=True)
     det.destroy()
     if dist:
