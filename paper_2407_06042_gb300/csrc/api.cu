@@ -384,10 +384,13 @@ mcmc_status build_groups(mcmc_detector *d)
             if (g.tile <= 0 || !simt_fit(d, g.tile, g.max_n, g.max_nop, &g.bt_smem, &g.smem))
                 return fail(d, MCMC_EUNSUPPORTED, "channels of N = %d do not fit the CUDA-core kernel", g.max_n);
         }
-        g.items.reserve(kv.second.size() * (size_t)((Np + g.tile - 1) / g.tile));
+        // chains per work item: the SIMT tile, or the tcgen05 plan's chains per CTA (the tile
+        // times its chain groups)
+        const int per = g.engine == MCMC_ENGINE_TC ? g.plan.chains_per_cta : g.tile;
+        g.items.reserve(kv.second.size() * (size_t)((Np + per - 1) / per));
         for (int b : kv.second)
-            for (int c0 = 0; c0 < Np; c0 += g.tile)
-                g.items.push_back(WorkItem{b, c0, std::min(g.tile, Np - c0), 0});
+            for (int c0 = 0; c0 < Np; c0 += per)
+                g.items.push_back(WorkItem{b, c0, std::min(per, Np - c0), 0});
         if (!d->spare_items.empty()) {
             g.d_items = d->spare_items.back();
             d->spare_items.pop_back();
@@ -494,9 +497,10 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
                           ? tc_make_plan(g.max_n, g.tile, d->cfg.split_terms, d->smem_optin, &g.plan)
                           : simt_fit(d, g.tile, g.max_n, g.max_nop, &g.bt_smem, &g.smem);
             if (!ok) continue;
+            const int per = cand.engine == MCMC_ENGINE_TC ? g.plan.chains_per_cta : g.tile;
             for (int b : sample)
-                for (int cc = 0; cc < d->cfg.chains; cc += g.tile)
-                    g.items.push_back(WorkItem{b, cc, std::min(g.tile, d->cfg.chains - cc), 0});
+                for (int cc = 0; cc < d->cfg.chains; cc += per)
+                    g.items.push_back(WorkItem{b, cc, std::min(per, d->cfg.chains - cc), 0});
             CK(ensure(g.d_items, sizeof(WorkItem) * g.items.size()), "alloc probe items");
             CK(cudaMemcpyAsync(g.d_items.p, g.items.data(), sizeof(WorkItem) * g.items.size(),
                                cudaMemcpyHostToDevice, d->stream), "copy probe items");

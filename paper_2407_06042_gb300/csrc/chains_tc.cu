@@ -75,6 +75,10 @@ struct TcLayout {
 // shared memory and is streamed from L2 in 128-row x Kp chunks through two buffers.
 __host__ __device__ constexpr bool tc_streamed(int MT) { return MT >= 3; }
 
+// Chain groups per CTA: channels of N <= 32 use half of the 64 dimension rows of a tile, so the
+// tile holds their rows twice and each copy serves its own group of chains.
+__host__ __device__ inline int tc_groups(int N) { return (N + 15) / 16 * 16 <= 32 ? 2 : 1; }
+
 __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
 {
     TcLayout L{};
@@ -129,6 +133,9 @@ struct TcCtx {
     uint32_t idesc;
     uint32_t sbo_a, sbo_b;
     int tid, warp, lane, q, cgi, h, dl, C, S, Kp;
+    // chain groups: with N <= 32 the four TMEM lane quadrants hold two copies of the operand rows
+    // (quadrants 0-1 and 2-3), and each copy serves its own C / 2 chains
+    int gofs;                     // first chain of this thread's group
     uint32_t mma_phase;
     // streamed A operand (thread 0's pipeline state)
     const uint8_t *asrc;          // this work item's operand block in global memory
@@ -283,7 +290,7 @@ __device__ __forceinline__ void tc_read(const TcCtx &x, float (&g)[MT][4], float
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
         float v[8];
-        tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + 8 * x.cgi), v);
+        tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + x.gofs + 8 * x.cgi), v);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float send = x.h ? v[j] : v[4 + j];
@@ -300,7 +307,7 @@ __device__ __forceinline__ void tc_read(const TcCtx &x, float (&g)[MT][4], float
 __device__ __forceinline__ void tc_read_tile(const TcCtx &x, int t, float (&g)[4], float (&m)[4])
 {
     float v[8];
-    tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + 8 * x.cgi), v);
+    tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + x.gofs + 8 * x.cgi), v);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const float send = x.h ? v[j] : v[4 + j];
@@ -352,7 +359,7 @@ __device__ __forceinline__ void table_load(uint32_t ta, uint32_t te, Table2<L> &
 // One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
 // every chain column is live, so no per-(dimension, chain) validity test is needed. Levels are
 // held as exact small floats.
-template <int MT, int L, bool FULL>
+template <int MT, int L, bool FULL, int G>
 __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const ChannelDesc &d,
                         bool &alive)
 {
@@ -363,7 +370,20 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     const float inv2c = 0.5f / c2;
     const float cf2 = (float)d.cf * kLog2e;       // df_tau -> log2 units
     const float lm1 = (float)(L - 1);
-    const int cbase = 8 * x.cgi + 4 * x.h;         // first of this thread's 4 chains (CTA-local)
+    static_assert(G == 1 || (G == 2 && MT == 1), "two chain groups only for one tile");
+    const int Cq = C / G;                                  // chains per group
+    const int gofs = G == 1 ? 0 : (x.q >> 1) * Cq;         // this thread's group's first chain
+    const int cbase = gofs + 8 * x.cgi + 4 * x.h;          // first of its 4 chains (CTA-local)
+    // sum of the per-quadrant partials of chain c over the quadrants holding its dimensions
+    auto quad_sum = [&](const float *v, int c) {
+        if constexpr (G == 1) {
+            return v[c] + v[Cq + c] + v[2 * Cq + c] + v[3 * Cq + c];
+        } else {
+            const bool hi = c >= Cq;
+            const int cl = hi ? c - Cq : c, g0 = hi ? 2 : 0;
+            return v[g0 * Cq + cl] + v[(g0 + 1) * Cq + cl];
+        }
+    };
     float zt[MT], wt[MT];
     int nd[MT];
     bool live[MT][4];
@@ -386,7 +406,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     uint32_t boff[MT];                             // byte offset of this thread's B element, chain cbase
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
-        const int n = 64 * t + 16 * x.q + x.dl;
+        const int n = 64 * t + 16 * (G == 1 ? x.q : (x.q & 1)) + x.dl;
         nd[t] = n;
         const bool v = FULL || n < N;
         zt[t] = v ? gz[n] : 0.f;
@@ -494,14 +514,14 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         const float rq = reduce_scatter16(quad, x.dl);
         if ((x.dl & 3) == 0) {
             const int c = cbase + (x.dl >> 2);
-            x.red[x.q * C + c] = rl;
-            x.dred[x.q * C + c] = rq;
+            x.red[x.q * Cq + c - gofs] = rl;
+            x.dred[x.q * Cq + c - gofs] = rq;
         }
         __syncthreads();
         if (x.tid < nC) {
             const int c = x.tid;
-            const double l = (double)x.red[c] + x.red[C + c] + x.red[2 * C + c] + x.red[3 * C + c];
-            const double qd = (double)x.dred[c] + x.dred[C + c] + x.dred[2 * C + c] + x.dred[3 * C + c];
+            const double l = (double)quad_sum(x.red, c);
+            const double qd = (double)quad_sum(x.dred, c);
             const double f0 = -(A.yy[it.b] - 2.0 * l + qd) * d.inv_s2;
             x.sfc[c] = f0;
             x.sfb[c] = f0;
@@ -610,15 +630,15 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         const float rd = reduce_scatter16(dpart, x.dl);
         if ((x.dl & 3) == 0) {
             const int c = cbase + (x.dl >> 2);
-            x.red[x.q * C + c] = rs;
-            x.dred[x.q * C + c] = rd;
+            x.red[x.q * Cq + c - gofs] = rs;
+            x.dred[x.q * Cq + c - gofs] = rd;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         if (__syncthreads_or(!mma_ok)) { alive = false; set_status(A.status, kStatusTimeout); break; }
         if (x.tid < nC) {
             const int c = x.tid;
-            const float s = x.red[c] + x.red[C + c] + x.red[2 * C + c] + x.red[3 * C + c];
-            const float sd = x.dred[c] + x.dred[C + c] + x.dred[2 * C + c] + x.dred[3 * C + c];
+            const float s = quad_sum(x.red, c);
+            const float sd = quad_sum(x.dred, c);
             const float logr = fmaf(cf2, sd, s);
             const float loga = logr < 0.f ? logr : 0.f;
             int ok = logu < loga;
@@ -767,15 +787,16 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     }
 }
 
-template <int MT, int L>
+template <int MT, int L, int G>
 __device__ __forceinline__ void tc_item_dispatch(const ChainArgs &A, TcCtx &x, const WorkItem &it,
                                                  const ChannelDesc &d, bool &alive)
 {
-    if (d.N == 64 * MT && it.nc == x.C) tc_item<MT, L, true>(A, x, it, d, alive);
-    else tc_item<MT, L, false>(A, x, it, d, alive);
+    if (d.N == 64 * MT / G && it.nc == x.C) tc_item<MT, L, true, G>(A, x, it, d, alive);
+    else tc_item<MT, L, false, G>(A, x, it, d, alive);
 }
 
-template <int MT>
+// G: chain groups per CTA (2 for N <= 32, one tile); C: chains per CTA over all groups.
+template <int MT, int G>
 __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
     chains_tc_kernel(const ChainArgs A, const int C, const int S, const int Kp)
 {
@@ -808,6 +829,7 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
     x.h = x.lane >> 4;
     x.dl = x.lane & 15;
     x.C = C;
+    x.gofs = G == 1 ? 0 : (x.q >> 1) * (C / G);   // first chain of this thread's group
     x.S = S;
     x.Kp = Kp;
     x.sbo_a = (uint32_t)(Kp / 8) * 128u;
@@ -858,9 +880,9 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
         if constexpr (tc_streamed(MT)) {
             // chunks are streamed by the transitions themselves
             switch (d.L) {
-            case 2: tc_item_dispatch<MT, 2>(A, x, it, d, alive); break;
-            case 4: tc_item_dispatch<MT, 4>(A, x, it, d, alive); break;
-            default: tc_item_dispatch<MT, 8>(A, x, it, d, alive); break;
+            case 2: tc_item_dispatch<MT, 2, G>(A, x, it, d, alive); break;
+            case 4: tc_item_dispatch<MT, 4, G>(A, x, it, d, alive); break;
+            default: tc_item_dispatch<MT, 8, G>(A, x, it, d, alive); break;
             }
             const bool drained = x.tid != 0 || tc_stream_drain(x);
             if (__syncthreads_or(!drained || (x.tid == 0 && x.fail)) && alive) {
@@ -895,9 +917,9 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
         tma_phase ^= 1u;
         if (!alive) break;
         switch (d.L) {
-        case 2: tc_item_dispatch<MT, 2>(A, x, it, d, alive); break;
-        case 4: tc_item_dispatch<MT, 4>(A, x, it, d, alive); break;
-        default: tc_item_dispatch<MT, 8>(A, x, it, d, alive); break;
+        case 2: tc_item_dispatch<MT, 2, G>(A, x, it, d, alive); break;
+        case 4: tc_item_dispatch<MT, 4, G>(A, x, it, d, alive); break;
+        default: tc_item_dispatch<MT, 8, G>(A, x, it, d, alive); break;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -927,7 +949,8 @@ __global__ void pack_kernel(const ChannelDesc *desc, const float *bt32, uint8_t 
         const int t = u / (128 * kgs), rem = u % (128 * kgs);
         const int r = rem / kgs, kg = rem % kgs;
         const int q = r >> 5, l = r & 31;
-        const int n = 64 * t + 16 * q + (l & 15), part = l >> 4;
+        const int qpg = tc_groups(N) == 2 ? 2 : 4;     // two copies of the rows for N <= 32
+        const int n = 64 * t + 16 * (q % qpg) + (l & 15), part = l >> 4;
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -970,18 +993,20 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
     if (16 * chains_per_cta > TC_MAX_THREADS) return false;
     const int MT = (max_n + 63) / 64;
     const int Kp = (max_n + 15) / 16 * 16;
-    const int C = chains_per_cta;
+    const int C = chains_per_cta;                  // chains per group (one group of threads each)
+    const int Ct = tc_groups(max_n) * C;           // chains per CTA and work item
     const int S = split_terms;
-    const TcLayout L = tc_layout(S, MT, Kp, C);
+    const TcLayout L = tc_layout(S, MT, Kp, Ct);
     if (L.total > smem_optin) return false;
     plan->valid = 1;
-    plan->chains_per_cta = C;
+    plan->chains_per_cta = Ct;
+    plan->groups = Ct / C;
     plan->m_tiles = MT;
     plan->kdim = Kp;
     plan->max_n = max_n;
     plan->split_terms = S;
     plan->threads = 16 * C;                   // 4 TMEM quadrants x C/8 column groups x 32
-    plan->tmem_cols = pow2_at_least(MT * C + tc_table_cols(MT, C));   // accumulators + carried factors
+    plan->tmem_cols = pow2_at_least(MT * Ct + tc_table_cols(MT, C));   // accumulators + carried factors
     // resident CTAs per SM: shared memory, threads, registers (as the launch bounds allow: 64
     // per thread for one tile, 128 beyond, at the default bounds), and TMEM
     const int regs = std::min(255, (MT == 1 ? 65536 / (TC_MIN_BLOCKS * TC_MAX_THREADS)
@@ -1028,10 +1053,10 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
         return cudaSuccess;
     };
     switch (plan.m_tiles) {
-    case 1: e = go(chains_tc_kernel<1>); break;
-    case 2: e = go(chains_tc_kernel<2>); break;
-    case 3: e = go(chains_tc_kernel<3>); break;
-    default: e = go(chains_tc_kernel<4>); break;
+    case 1: e = plan.groups == 2 ? go(chains_tc_kernel<1, 2>) : go(chains_tc_kernel<1, 1>); break;
+    case 2: e = go(chains_tc_kernel<2, 1>); break;
+    case 3: e = go(chains_tc_kernel<3, 1>); break;
+    default: e = go(chains_tc_kernel<4, 1>); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

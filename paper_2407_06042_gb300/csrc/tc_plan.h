@@ -11,6 +11,7 @@ namespace mcmcdet {
 struct TcPlan {
     int valid;
     int chains_per_cta;     // MMA N extent: chains of one channel per CTA (multiple of 16)
+    int groups;             // chain groups per CTA: 2 when N <= 32 (the operand rows held twice)
     int m_tiles;            // 128-row tiles of the A operand (interleaved Gt / P~Gt rows)
     int kdim;               // K extent: N rounded up to 16
     int max_n;
@@ -22,7 +23,8 @@ struct TcPlan {
 };
 
 // Kernel shape for a group of channels with the same K extent (N rounded up to 16) and tile
-// count, `chains_per_cta` chains (multiple of 16) per CTA; false if it does not fit.
+// count, `chains_per_cta` chains (multiple of 16) per group of threads (twice that per CTA and
+// work item when N <= 32); false if it does not fit.
 bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, TcPlan *plan);
 
 // Bytes of one channel's packed BF16 operand block (depends on its N only).
