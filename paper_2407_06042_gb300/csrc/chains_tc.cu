@@ -21,7 +21,9 @@
 //   5. accepted chains keep x', Gt x' and the drift slope of x'.
 // A-operand row layout (128 rows per tile t): row 32q + l holds dimension 64t + 16q + (l & 15) of
 // Gt (l < 16) or of P~ Gt (l >= 16), so each warp's TMEM quadrant carries both quantities of
-// 16 dimensions; each thread owns one dimension of 4 chains per tile. Both operands are K-major,
+// 16 dimensions; each thread owns one dimension of 4 chains per tile. Channels of N <= 32 hold
+// their rows twice (quadrants 0-1 and 2-3: dimension 16 (q mod 2) + (l & 15)), and each copy
+// serves its own group of chains, so a CTA runs twice the chains with the same threads. Both operands are K-major,
 // no swizzle, in 8 x 16-byte core matrices: K-adjacent core matrices 128 B apart (LBO), 8-row
 // groups (K/8)*128 B apart (SBO).
 // Every wait is bounded: a wait that runs out sets the timeout status bit, the CTA stops issuing
@@ -68,7 +70,7 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 
 // Shared-memory layout of the kernel (bytes).
 struct TcLayout {
-    uint32_t a, b, red, dred, acc, impr, ref, fst, cnt, fref, kb, dg, bar, tmem, total;
+    uint32_t a, b, red, dred, acc, ref, fst, cnt, fref, kb, dg, bar, tmem, total;
 };
 
 // The A operand stays resident for MT <= 2 (N <= 128). Beyond that it no longer fits one SM's
@@ -94,7 +96,6 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
     L.red = take(4u * C * 4, 16);
     L.dred = take(4u * C * 4, 16);
     L.acc = take((uint32_t)C * 4, 16);
-    L.impr = take((uint32_t)C * 4, 16);
     L.ref = take((uint32_t)C * 8, 16);       // FP64 refresh results per chain
     L.fst = take((uint32_t)C * 16, 16);      // tracked and best energies per chain
     L.cnt = take((uint32_t)C * 4, 16);       // accepted moves per chain
@@ -120,7 +121,7 @@ __host__ __device__ inline uint32_t b_sbo(int Kp)
 struct TcCtx {
     unsigned char *sA, *sB;
     float *red, *dred;
-    int *sacc, *simpr;
+    int *sacc;
     double *sref;
     double *sfc, *sfb;            // tracked and best energies of the CTA's chains
     unsigned *scnt;
@@ -808,7 +809,6 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
     x.red = reinterpret_cast<float *>(smem + lay.red);
     x.dred = reinterpret_cast<float *>(smem + lay.dred);
     x.sacc = reinterpret_cast<int *>(smem + lay.acc);
-    x.simpr = reinterpret_cast<int *>(smem + lay.impr);
     x.sref = reinterpret_cast<double *>(smem + lay.ref);
     x.sfc = reinterpret_cast<double *>(smem + lay.fst);
     x.sfb = x.sfc + C;
