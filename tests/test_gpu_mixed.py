@@ -143,3 +143,20 @@ def test_mixed_kronecker_256_refresh():
             assert abs(f[ch * 32 + c] - fx) <= 1e-9 * abs(fx)
     assert out["stats"]["refresh_drift"] < 1e-1
     det.destroy()
+
+
+@pytest.mark.parametrize("tile,shapes", [
+    (16, [(16, 16, 16, 16.0)] * 3),                  # N = 32: every work item full, 2 x 16 chains
+    (32, [(16, 16, 16, 16.0), (16, 20, 4, 10.0)]),   # 2 x 32 chains per CTA (64 per work item)
+    (16, [(15, 15, 16, 14.0), (9, 12, 64, 22.0)]),   # N = 30, 18: ragged dimensions in each group
+])
+def test_mixed_two_chain_groups(tile, shapes):
+    """Channels of N <= 32 run two chain groups per CTA (the operand rows held twice); step
+    parity against the oracle with full and partial work items and both tiles."""
+    b = workload.generate(shapes, 93)
+    det = H.make_detector(b, chains=96, precision="mixed", split_terms=2, seed=5, engine=TC, tile=tile)
+    r = H.step_parity(det, b, H.targets(b), seed=5, steps=4, w_cat=2e-4, w_acc=2e-3)
+    assert r["steps"] == 4 * 96 * b.n_channels
+    assert r["bad"] == 0, r
+    assert r["mism"] <= max(4, r["steps"] // 500), r
+    det.destroy()
