@@ -195,9 +195,9 @@ int64_t mcmc_detect_kernel_launches(const mcmc_detector *d);
 #define MCMC_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* Whole FP32 detection of a small batch without any device allocation. The paper has no
- * counterpart: this entry point exists for callers that cannot call cudaMalloc -- code running
- * while a CUDA graph is captured on its stream, real-time loops that must not block on the
- * allocator, hosts whose device memory belongs to a pool they do not control.
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc -- real-time loops
+ * that must not block on the allocator, hosts whose device memory belongs to a pool they do not
+ * control, components whose device memory budget is fixed when they start.
  *
  * It performs what mcmc_detect_create + preprocess + run_chains(iterations, 0) + estimate do
  * for precision MCMC_PREC_FP32 (same kernels, same results), but takes every intermediate buffer

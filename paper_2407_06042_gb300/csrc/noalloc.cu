@@ -1,8 +1,8 @@
 // noalloc.cu -- one-call detection of a small batch that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured on
-// their stream, real-time loops that must never block on the allocator, and hosts whose device
-// memory is carved up in advance by a pool they do not control. For them this entry point runs
+// Some callers cannot call cudaMalloc: real-time loops that must never block on the allocator,
+// hosts whose device memory is carved up in advance by a pool they do not control, and
+// components whose device memory budget is fixed when they start. For them this entry point runs
 // the whole FP32 detection (preparation, chains, read-out) with every intermediate buffer taken
 // from one fixed array in device global memory, declared below at file scope. The array exists
 // on every GPU that loads this library, from load until the process exits.

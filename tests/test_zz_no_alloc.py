@@ -1,8 +1,8 @@
 """The allocation-free detection entry point against the handle-based one.
 
-``mcmc_detect_noalloc`` is for callers that cannot call cudaMalloc (code running inside CUDA
-graph capture, real-time loops that must not wait on the allocator, hosts whose device memory
-belongs to a pool they do not manage). It runs the same FP32 kernels with every intermediate
+``mcmc_detect_noalloc`` is for callers that cannot call cudaMalloc (real-time loops that must not
+wait on the allocator, hosts whose device memory belongs to a pool they do not manage,
+components whose device memory budget is fixed when they start). It runs the same FP32 kernels with every intermediate
 buffer in one fixed device array, so its labels, LLRs and energies must equal those of
 create / preprocess / run_chains / estimate, within the FP32 tolerances the other GPU tests
 use. Two calls in a row (different batches, then a repeat) check that each call starts from a
