@@ -83,24 +83,29 @@ typedef struct {
                                (FP32/MIXED; FP64 mode is exact throughout); 0: never during a run */
     int32_t split_terms;    /* MIXED: BF16 terms G is split into (2 = hi+lo, 3 = hi+lo+lo2) */
     int32_t engine;         /* MCMC_ENGINE_AUTO (autotuned per shape class), _SIMT or _TC, optionally
-                               OR-ed with MCMC_ENGINE_GRAPH */
-    int32_t tile;           /* with an explicit engine: chains per work item (TC: 16 or 32; SIMT: a
-                               multiple of 8, at most 64); 0: the engine's default. Must be 0 with
-                               MCMC_ENGINE_AUTO (the autotuner picks it) */
+                               OR-ed with MCMC_ENGINE_GRAPH and MCMC_ENGINE_NO_CLUSTER */
+    int32_t tile;           /* with an explicit engine: chains per work item (TC: 16 or 32, and 64
+                               for channels with N = 2 Nt > 128, which run on thread-block
+                               clusters; SIMT: a multiple of 8, at most 64); 0: the engine's
+                               default. Must be 0 with MCMC_ENGINE_AUTO (the autotuner picks it) */
     uint64_t seed;          /* Philox key */
     void *stream;           /* cudaStream_t to enqueue on; NULL: the handle creates its own */
 } mcmc_config;
 
 /* Chain-kernel engine. AUTO: every shape class (N, L) of a batch gets the launch shape an
  * autotuner found fastest when the class was first seen in the process (probe launches timed on
- * that batch at preprocess): for MIXED precision the tcgen05 kernel at 16 or 32 chains per CTA or
- * the CUDA-core kernel (FP32 products, at least as accurate as the split-BF16 ones); for FP32 the
+ * that batch at preprocess): for MIXED precision the tcgen05 kernel at 16 or 32 chains per CTA
+ * (also 64 for N > 128) or the CUDA-core kernel (FP32 products, at least as accurate as the split-BF16 ones); for FP32 the
  * CUDA-core kernel's chain tile. SIMT / TC force an engine (TC requires MIXED). GRAPH: each
  * run_chains captures its launches (one per shape class) into a CUDA graph and replays it. */
 #define MCMC_ENGINE_AUTO 0
 #define MCMC_ENGINE_SIMT 1      /* CUDA-core chain kernel (FP64 / FP32 / MIXED) */
-#define MCMC_ENGINE_TC 2        /* tcgen05 chain kernel (MIXED, N <= 128) */
+#define MCMC_ENGINE_TC 2        /* tcgen05 chain kernel (MIXED, N <= 256) */
 #define MCMC_ENGINE_GRAPH 4     /* flag: replay run_chains from a captured CUDA graph */
+#define MCMC_ENGINE_NO_CLUSTER 8 /* flag: channels with N > 128 run the single-CTA tcgen05 kernel,
+                                    which streams the Gram operand from L2 every transition,
+                                    instead of a thread-block cluster with one resident operand
+                                    tile per CTA */
 
 /* Per-batch statistics (host struct, filled by mcmc_detect_estimate when non-NULL). */
 typedef struct {

@@ -20,12 +20,13 @@ from . import build as _build
 __all__ = [
     "Detector", "Config", "Stats", "lib", "load", "MCMC_PREC_FP64", "MCMC_PREC_FP32",
     "MCMC_PREC_MIXED", "MCMC_ENGINE_AUTO", "MCMC_ENGINE_SIMT", "MCMC_ENGINE_TC",
-    "MCMC_ENGINE_GRAPH", "McmcError", "Mlp",
+    "MCMC_ENGINE_GRAPH", "MCMC_ENGINE_NO_CLUSTER", "McmcError", "Mlp",
     "ABI_FUNCTIONS", "ABI_FUNCTIONS_LEARNED", "ABI_FUNCTIONS_DIAG", "transition_diagnostics",
 ]
 
 MCMC_PREC_FP64, MCMC_PREC_FP32, MCMC_PREC_MIXED = 0, 1, 2
 MCMC_ENGINE_AUTO, MCMC_ENGINE_SIMT, MCMC_ENGINE_TC, MCMC_ENGINE_GRAPH = 0, 1, 2, 4
+MCMC_ENGINE_NO_CLUSTER = 8
 _PREC = {"fp64": MCMC_PREC_FP64, "fp32": MCMC_PREC_FP32, "mixed": MCMC_PREC_MIXED}
 STATUS = {0: "MCMC_OK", 1: "MCMC_EINVAL", 2: "MCMC_ENOMEM", 3: "MCMC_ECUDA", 4: "MCMC_ETIMEOUT",
           5: "MCMC_ENUMERIC", 6: "MCMC_ESTATE", 7: "MCMC_EUNSUPPORTED"}

@@ -310,7 +310,7 @@ std::mutex g_tuned_mu;
 ClassKey class_key(const mcmc_detector *d, const ChannelDesc &c)
 {
     return ClassKey{c.N, c.L, d->cfg.chains, d->cfg.precision, d->cfg.preconditioned,
-                    d->cfg.split_terms, d->cfg.engine & 3};
+                    d->cfg.split_terms, d->cfg.engine & (3 | MCMC_ENGINE_NO_CLUSTER)};
 }
 
 // SIMT launch shape for chains-per-item cg: whether the operand fits shared memory and the size.
@@ -378,7 +378,8 @@ mcmc_status build_groups(mcmc_detector *d)
             g.max_nop = std::max(g.max_nop, d->desc[b].NOp);
         }
         if (g.engine == MCMC_ENGINE_TC) {
-            if (!tc_make_plan(g.max_n, g.tile, d->cfg.split_terms, d->smem_optin, &g.plan))
+            if (!tc_make_plan(g.max_n, g.tile, d->cfg.split_terms, d->smem_optin,
+                              !(d->cfg.engine & MCMC_ENGINE_NO_CLUSTER), &g.plan))
                 return fail(d, MCMC_EUNSUPPORTED, "no tensor-core plan for N = %d", g.max_n);
         } else {
             if (g.tile <= 0 || !simt_fit(d, g.tile, g.max_n, g.max_nop, &g.bt_smem, &g.smem))
@@ -469,6 +470,7 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
         const ChannelDesc &c0 = d->desc[kv.second[0]];
         std::vector<Choice> cands;
         if (prec == MCMC_PREC_MIXED && c0.N <= kMaxN) {
+            if (c0.N > 128) cands.push_back(Choice{MCMC_ENGINE_TC, 64});   // cluster kernel only
             cands.push_back(Choice{MCMC_ENGINE_TC, 32});
             cands.push_back(Choice{MCMC_ENGINE_TC, 16});
         }
@@ -494,7 +496,8 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
             g.max_n = c0.N;
             g.max_nop = c0.NOp;
             bool ok = cand.engine == MCMC_ENGINE_TC
-                          ? tc_make_plan(g.max_n, g.tile, d->cfg.split_terms, d->smem_optin, &g.plan)
+                          ? tc_make_plan(g.max_n, g.tile, d->cfg.split_terms, d->smem_optin,
+                                         !(d->cfg.engine & MCMC_ENGINE_NO_CLUSTER), &g.plan)
                           : simt_fit(d, g.tile, g.max_n, g.max_nop, &g.bt_smem, &g.smem);
             if (!ok) continue;
             const int per = cand.engine == MCMC_ENGINE_TC ? g.plan.chains_per_cta : g.tile;
@@ -597,9 +600,10 @@ mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out)
         cfg->precision < MCMC_PREC_FP64 || cfg->precision > MCMC_PREC_MIXED ||
         (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < 0 ||
         cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 ||
-        (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH)) != 0 || (cfg->engine & 3) == 3 ||
+        (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH | MCMC_ENGINE_NO_CLUSTER)) != 0 || (cfg->engine & 3) == 3 ||
         cfg->tile < 0 || (cfg->tile != 0 && (cfg->engine & 3) == MCMC_ENGINE_AUTO) ||
-        ((cfg->engine & 3) == MCMC_ENGINE_TC && cfg->tile != 0 && cfg->tile != 16 && cfg->tile != 32) ||
+        ((cfg->engine & 3) == MCMC_ENGINE_TC && cfg->tile != 0 && cfg->tile != 16 && cfg->tile != 32 &&
+         cfg->tile != 64) ||
         ((cfg->engine & 3) == MCMC_ENGINE_SIMT && (cfg->tile % 8 != 0 || cfg->tile > 64)))
         return MCMC_EINVAL;
     if (cfg->precision != MCMC_PREC_MIXED && (cfg->engine & 3) == MCMC_ENGINE_TC) return MCMC_EINVAL;

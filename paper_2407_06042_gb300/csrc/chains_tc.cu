@@ -70,7 +70,7 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 
 // Shared-memory layout of the kernel (bytes).
 struct TcLayout {
-    uint32_t a, b, red, dred, acc, ref, fst, cnt, fref, kb, dg, bar, tmem, total;
+    uint32_t a, b, red, dred, acc, ref, fst, cnt, fref, kb, dg, xs, bar, tmem, total;
 };
 
 // The A operand stays resident for MT <= 2 (N <= 128). Beyond that it no longer fits one SM's
@@ -81,7 +81,8 @@ __host__ __device__ constexpr bool tc_streamed(int MT) { return MT >= 3; }
 // tile holds their rows twice and each copy serves its own group of chains.
 __host__ __device__ inline int tc_groups(int N) { return (N + 15) / 16 * 16 <= 32 ? 2 : 1; }
 
-__host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
+// CL > 1: one CTA of a CL-CTA cluster (MT = 1 local tile, Kp the whole channel's K extent).
+__host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C, int CL = 1)
 {
     TcLayout L{};
     uint32_t o = 0;
@@ -96,14 +97,19 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C)
     L.red = take(4u * C * 4, 16);
     L.dred = take(4u * C * 4, 16);
     L.acc = take((uint32_t)C * 4, 16);
-    L.ref = take((uint32_t)C * 8, 16);       // FP64 refresh results per chain
+    L.ref = take((uint32_t)C * 16, 16);      // FP64 refresh results per chain
     L.fst = take((uint32_t)C * 16, 16);      // tracked and best energies per chain
     L.cnt = take((uint32_t)C * 4, 16);       // accepted moves per chain
-    L.fref = take((uint32_t)C * kMaxN, 16);  // states for the FP64 refresh
-    L.kb = take((uint32_t)C * kMaxN, 16);    // best visited state of every chain
+    // states for the FP64 refresh (a cluster CTA reads them from its B operand instead) and the
+    // best visited state of every chain (a cluster CTA: its own 64 dimensions)
+    L.fref = take(CL > 1 ? 0u : (uint32_t)C * kMaxN, 16);
+    L.kb = take((uint32_t)C * (CL > 1 ? 64u : (uint32_t)kMaxN), 16);
     // streamed kernels: Gt x of every thread's (tile, chain pair), [2 MT][threads] packed pairs
     L.dg = take(tc_streamed(MT) ? (uint32_t)(2 * MT) * (16u * C) * 8u : 0u, 16);
-    L.bar = take(6 * 8, 8);                  // TMA, MMA, streamed chunks full[2] / empty[2]
+    // cluster exchange slots: [2 alternating buffers][CL ranks][C chains] x 16 bytes
+    L.xs = take(CL > 1 ? 2u * (uint32_t)CL * (uint32_t)C * 16u : 0u, 16);
+    // TMA, MMA, streamed chunks full[2] / empty[2], cluster B slices and exchange
+    L.bar = take(8 * 8, 8);
     L.tmem = take(4, 4);
     L.total = (o + 127) / 128 * 128;
     return L;
@@ -143,8 +149,136 @@ struct TcCtx {
     uint32_t bar_full[2], bar_empty[2];
     uint32_t full_phase[2], empty_phase[2];
     bool pend[2];                 // a chunk copy into buffer b is requested and not yet waited for
-    bool fail;                    // a streamed wait ran out
+    bool fail;                    // a streamed wait (or a cluster B-slice wait) ran out
+    // cluster kernels: this CTA's rank (its 128-row tile and 64 dimensions), the barrier that
+    // counts the other CTAs' slices of the B operand, the one that counts exchange arrivals,
+    // their phases, and the exchange slots (two alternating buffers)
+    int rank;
+    uint32_t bar_b, bar_x, b_phase, x_phase, x_buf;
+    unsigned char *sx;
 };
+
+// ------------------------------------------------------------------------------------------
+// Thread-block clusters (N > 128): CTA r of a cluster of CL keeps tile r of the A operand
+// resident and owns dimensions 64r .. 64r + 63 of every chain of the work item. Per transition
+//   - each CTA writes its part of x' into its own B operand and sends that slice (its K groups,
+//     for every 8-chain group) to the other CTAs by bulk shared::cta -> shared::cluster copies
+//     that complete on their B-slice barrier; the MMA waits for the other slices;
+//   - per-chain partial sums (log q and energy terms) are exchanged through distributed shared
+//     memory: every CTA stores its partials into a slot of every CTA and arrives on that CTA's
+//     exchange barrier, so each CTA sums the same values in the same (rank) order and takes the
+//     same MH decisions.
+// The exchanges alternate with the B-slice transfers (every CTA joins an exchange only after its
+// MMA consumed the previous slices), which orders every write into another CTA's shared memory
+// after that CTA's last read of the same bytes.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cl_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_count()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_map(uint32_t addr, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Bounded wait with cluster-scope acquire (the exchange barrier's arrivals come from other CTAs).
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// K groups (8 dimensions) of the B operand that CTA r of the cluster writes.
+__device__ __forceinline__ int cl_kg0(int r) { return 8 * r; }
+__device__ __forceinline__ int cl_kg1(int r, int Kp) { return min(8 * r + 8, Kp / 8); }
+
+// Thread 0: arm this CTA's B-slice barrier for the other CTAs' slices and send this CTA's slice
+// (for every 8-chain group: its K groups, contiguous at a 144-byte K stride) to every other CTA.
+template <int CL>
+__device__ __forceinline__ void cl_send_b(const TcCtx &x)
+{
+    const uint32_t groups = (uint32_t)x.C / 8u;
+    uint32_t expect = 0;
+#pragma unroll
+    for (int r = 0; r < CL; ++r)
+        if (r != x.rank) expect += (uint32_t)(cl_kg1(r, x.Kp) - cl_kg0(r)) * b_lbo() * groups;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(x.bar_b), "r"(expect)
+                 : "memory");
+    const uint32_t bytes = (uint32_t)(cl_kg1(x.rank, x.Kp) - cl_kg0(x.rank)) * b_lbo();
+    const uint32_t base = smem_u32(x.sB) + (uint32_t)cl_kg0(x.rank) * b_lbo();
+#pragma unroll
+    for (int r = 0; r < CL; ++r) {
+        if (r == x.rank) continue;
+        const uint32_t bar = cl_map(x.bar_b, r);
+        for (uint32_t g = 0; g < groups; ++g) {
+            const uint32_t src = base + g * x.sbo_b;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], "
+                "%2, [%3];" ::"r"(cl_map(src, r)),
+                "r"(src), "r"(bytes), "r"(bar)
+                : "memory");
+        }
+    }
+}
+
+// Threads 0 .. C-1 (chain c): publish 16 bytes into slot [buffer][this rank][c] of every CTA of
+// the cluster and wait (bounded) until every CTA has published. The caller reads the CL slots of
+// chain c with cl_slot() and then calls cl_next() (all threads).
+template <int CL>
+__device__ __forceinline__ bool cl_exchange(const TcCtx &x, int c, uint4 v)
+{
+    const uint32_t slot =
+        smem_u32(x.sx) + (uint32_t)(((x.x_buf * CL + x.rank) * x.C + c) * 16);
+#pragma unroll
+    for (int r = 0; r < CL; ++r) {
+        asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(cl_map(slot, r)),
+                     "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                     : "memory");
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                         cl_map(x.bar_x, r))
+                     : "memory");
+    }
+    return mbar_wait_cl(x.bar_x, x.x_phase);
+}
+__device__ __forceinline__ uint4 cl_slot(const TcCtx &x, int CL, int r, int c)
+{
+    return reinterpret_cast<const uint4 *>(x.sx)[(x.x_buf * CL + r) * x.C + c];
+}
+__device__ __forceinline__ void cl_next(TcCtx &x)
+{
+    x.x_phase ^= 1u;
+    x.x_buf ^= 1u;
+}
 
 // Issue the MMAs of one transition (thread 0, after a CTA barrier that publishes the B operand)
 // and, separately, wait for them (everyone). The wait returns false on a bounded-wait expiry of
@@ -233,7 +367,7 @@ __device__ __forceinline__ bool tc_stream_drain(TcCtx &x)
     return ok;
 }
 
-template <int MT>
+template <int MT, int CL = 1>
 __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -248,8 +382,14 @@ __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
     }
     if (x.tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool go = true;
+        if constexpr (CL > 1) {
+            // the other CTAs' slices of x' complete on the B-slice barrier
+            cl_send_b<CL>(x);
+            if (!mbar_wait(x.bar_b, x.b_phase)) { x.fail = true; go = false; }
+        }
         const uint32_t a0 = smem_u32(x.sA), b0 = smem_u32(x.sB);
-        for (int t = 0; t < MT; ++t) {
+        for (int t = 0; t < MT && go; ++t) {
             uint32_t first = 1;
             for (int s = 0; s < x.S; ++s) {
                 const uint32_t ab = a0 + (uint32_t)((s * MT + t) * 128 * x.Kp * 2);
@@ -266,15 +406,18 @@ __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
                 x.bar_mma)
             : "memory");
     }
+    if constexpr (CL > 1) x.b_phase ^= 1u;   // every thread tracks the B-slice phase
 }
 
 // prefetch_next: another transition of the same work item follows (streamed operand only).
-template <int MT>
+// In a cluster, thread 0's verdict includes its wait for the other CTAs' B slices.
+template <int MT, int CL = 1>
 __device__ __forceinline__ bool tc_gemm_wait(TcCtx &x, bool prefetch_next)
 {
     const bool ok = mbar_wait(x.bar_mma, x.mma_phase);
     x.mma_phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if constexpr (CL > 1) return ok && !(x.tid == 0 && x.fail);
     if constexpr (tc_streamed(MT)) {
         if (x.tid == 0) {
             if (ok && prefetch_next) tc_stream_prefetch<MT>(x);
@@ -360,7 +503,7 @@ __device__ __forceinline__ void table_load(uint32_t ta, uint32_t te, Table2<L> &
 // One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
 // every chain column is live, so no per-(dimension, chain) validity test is needed. Levels are
 // held as exact small floats.
-template <int MT, int L, bool FULL, int G>
+template <int MT, int L, bool FULL, int G, int CL>
 __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const ChannelDesc &d,
                         bool &alive)
 {
@@ -372,6 +515,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     const float cf2 = (float)d.cf * kLog2e;       // df_tau -> log2 units
     const float lm1 = (float)(L - 1);
     static_assert(G == 1 || (G == 2 && MT == 1), "two chain groups only for one tile");
+    static_assert(CL == 1 || (MT == 1 && G == 1), "a cluster CTA holds one tile of one group");
     const int Cq = C / G;                                  // chains per group
     const int gofs = G == 1 ? 0 : (x.q >> 1) * Cq;         // this thread's group's first chain
     const int cbase = gofs + 8 * x.cgi + 4 * x.h;          // first of its 4 chains (CTA-local)
@@ -392,7 +536,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     uint64_t k2[MT][2], sl2[MT][2];
     // Gt x of the current states: registers, or shared memory for more than two tiles
     constexpr bool kDgSmem = tc_streamed(MT);
-    uint64_t Dg2r[kDgSmem ? 1 : MT][2];
+    uint64_t Dg2r[kDgSmem ? 1 : MT][2] = {};
     auto dg_get = [&](int t, int p) -> uint64_t {
         if constexpr (kDgSmem) return x.sdg[(2 * t + p) * x.nthr + x.tid];
         else return Dg2r[t][p];
@@ -401,13 +545,14 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         if constexpr (kDgSmem) x.sdg[(2 * t + p) * x.nthr + x.tid] = v;
         else Dg2r[t][p] = v;
     };
-    int8_t *skb = x.skb;                           // best visited states [C][kMaxN]
+    int8_t *skb = x.skb;   // best visited states [C][kMaxN] (cluster CTAs: [C][64], own dimensions)
+    auto kbi = [&](int c, int n) { return CL > 1 ? c * 64 + (n & 63) : c * kMaxN + n; };
     const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
     const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
     uint32_t boff[MT];                             // byte offset of this thread's B element, chain cbase
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
-        const int n = 64 * t + 16 * (G == 1 ? x.q : (x.q & 1)) + x.dl;
+        const int n = 64 * (CL > 1 ? x.rank : t) + 16 * (G == 1 ? x.q : (x.q & 1)) + x.dl;
         nd[t] = n;
         const bool v = FULL || n < N;
         zt[t] = v ? gz[n] : 0.f;
@@ -423,7 +568,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             if (live[t][j]) {
                 const long long e = d.state_off + (long long)(it.c0 + c) * N + n;
                 kv[j] = (float)A.states[e];
-                skb[c * kMaxN + n] = A.best_states[e];
+                skb[kbi(c, n)] = A.best_states[e];
             }
         }
         k2[t][0] = f2_pack(kv[0], kv[1]);
@@ -470,11 +615,20 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     auto slope2 = [&](int t, uint64_t g, uint64_t m) {
         return f2_mul(f2_splat(a2s), f2_fma(mone, pre ? m : g, f2_splat(pre ? wt[t] : zt[t])));
     };
+    // x (BF16 bits of an odd level) of chain c, dimension n, from the B operand
+    auto b_level = [&](int c, int n) -> float {
+        const unsigned short bits = *reinterpret_cast<const unsigned short *>(
+            x.sB + (uint32_t)(c >> 3) * x.sbo_b + (uint32_t)(n >> 3) * b_lbo() + (uint32_t)(c & 7) * 16u +
+            (uint32_t)(n & 7) * 2u);
+        return __uint_as_float((uint32_t)bits << 16);
+    };
     write_b(k2);
+    bool lf0 = false;   // cluster: a failed first MMA wait, reported through the first exchange
     if (alive) {
-        tc_gemm_issue<MT>(x);
-        const bool ok = tc_gemm_wait<MT>(x, A.iterations > 0);
-        if (__syncthreads_or(!ok)) { alive = false; set_status(A.status, kStatusTimeout); }
+        tc_gemm_issue<MT, CL>(x);
+        const bool ok = tc_gemm_wait<MT, CL>(x, A.iterations > 0);
+        if constexpr (CL > 1) lf0 = __syncthreads_or(!ok);
+        else if (__syncthreads_or(!ok)) { alive = false; set_status(A.status, kStatusTimeout); }
     }
     {
         float g[MT][4], m[MT][4];
@@ -489,9 +643,9 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 sl2[t][p] = alive ? slope2(t, gg, mm) : 0ull;
             }
     }
-    if (A.init_f && alive) {
-        // tracked energies of the current states from the tensor-core Gt x; the running best
-        // restarts from them
+    // tracked energies of the current states from the tensor-core Gt x; the running best
+    // restarts from them. Per-quadrant partial sums of chain c go to red / dred.
+    auto init_partials = [&]() {
         float lin[4], quad[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) { lin[j] = 0.f; quad[j] = 0.f; }
@@ -508,7 +662,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 const float xn = fmaf(2.f, kv[j], -lm1);
                 lin[j] = fmaf(xn, zt[t], lin[j]);
                 quad[j] = fmaf(xn, dg[j], quad[j]);
-                skb[(cbase + j) * kMaxN + nd[t]] = (int8_t)kv[j];
+                skb[kbi(cbase + j, nd[t])] = (int8_t)kv[j];
             }
         }
         const float rl = reduce_scatter16(lin, x.dl);
@@ -518,6 +672,38 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             x.red[x.q * Cq + c - gofs] = rl;
             x.dred[x.q * Cq + c - gofs] = rq;
         }
+    };
+    if constexpr (CL > 1) {
+        // the first exchange always runs: it carries the energies' partial sums (or zeros) and the
+        // first MMA's verdict, and it separates this work item's first B-slice transfer from the next
+        if (A.init_f) init_partials();
+        __syncthreads();
+        bool xf = false;
+        if (x.tid < C) {
+            const int c = x.tid;
+            const float l = A.init_f ? quad_sum(x.red, c) : 0.f;
+            const float qd = A.init_f ? quad_sum(x.dred, c) : 0.f;
+            xf = !cl_exchange<CL>(x, c, make_uint4(__float_as_uint(l), __float_as_uint(qd), lf0 ? 1u : 0u, 0u));
+            if (!xf) {
+                float sl = 0.f, sq = 0.f;
+#pragma unroll
+                for (int r = 0; r < CL; ++r) {
+                    const uint4 v = cl_slot(x, CL, r, c);
+                    sl += __uint_as_float(v.x);
+                    sq += __uint_as_float(v.y);
+                    xf |= v.z != 0u;
+                }
+                if (A.init_f && c < nC) {
+                    const double f0 = -(A.yy[it.b] - 2.0 * (double)sl + (double)sq) * d.inv_s2;
+                    x.sfc[c] = f0;
+                    x.sfb[c] = f0;
+                }
+            }
+        }
+        cl_next(x);
+        if (__syncthreads_or(xf)) { alive = false; set_status(A.status, kStatusTimeout); }
+    } else if (A.init_f && alive) {
+        init_partials();
         __syncthreads();
         if (x.tid < nC) {
             const int c = x.tid;
@@ -575,7 +761,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         write_b(kp2);
         // 2. D' = A X'^T on the tensor core; while it runs, the chains' acceptance uniforms
         //    (the timeout verdict joins the next CTA barrier)
-        tc_gemm_issue<MT>(x);
+        tc_gemm_issue<MT, CL>(x);
         float logu = 0.f;
         if (x.tid < nC) {
             const int cc = it.c0 + x.tid;
@@ -583,7 +769,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                                           A.philox_rk);
             logu = lg2_approx(uniform_f(word_of(w, cc & 3)));
         }
-        const bool mma_ok = tc_gemm_wait<MT>(x, i + 1 < A.iterations);
+        const bool mma_ok = tc_gemm_wait<MT, CL>(x, i + 1 < A.iterations);
         // 3. reverse factor and energy difference (with more than two tiles, the products and
         //    levels of x' are not kept in registers: the update reads them again)
         constexpr bool kReread = tc_streamed(MT);
@@ -635,11 +821,8 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             x.dred[x.q * Cq + c - gofs] = rd;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!mma_ok)) { alive = false; set_status(A.status, kStatusTimeout); break; }
-        if (x.tid < nC) {
-            const int c = x.tid;
-            const float s = quad_sum(x.red, c);
-            const float sd = quad_sum(x.dred, c);
+        // MH decision of chain c (thread c) from its summed log q terms s and energy terms sd
+        auto decide = [&](int c, float s, float sd) {
             const float logr = fmaf(cf2, sd, s);
             const float loga = logr < 0.f ? logr : 0.f;
             int ok = logu < loga;
@@ -652,8 +835,36 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 if (fc > x.sfb[c]) { x.sfb[c] = fc; im = 1; }
             }
             x.sacc[c] = ok | (im << 1);
+        };
+        if constexpr (CL == 1) {
+            if (__syncthreads_or(!mma_ok)) { alive = false; set_status(A.status, kStatusTimeout); break; }
+            if (x.tid < nC) decide(x.tid, quad_sum(x.red, x.tid), quad_sum(x.dred, x.tid));
+            __syncthreads();
+        } else {
+            // the CTA's partial sums (its 64 dimensions) to every CTA of the cluster; every CTA
+            // adds the CL partials in rank order and takes the same decisions
+            const bool lf = __syncthreads_or(!mma_ok);
+            bool xf = false;
+            if (x.tid < C) {
+                const int c = x.tid;
+                xf = !cl_exchange<CL>(x, c,
+                                      make_uint4(__float_as_uint(quad_sum(x.red, c)),
+                                                 __float_as_uint(quad_sum(x.dred, c)), lf ? 1u : 0u, 0u));
+                if (!xf) {
+                    float ss = 0.f, sd = 0.f;
+#pragma unroll
+                    for (int r = 0; r < CL; ++r) {
+                        const uint4 v = cl_slot(x, CL, r, c);
+                        ss += __uint_as_float(v.x);
+                        sd += __uint_as_float(v.y);
+                        xf |= v.z != 0u;
+                    }
+                    if (!xf && c < nC) decide(c, ss, sd);
+                }
+            }
+            cl_next(x);
+            if (__syncthreads_or(xf)) { alive = false; set_status(A.status, kStatusTimeout); break; }
         }
-        __syncthreads();
         // 5. accepted chains take x' and its caches
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
@@ -680,7 +891,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                     ka[h] = ok ? kb[h] : ka[h];
                     da[h] = ok ? db[h] : da[h];
                     sa[h] = ok ? sb[h] : sa[h];
-                    if (im && live[t][2 * p + h]) skb[(cbase + 2 * p + h) * kMaxN + nd[t]] = (int8_t)kb[h];
+                    if (im && live[t][2 * p + h]) skb[kbi(cbase + 2 * p + h, nd[t])] = (int8_t)kb[h];
                 }
                 k2[t][p] = f2_pack(ka[0], ka[1]);
                 dg_set(t, p, f2_pack(da[0], da[1]));
@@ -721,7 +932,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                             ka[h] = kb;
                             da[h] = g[j];
                             sa[h] = sb[h];
-                            if ((fl[j] & 2) && live[t][j]) skb[(cbase + j) * kMaxN + nd[t]] = (int8_t)kb;
+                            if ((fl[j] & 2) && live[t][j]) skb[kbi(cbase + j, nd[t])] = (int8_t)kb;
                         }
                         k2[t][p] = f2_pack(ka[0], ka[1]);
                         dg_set(t, p, f2_pack(da[0], da[1]));
@@ -731,7 +942,60 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             }
         }
         // periodic FP64 refresh of the tracked energies (decisions never read them)
-        if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
+        if constexpr (CL > 1) {
+            if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
+                // every CTA needs the whole state: x goes through the B operand's slice transfer,
+                // then each CTA evaluates its share of the upper-triangle row pairs in FP64 and the
+                // partial sums are exchanged (and added in rank order, identically in every CTA)
+                write_b(k2);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (x.tid == 0) cl_send_b<CL>(x);
+                const bool okb = mbar_wait(x.bar_b, x.b_phase);
+                x.b_phase ^= 1u;
+                const double *Gm = A.G64 + d.mat_off;
+                const double *z = A.z64 + d.vec_off;
+                for (int c = x.warp; c < nC; c += blockDim.x >> 5) {
+                    double quad, lin;
+                    quad_lin_fp64_part(Gm, z, N, x.rank + CL * x.lane, 32 * CL,
+                                       [&](int n) { return (double)b_level(c, n); }, quad, lin);
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) {
+                        quad += __shfl_xor_sync(0xffffffffu, quad, o);
+                        lin += __shfl_xor_sync(0xffffffffu, lin, o);
+                    }
+                    if (x.lane == 0) {
+                        x.sref[2 * c] = quad;
+                        x.sref[2 * c + 1] = lin;
+                    }
+                }
+                bool xf = __syncthreads_or(!okb);
+                if (x.tid < C) {
+                    const int c = x.tid;
+                    const double q = c < nC ? x.sref[2 * c] : 0.0, l = c < nC ? x.sref[2 * c + 1] : 0.0;
+                    const unsigned long long qb = (unsigned long long)__double_as_longlong(q);
+                    const unsigned long long lb = (unsigned long long)__double_as_longlong(l);
+                    const bool okx = cl_exchange<CL>(
+                        x, c, make_uint4((uint32_t)qb, (uint32_t)(qb >> 32), (uint32_t)lb, (uint32_t)(lb >> 32)));
+                    xf |= !okx;
+                    if (okx && c < nC) {
+                        double sq = 0.0, sl = 0.0;
+#pragma unroll
+                        for (int r = 0; r < CL; ++r) {
+                            const uint4 v = cl_slot(x, CL, r, c);
+                            sq += __longlong_as_double((long long)(((unsigned long long)v.y << 32) | v.x));
+                            sl += __longlong_as_double((long long)(((unsigned long long)v.w << 32) | v.z));
+                        }
+                        const double fr = -(A.yy[it.b] - 2.0 * sl + sq) * d.inv_s2;
+                        if (x.rank == 0)
+                            atomicMax(A.drift_bits, (unsigned long long)__double_as_longlong(fabs(fr - x.sfc[c])));
+                        x.sfc[c] = fr;
+                    }
+                }
+                cl_next(x);
+                if (__syncthreads_or(xf)) { alive = false; set_status(A.status, kStatusTimeout); break; }
+            }
+        } else if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
 #pragma unroll
             for (int t = 0; t < MT; ++t) {
                 float kv[4];
@@ -742,11 +1006,11 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                     if (live[t][j]) x.sfs[(cbase + j) * kMaxN + nd[t]] = (int8_t)kv[j];
             }
             __syncthreads();
-            const double *G = A.G64 + d.mat_off;
+            const double *Gm = A.G64 + d.mat_off;
             const double *z = A.z64 + d.vec_off;
             for (int c = x.warp; c < nC; c += blockDim.x >> 5) {
                 double quad, lin;
-                quad_lin_fp64(G, z, N, x.lane,
+                quad_lin_fp64(Gm, z, N, x.lane,
                               [&](int n) { return (double)odd_of(x.sfs[c * kMaxN + n], L); }, quad, lin);
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
@@ -776,11 +1040,11 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             if (!live[t][j]) continue;
             const long long e = d.state_off + (long long)(it.c0 + cbase + j) * N + nd[t];
             A.states[e] = (int8_t)kv[j];
-            A.best_states[e] = skb[(cbase + j) * kMaxN + nd[t]];
+            A.best_states[e] = skb[kbi(cbase + j, nd[t])];
             if (A.dexp) A.dexp[e] = dg[j];
         }
     }
-    if (x.tid < nC) {
+    if (x.tid < nC && (CL == 1 || x.rank == 0)) {
         const long long ci = (long long)it.b * A.chains + it.c0 + x.tid;
         A.f[ci] = x.sfc[x.tid];
         A.best_f[ci] = x.sfb[x.tid];
@@ -788,21 +1052,22 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     }
 }
 
-template <int MT, int L, int G>
+template <int MT, int L, int G, int CL>
 __device__ __forceinline__ void tc_item_dispatch(const ChainArgs &A, TcCtx &x, const WorkItem &it,
                                                  const ChannelDesc &d, bool &alive)
 {
-    if (d.N == 64 * MT / G && it.nc == x.C) tc_item<MT, L, true, G>(A, x, it, d, alive);
-    else tc_item<MT, L, false, G>(A, x, it, d, alive);
+    if (d.N == 64 * MT * CL / G && it.nc == x.C) tc_item<MT, L, true, G, CL>(A, x, it, d, alive);
+    else tc_item<MT, L, false, G, CL>(A, x, it, d, alive);
 }
 
 // G: chain groups per CTA (2 for N <= 32, one tile); C: chains per CTA over all groups.
-template <int MT, int G>
-__global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
+// CL > 1: one CTA of a cluster of CL (MT = 1 local tile of a channel with CL tiles).
+template <int MT, int G, int CL>
+__global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL == 1 ? TC_MIN_BLOCKS : 1)
     chains_tc_kernel(const ChainArgs A, const int C, const int S, const int Kp)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const TcLayout lay = tc_layout(S, MT, Kp, C);
+    const TcLayout lay = tc_layout(S, MT, Kp, C, CL);
     TcCtx x;
     x.sA = smem + lay.a;
     x.sB = smem + lay.b;
@@ -846,6 +1111,13 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
         x.pend[b] = false;
     }
     x.fail = false;
+    x.rank = CL > 1 ? (int)cl_rank() : 0;
+    x.bar_b = smem_u32(&bars[6]);
+    x.bar_x = smem_u32(&bars[7]);
+    x.b_phase = 0;
+    x.x_phase = 0;
+    x.x_buf = 0;
+    x.sx = smem + lay.xs;
     const int ncols_alloc = A.tc_tmem_cols;   // TMEM columns to allocate (power of 2, >= 32)
 
     if (x.tid == 0) {
@@ -855,6 +1127,8 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
             mbar_init(x.bar_full[b], 1);
             mbar_init(x.bar_empty[b], 1);
         }
+        mbar_init(x.bar_b, 1);
+        mbar_init(x.bar_x, (uint32_t)(CL * C));   // every CTA's C exchanging threads
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (x.warp == 0) {
@@ -872,17 +1146,21 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
         reinterpret_cast<uint4 *>(x.sB)[e] = make_uint4(0, 0, 0, 0);
     uint32_t tma_phase = 0;
     bool alive = true;
+    // a cluster's CTAs start exchanging only once every CTA's barriers and B operand are set up
+    if constexpr (CL > 1) cl_sync();
+    const int item0 = CL > 1 ? (int)cl_id() : (int)blockIdx.x;
+    const int istep = CL > 1 ? (int)cl_count() : (int)gridDim.x;
 
-    for (int item = blockIdx.x; item < A.n_items && alive; item += gridDim.x) {
+    for (int item = item0; item < A.n_items && alive; item += istep) {
         const WorkItem it = A.items[item];
         const ChannelDesc d = A.desc[it.b];
         x.asrc = A.tc_ops + d.tc_off;
         if constexpr (tc_streamed(MT)) {
             // chunks are streamed by the transitions themselves
             switch (d.L) {
-            case 2: tc_item_dispatch<MT, 2, G>(A, x, it, d, alive); break;
-            case 4: tc_item_dispatch<MT, 4, G>(A, x, it, d, alive); break;
-            default: tc_item_dispatch<MT, 8, G>(A, x, it, d, alive); break;
+            case 2: tc_item_dispatch<MT, 2, G, CL>(A, x, it, d, alive); break;
+            case 4: tc_item_dispatch<MT, 4, G, CL>(A, x, it, d, alive); break;
+            default: tc_item_dispatch<MT, 8, G, CL>(A, x, it, d, alive); break;
             }
             const bool drained = x.tid != 0 || tc_stream_drain(x);
             if (__syncthreads_or(!drained || (x.tid == 0 && x.fail)) && alive) {
@@ -893,21 +1171,28 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
             __syncthreads();
             continue;
         }
-        // stage this channel's A operand (TMA bulk copy, mbarrier completion)
+        // stage this channel's A operand (TMA bulk copy, mbarrier completion); a cluster CTA
+        // stages the S terms of its own tile (rank) of the channel's CL tiles
         const uint32_t abytes = (uint32_t)S * MT * 128u * (uint32_t)Kp * 2u;
         if (x.tid == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_tma),
                          "r"(abytes)
                          : "memory");
-            const unsigned char *src = A.tc_ops + d.tc_off;
+            const uint32_t tbytes = 128u * (uint32_t)Kp * 2u;
             const uint32_t chunk = 1u << 16;
-            for (uint32_t off = 0; off < abytes; off += chunk) {
-                const uint32_t n = abytes - off < chunk ? abytes - off : chunk;
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
-                    "%2, [%3];" ::"r"(smem_u32(x.sA) + off),
-                    "l"(src + off), "r"(n), "r"(bar_tma)
-                    : "memory");
+            for (int sc = 0; sc < (CL > 1 ? S : 1); ++sc) {
+                const unsigned char *src =
+                    A.tc_ops + d.tc_off + (CL > 1 ? (size_t)(sc * CL + x.rank) * tbytes : 0);
+                const uint32_t dst = smem_u32(x.sA) + (CL > 1 ? (uint32_t)sc * tbytes : 0u);
+                const uint32_t nb = CL > 1 ? tbytes : abytes;
+                for (uint32_t off = 0; off < nb; off += chunk) {
+                    const uint32_t n = nb - off < chunk ? nb - off : chunk;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
+                        "%2, [%3];" ::"r"(dst + off),
+                        "l"(src + off), "r"(n), "r"(bar_tma)
+                        : "memory");
+                }
             }
         }
         if (__syncthreads_or(!mbar_wait(bar_tma, tma_phase))) {
@@ -917,13 +1202,15 @@ __global__ void __launch_bounds__(TC_MAX_THREADS, MT == 1 ? TC_MIN_BLOCKS : 1)
         tma_phase ^= 1u;
         if (!alive) break;
         switch (d.L) {
-        case 2: tc_item_dispatch<MT, 2, G>(A, x, it, d, alive); break;
-        case 4: tc_item_dispatch<MT, 4, G>(A, x, it, d, alive); break;
-        default: tc_item_dispatch<MT, 8, G>(A, x, it, d, alive); break;
+        case 2: tc_item_dispatch<MT, 2, G, CL>(A, x, it, d, alive); break;
+        case 4: tc_item_dispatch<MT, 4, G, CL>(A, x, it, d, alive); break;
+        default: tc_item_dispatch<MT, 8, G, CL>(A, x, it, d, alive); break;
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
+    // no CTA leaves while another may still store into its shared memory
+    if constexpr (CL > 1) cl_sync();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (x.warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(x.tmem),
@@ -985,10 +1272,66 @@ int pow2_at_least(int v)
 
 }  // namespace
 
-bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, TcPlan *plan)
+namespace {
+
+using TcKernel = void (*)(const ChainArgs, const int, const int, const int);
+
+TcKernel cluster_kernel(int CL) { return CL == 3 ? chains_tc_kernel<1, 1, 3> : chains_tc_kernel<1, 1, 4>; }
+
+// Clusters of CL CTAs (smem bytes, threads each) that can be resident at once; 0 if none.
+int cluster_capacity(int CL, size_t smem, int threads)
+{
+    const TcKernel k = cluster_kernel(CL);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)CL, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+}  // namespace
+
+bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, bool allow_cluster,
+                  TcPlan *plan)
 {
     *plan = TcPlan{};
     if (max_n < 1 || max_n > kMaxN) return false;
+    if (max_n > 128 && allow_cluster) {
+        // three or four tiles: a cluster with one resident tile per CTA, where it fits
+        const int CL = (max_n + 63) / 64, Kp = (max_n + 15) / 16 * 16, C = chains_per_cta;
+        if (C == 16 || C == 32 || C == 64) {
+            const TcLayout L = tc_layout(split_terms, 1, Kp, C, CL);
+            if (L.total <= smem_optin && cluster_capacity(CL, L.total, 16 * C) > 0) {
+                plan->valid = 1;
+                plan->chains_per_cta = C;
+                plan->groups = 1;
+                plan->m_tiles = CL;
+                plan->kdim = Kp;
+                plan->max_n = max_n;
+                plan->split_terms = split_terms;
+                plan->threads = 16 * C;
+                plan->tmem_cols = pow2_at_least(C + tc_table_cols(1, C));
+                plan->ctas_per_sm = 1;
+                plan->smem = L.total;
+                plan->cluster = CL;
+                return true;
+            }
+        }
+    }
     if (chains_per_cta < 16 || chains_per_cta > 32 || chains_per_cta % 16) return false;
     if (16 * chains_per_cta > TC_MAX_THREADS) return false;
     const int MT = (max_n + 63) / 64;
@@ -1017,6 +1360,7 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
     const int by_tmem = 512 / plan->tmem_cols;
     plan->ctas_per_sm = std::max(1, std::min(by_occ, by_tmem));
     plan->smem = L.total;
+    plan->cluster = 1;
     return true;
 }
 
@@ -1044,8 +1388,28 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::min(a.n_items, std::max(1, sms * plan.ctas_per_sm));
     cudaError_t e;
+    if (plan.cluster > 1) {
+        const int CL = plan.cluster;
+        const int ncl = cluster_capacity(CL, plan.smem, plan.threads);
+        if (ncl <= 0) return cudaErrorInvalidConfiguration;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(CL * std::min(a.n_items, ncl)), 1, 1);
+        cfg.blockDim = dim3((unsigned)plan.threads, 1, 1);
+        cfg.dynamicSmemBytes = plan.smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)CL;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, cluster_kernel(CL), a, plan.chains_per_cta, plan.split_terms, plan.kdim);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
+    const int grid = std::min(a.n_items, std::max(1, sms * plan.ctas_per_sm));
     auto go = [&](auto k) {
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem)) != cudaSuccess)
             return e;
@@ -1053,10 +1417,10 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
         return cudaSuccess;
     };
     switch (plan.m_tiles) {
-    case 1: e = plan.groups == 2 ? go(chains_tc_kernel<1, 2>) : go(chains_tc_kernel<1, 1>); break;
-    case 2: e = go(chains_tc_kernel<2, 1>); break;
-    case 3: e = go(chains_tc_kernel<3, 1>); break;
-    default: e = go(chains_tc_kernel<4, 1>); break;
+    case 1: e = plan.groups == 2 ? go(chains_tc_kernel<1, 2, 1>) : go(chains_tc_kernel<1, 1, 1>); break;
+    case 2: e = go(chains_tc_kernel<2, 1, 1>); break;
+    case 3: e = go(chains_tc_kernel<3, 1, 1>); break;
+    default: e = go(chains_tc_kernel<4, 1, 1>); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -142,17 +142,18 @@ __device__ __forceinline__ void set_status(unsigned *status, unsigned bit)
     atomicOr(status, bit);
 }
 
-// FP64 x^T G x and x^T z for one state (G symmetric N x N), this lane's share of a warp's work:
-// the lane takes row pairs (r, N - 1 - r), each row contributing x_n (G_nn x_n + 2 sum_{m>n}
-// G_nm x_m), so every lane does N - 1 products per pair, half of the full N^2. level(n) returns
-// the odd-integer value of dimension n. The caller sums quad and lin over the warp.
+// FP64 x^T G x and x^T z for one state (G symmetric N x N), one share of the work: the row pairs
+// (r, N - 1 - r) for r = first, first + stride, ..., each row contributing
+// x_n (G_nn x_n + 2 sum_{m>n} G_nm x_m), so every pair costs N - 1 products (half of the full N^2
+// over all pairs). level(n) returns the odd-integer value of dimension n. The caller sums quad
+// and lin over the shares.
 template <typename Level>
-__device__ __forceinline__ void quad_lin_fp64(const double *G, const double *z, int N, int lane,
-                                              Level level, double &quad, double &lin)
+__device__ __forceinline__ void quad_lin_fp64_part(const double *G, const double *z, int N, int first,
+                                                   int stride, Level level, double &quad, double &lin)
 {
     quad = 0.0;
     lin = 0.0;
-    for (int r = lane; r < (N + 1) / 2; r += 32) {
+    for (int r = first; r < (N + 1) / 2; r += stride) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int n = h ? N - 1 - r : r;
@@ -165,6 +166,13 @@ __device__ __forceinline__ void quad_lin_fp64(const double *G, const double *z, 
             lin = fma(xn, z[n], lin);
         }
     }
+}
+// A lane's share of a warp's work (row pairs r = lane, lane + 32, ...).
+template <typename Level>
+__device__ __forceinline__ void quad_lin_fp64(const double *G, const double *z, int N, int lane,
+                                              Level level, double &quad, double &lin)
+{
+    quad_lin_fp64_part(G, z, N, lane, 32, level, quad, lin);
 }
 
 }  // namespace mcmcdet

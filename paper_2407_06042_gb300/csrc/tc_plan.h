@@ -20,12 +20,17 @@ struct TcPlan {
     int tmem_cols;
     int ctas_per_sm;
     size_t smem;            // dynamic shared memory per CTA (bytes)
+    int cluster;            // CTAs per thread-block cluster: m_tiles for N > 128 (one resident
+                            // tile per CTA, chains_per_cta 16, 32 or 64), else 1
 };
 
 // Kernel shape for a group of channels with the same K extent (N rounded up to 16) and tile
 // count, `chains_per_cta` chains (multiple of 16) per group of threads (twice that per CTA and
-// work item when N <= 32); false if it does not fit.
-bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, TcPlan *plan);
+// work item when N <= 32); false if it does not fit. N > 128 takes a thread-block cluster of
+// one CTA per tile where allowed, its shared memory fits and such clusters can be resident (then
+// 64 chains per CTA are allowed too), else the single-CTA kernel that streams the operand from L2.
+bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, bool allow_cluster,
+                  TcPlan *plan);
 
 // Bytes of one channel's packed BF16 operand block (depends on its N only).
 long long tc_operand_bytes(int N, int split_terms);

@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 TC = 2            # MCMC_ENGINE_TC: these tests pin the tensor-core kernel itself
 GRAPH = 4         # MCMC_ENGINE_GRAPH
+NO_CLUSTER = 8    # MCMC_ENGINE_NO_CLUSTER: N > 128 on the single-CTA kernel (operand streamed)
 
 
 def _small(n=16, snr=12.0, seed=1001):
@@ -33,15 +34,18 @@ def test_mixed_step_parity(terms, w_cat, w_acc):
     det.destroy()
 
 
-def test_mixed_one_launch_equals_single_step_launches():
-    b = _small(6)
+@pytest.mark.parametrize("big", [False, True])
+def test_mixed_one_launch_equals_single_step_launches(big):
+    # big: N = 200 on four-CTA clusters, whose decisions come from exchanged partial sums
+    b = workload.generate([(100, 100, 16, 20.0)] * 2, 97) if big else _small(6)
+    steps = 8 if big else 20
     d1 = H.make_detector(b, chains=32, precision="mixed", engine=TC)
-    d1.run_chains(20)
-    s1, _ = d1.get_chains()
+    d1.run_chains(steps)
+    s1, f1 = d1.get_chains()
     d2 = H.make_detector(b, chains=32, precision="mixed", engine=TC)
-    for t in range(20):
+    for t in range(steps):
         d2.run_chains(1, t)
-    s2, _ = d2.get_chains()
+    s2, f2 = d2.get_chains()
     np.testing.assert_array_equal(s1, s2)
     d1.destroy()
     d2.destroy()
@@ -51,13 +55,36 @@ def test_mixed_one_launch_equals_single_step_launches():
     [(36, 40, 16, 18.0), (33, 33, 64, 26.0)],          # N = 72, 66: ragged K and dimensions
     [(64, 64, 16, 20.0), (64, 128, 4, 8.0)],           # N = 128: two A-operand tiles
     [(1, 2, 4, 6.0), (3, 3, 64, 20.0), (8, 16, 16, 14.0)],
-    [(80, 96, 16, 18.0), (100, 100, 4, 12.0)],         # N = 160, 200: streamed operand, 3 / 4 tiles
+    [(80, 96, 16, 18.0), (100, 100, 4, 12.0)],         # N = 160, 200: 3- / 4-CTA clusters
     [(128, 128, 64, 28.0)],                            # N = 256: the largest channel
 ])
-def test_mixed_step_parity_shapes(shapes):
+@pytest.mark.parametrize("flags", [0, NO_CLUSTER])
+def test_mixed_step_parity_shapes(shapes, flags):
+    # flags: N > 128 on thread-block clusters (resident operand tiles), or on the single-CTA
+    # kernel that streams the operand from L2
     b = workload.generate(shapes, 91)
-    det = H.make_detector(b, chains=36, precision="mixed", split_terms=3, seed=2, engine=TC)
+    det = H.make_detector(b, chains=36, precision="mixed", split_terms=3, seed=2, engine=TC | flags)
     r = H.step_parity(det, b, H.targets(b), seed=2, steps=6, w_cat=2e-4, w_acc=2e-3)
+    assert r["bad"] == 0, r
+    assert r["mism"] <= max(4, r["steps"] // 500), r
+    det.destroy()
+
+
+@pytest.mark.parametrize("tile,terms,shapes", [
+    (64, 2, [(128, 128, 64, 28.0), (120, 128, 16, 24.0)]),   # N = 256, 240: 64 chains per CTA
+    (16, 2, [(70, 80, 4, 14.0)]),                             # N = 140: three-CTA clusters
+    (32, 3, [(100, 100, 64, 26.0)]),                          # N = 200: fourth tile a quarter full
+])
+def test_mixed_cluster_tiles(tile, terms, shapes):
+    """N > 128 on thread-block clusters (one resident operand tile per CTA; x' slices and the
+    chains' partial sums exchanged through distributed shared memory) at every chain tile: step
+    parity against the oracle with full and partial work items (100 chains per channel)."""
+    b = workload.generate(shapes, 95)
+    det = H.make_detector(b, chains=100, precision="mixed", split_terms=terms, seed=6, engine=TC,
+                          tile=tile)
+    w = 1.0 if terms == 3 else 32.0
+    r = H.step_parity(det, b, H.targets(b), seed=6, steps=4, w_cat=2e-4 * w, w_acc=2e-3 * w)
+    assert r["steps"] == 4 * 100 * b.n_channels
     assert r["bad"] == 0, r
     assert r["mism"] <= max(4, r["steps"] // 500), r
     det.destroy()
@@ -123,13 +150,14 @@ def test_uneven_batch_autotuned_and_graph_replay():
     d2.destroy()
 
 
-def test_mixed_kronecker_256_refresh():
-    """128x128 64-QAM Kronecker channels (N = 256, streamed tensor-core operand) with the FP64
-    refresh every 10 transitions: step parity, then tracked energies equal to FP64 evaluations
-    right after a refresh point."""
+@pytest.mark.parametrize("flags", [0, NO_CLUSTER])
+def test_mixed_kronecker_256_refresh(flags):
+    """128x128 64-QAM Kronecker channels (N = 256: four-CTA clusters, or the single-CTA kernel
+    with the operand streamed) with the FP64 refresh every 10 transitions: step parity, then
+    tracked energies equal to FP64 evaluations right after a refresh point."""
     b = workload.kronecker_batch(128, 128, 64, [30.0], 2, 0.5, 77)
     det = H.make_detector(b, chains=32, precision="mixed", split_terms=3, refresh_period=10,
-                          seed=5, engine=TC)
+                          seed=5, engine=TC | flags)
     r = H.step_parity(det, b, H.targets(b), seed=5, steps=3, w_cat=2e-4, w_acc=2e-3)
     assert r["bad"] == 0, r
     det.run_chains(17, 3)
