@@ -156,6 +156,7 @@ struct TcCtx {
     int rank;
     uint32_t bar_b, bar_x, b_phase, x_phase, x_buf;
     unsigned char *sx;
+    uint32_t bar_tma, tma_phase;  // the per-work-item operand copy (and its reload after a refresh)
 };
 
 // ------------------------------------------------------------------------------------------
@@ -498,6 +499,47 @@ __device__ __forceinline__ void table_load(uint32_t ta, uint32_t te, Table2<L> &
     tb.B = f2_pack(__uint_as_float(e[0]), __uint_as_float(e[1]));
     tb.C0 = f2_pack(__uint_as_float(e[2]), __uint_as_float(e[3]));
     tb.lgS = f2_pack(__uint_as_float(e[4]), __uint_as_float(e[5]));
+}
+
+// Thread 0: bulk copy of this channel's resident A operand into shared memory, completing on the
+// TMA barrier (a cluster CTA copies the S terms of its own tile of the channel's CL tiles).
+template <int MT, int CL>
+__device__ __forceinline__ void tc_stage_a(const TcCtx &x, const unsigned char *ops)
+{
+    const uint32_t tbytes = 128u * (uint32_t)x.Kp * 2u;
+    const uint32_t abytes = (uint32_t)x.S * MT * tbytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(x.bar_tma), "r"(abytes)
+                 : "memory");
+    const uint32_t chunk = 1u << 16;
+    for (int sc = 0; sc < (CL > 1 ? x.S : 1); ++sc) {
+        const unsigned char *src = ops + (CL > 1 ? (size_t)(sc * CL + x.rank) * tbytes : 0);
+        const uint32_t dst = smem_u32(x.sA) + (CL > 1 ? (uint32_t)sc * tbytes : 0u);
+        const uint32_t nb = CL > 1 ? tbytes : abytes;
+        for (uint32_t off = 0; off < nb; off += chunk) {
+            const uint32_t n = nb - off < chunk ? nb - off : chunk;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst + off),
+                "l"(src + off), "r"(n), "r"(x.bar_tma)
+                : "memory");
+        }
+    }
+}
+
+// round(g 2^sh) for |g 2^sh| < 2^62, from the bits of g (integer operations only: this GPU's FP64
+// pipe runs at a small fraction of its integer and FP32 rates). Ties round away from zero.
+__device__ __forceinline__ long long fixed_of(double g, int sh)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+    const int ex = (int)((b >> 52) & 0x7FFull);
+    if (ex == 0) return 0;                                  // zero or subnormal
+    const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    const int p = ex - 1075 + sh;                           // g 2^sh = mant 2^p
+    long long v;
+    if (p >= 0) v = p < 10 ? mant << p : 0;                 // p > 0 is outside the contract
+    else if (p > -64) v = (mant + (1ll << (-p - 1))) >> (-p);
+    else v = 0;
+    return (b >> 63) ? -v : v;
 }
 
 // One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
@@ -944,31 +986,105 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         // periodic FP64 refresh of the tracked energies (decisions never read them)
         if constexpr (CL > 1) {
             if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
-                // every CTA needs the whole state: x goes through the B operand's slice transfer,
-                // then each CTA evaluates its share of the upper-triangle row pairs in FP64 and the
-                // partial sums are exchanged (and added in rank order, identically in every CTA)
+                // every CTA needs the whole state: x goes through the B operand's slice transfer.
+                // Then x^T G x over this CTA's rows n (all columns m) is evaluated exactly for
+                // G rounded to 53 bits below its largest entry (|G_nm| <= max_n G_nn, G being
+                // positive semidefinite): G_nm 2^sh = sum_k d_k,nm 256^k with balanced int8 digits
+                // d_k (k = 0..6), and Q_k = sum_n x_n sum_m d_k,nm x_m is an exact int32 sum of
+                // DP4A products. The partial sums sum_k Q_k 256^k 2^-sh (FP64) and z^T x over the
+                // rows are exchanged and added in rank order, identically in every CTA. The A
+                // operand's shared memory holds the scratch and is reloaded afterwards.
                 write_b(k2);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
                 if (x.tid == 0) cl_send_b<CL>(x);
-                const bool okb = mbar_wait(x.bar_b, x.b_phase);
+                bool okb = mbar_wait(x.bar_b, x.b_phase);
                 x.b_phase ^= 1u;
                 const double *Gm = A.G64 + d.mat_off;
                 const double *z = A.z64 + d.vec_off;
-                for (int c = x.warp; c < nC; c += blockDim.x >> 5) {
-                    double quad, lin;
-                    quad_lin_fp64_part(Gm, z, N, x.rank + CL * x.lane, 32 * CL,
-                                       [&](int n) { return (double)b_level(c, n); }, quad, lin);
+                const int Kp = x.Kp, XS = Kp + 16, nw = Kp / 4, n0 = 64 * x.rank;
+                int8_t *sX = reinterpret_cast<int8_t *>(x.sA);                    // [C][XS] states
+                uint32_t *sD = reinterpret_cast<uint32_t *>(x.sA + C * XS);       // [7][16][nw] digits
+                int *sQ = reinterpret_cast<int *>(x.sA + C * XS + 112 * Kp);     // [C][7] Q_k
+                if (x.warp == 0) {
+                    double mx = 0.0;
+                    for (int n = x.lane; n < N; n += 32) mx = fmax(mx, Gm[(long long)n * N + n]);
 #pragma unroll
-                    for (int o = 16; o; o >>= 1) {
-                        quad += __shfl_xor_sync(0xffffffffu, quad, o);
-                        lin += __shfl_xor_sync(0xffffffffu, lin, o);
-                    }
-                    if (x.lane == 0) {
-                        x.sref[2 * c] = quad;
-                        x.sref[2 * c + 1] = lin;
-                    }
+                    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                    if (x.lane == 0) x.sref[0] = mx;
                 }
+                for (int e = x.tid; e < C * Kp; e += x.nthr) {
+                    const int c = e / Kp, m = e - c * Kp;
+                    sX[c * XS + m] = (int8_t)b_level(c, m);
+                }
+                for (int e = x.tid; e < 7 * C; e += x.nthr) sQ[e] = 0;
+                __syncthreads();
+                int ex2;
+                frexp(x.sref[0], &ex2);
+                const int sh = 53 - ex2;                         // |G_nm| 2^sh < 2^53
+                const int cc = x.tid % C, rg = x.tid / C;        // chain; row rg of each 16-row block
+                int pk[7] = {0, 0, 0, 0, 0, 0, 0};
+                for (int rb = 0; rb < 4; ++rb) {
+                    if (rb) __syncthreads();                     // the last block's digits are read
+                    for (int u = x.tid; u < 16 * nw; u += x.nthr) {
+                        const int i = u / nw, w = u - i * nw, n = n0 + 16 * rb + i;
+                        uint32_t dw[7] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                        if (n < N) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int m = 4 * w + j;
+                                long long v = m < N ? fixed_of(Gm[(long long)n * N + m], sh) : 0;
+#pragma unroll
+                                for (int k = 0; k < 7; ++k) {
+                                    const int lo = (int)(v & 255), dk = lo >= 128 ? lo - 256 : lo;
+                                    v = (v - dk) >> 8;
+                                    dw[k] |= (uint32_t)(dk & 255) << (8 * j);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) sD[(k * 16 + i) * nw + w] = dw[k];
+                    }
+                    __syncthreads();
+                    int tk[7] = {0, 0, 0, 0, 0, 0, 0};
+                    const uint32_t *xw = reinterpret_cast<const uint32_t *>(sX + cc * XS);
+                    for (int w = 0; w < nw; w += 4) {
+                        const uint4 xv = *reinterpret_cast<const uint4 *>(xw + w);
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) {
+                            const uint4 dv = *reinterpret_cast<const uint4 *>(sD + (k * 16 + rg) * nw + w);
+                            int a = tk[k];
+                            a = __dp4a((int)dv.x, (int)xv.x, a);
+                            a = __dp4a((int)dv.y, (int)xv.y, a);
+                            a = __dp4a((int)dv.z, (int)xv.z, a);
+                            a = __dp4a((int)dv.w, (int)xv.w, a);
+                            tk[k] = a;
+                        }
+                    }
+                    const int n = n0 + 16 * rb + rg;
+                    const int xn = n < N ? (int)sX[cc * XS + n] : 0;
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) pk[k] += xn * tk[k];
+                }
+                // integer sums: exact in any order
+#pragma unroll
+                for (int k = 0; k < 7; ++k) atomicAdd(&sQ[cc * 7 + k], pk[k]);
+                __syncthreads();
+                if (x.tid < nC) {
+                    const int c = x.tid;
+                    double q = 0.0;
+                    for (int k = 6; k >= 0; --k) q = fma(q, 256.0, (double)sQ[c * 7 + k]);
+                    double l = 0.0;
+                    for (int n = n0; n < n0 + 64 && n < N; ++n) l = fma(z[n], (double)sX[c * XS + n], l);
+                    x.sref[2 * c] = ldexp(q, -sh);
+                    x.sref[2 * c + 1] = l;
+                }
+                // the scratch is read: reload the resident operand (complete before the next MMA)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (x.tid == 0) tc_stage_a<MT, CL>(x, A.tc_ops + d.tc_off);
+                okb = mbar_wait(x.bar_tma, x.tma_phase) && okb;
+                x.tma_phase ^= 1u;
                 bool xf = __syncthreads_or(!okb);
                 if (x.tid < C) {
                     const int c = x.tid;
@@ -1084,7 +1200,8 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     x.nthr = blockDim.x;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.tmem);
-    const uint32_t bar_tma = smem_u32(&bars[0]);
+    x.bar_tma = smem_u32(&bars[0]);
+    x.tma_phase = 0;
     x.bar_mma = smem_u32(&bars[1]);
     x.tid = threadIdx.x;
     x.warp = x.tid >> 5;
@@ -1121,7 +1238,7 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     const int ncols_alloc = A.tc_tmem_cols;   // TMEM columns to allocate (power of 2, >= 32)
 
     if (x.tid == 0) {
-        mbar_init(bar_tma, 1);
+        mbar_init(x.bar_tma, 1);
         mbar_init(x.bar_mma, 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(x.bar_full[b], 1);
@@ -1144,7 +1261,6 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     // zero the B operand once: padding columns / chains stay zero, the rest is rewritten
     for (int e = x.tid; e < (int)(lay.red - lay.b) / 16; e += blockDim.x)
         reinterpret_cast<uint4 *>(x.sB)[e] = make_uint4(0, 0, 0, 0);
-    uint32_t tma_phase = 0;
     bool alive = true;
     // a cluster's CTAs start exchanging only once every CTA's barriers and B operand are set up
     if constexpr (CL > 1) cl_sync();
@@ -1171,35 +1287,13 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
             __syncthreads();
             continue;
         }
-        // stage this channel's A operand (TMA bulk copy, mbarrier completion); a cluster CTA
-        // stages the S terms of its own tile (rank) of the channel's CL tiles
-        const uint32_t abytes = (uint32_t)S * MT * 128u * (uint32_t)Kp * 2u;
-        if (x.tid == 0) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_tma),
-                         "r"(abytes)
-                         : "memory");
-            const uint32_t tbytes = 128u * (uint32_t)Kp * 2u;
-            const uint32_t chunk = 1u << 16;
-            for (int sc = 0; sc < (CL > 1 ? S : 1); ++sc) {
-                const unsigned char *src =
-                    A.tc_ops + d.tc_off + (CL > 1 ? (size_t)(sc * CL + x.rank) * tbytes : 0);
-                const uint32_t dst = smem_u32(x.sA) + (CL > 1 ? (uint32_t)sc * tbytes : 0u);
-                const uint32_t nb = CL > 1 ? tbytes : abytes;
-                for (uint32_t off = 0; off < nb; off += chunk) {
-                    const uint32_t n = nb - off < chunk ? nb - off : chunk;
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
-                        "%2, [%3];" ::"r"(dst + off),
-                        "l"(src + off), "r"(n), "r"(bar_tma)
-                        : "memory");
-                }
-            }
-        }
-        if (__syncthreads_or(!mbar_wait(bar_tma, tma_phase))) {
+        // stage this channel's A operand (TMA bulk copy, mbarrier completion)
+        if (x.tid == 0) tc_stage_a<MT, CL>(x, A.tc_ops + d.tc_off);
+        if (__syncthreads_or(!mbar_wait(x.bar_tma, x.tma_phase))) {
             alive = false;
             set_status(A.status, kStatusTimeout);
         }
-        tma_phase ^= 1u;
+        x.tma_phase ^= 1u;
         if (!alive) break;
         switch (d.L) {
         case 2: tc_item_dispatch<MT, 2, G, CL>(A, x, it, d, alive); break;
@@ -1315,7 +1409,11 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
         const int CL = (max_n + 63) / 64, Kp = (max_n + 15) / 16 * 16, C = chains_per_cta;
         if (C == 16 || C == 32 || C == 64) {
             const TcLayout L = tc_layout(split_terms, 1, Kp, C, CL);
-            if (L.total <= smem_optin && cluster_capacity(CL, L.total, 16 * C) > 0) {
+            // the FP64 refresh's scratch (states, one 16-row block of digits, sums) lives in the
+            // A operand's shared memory
+            const long long scratch = (long long)C * (Kp + 16) + 112LL * Kp + 28LL * C;
+            if (L.total <= smem_optin && scratch <= (long long)split_terms * 256 * Kp &&
+                cluster_capacity(CL, L.total, 16 * C) > 0) {
                 plan->valid = 1;
                 plan->chains_per_cta = C;
                 plan->groups = 1;
