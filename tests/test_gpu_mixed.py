@@ -122,7 +122,7 @@ def test_mixed_energies_refresh():
     for ch in range(b.n_channels):
         for c in range(32):
             fx = oracle.f_value(tg[ch].Hr, tg[ch].yr, tg[ch].sigma2, tg[ch].values(st[ch][c]))
-            assert abs(f[ch * 32 + c] - fx) <= 1e-9 * abs(fx)
+            assert abs(f[ch * 32 + c] - fx) <= 1e-10 * abs(fx)
     assert out["stats"]["refresh_drift"] < 1e-2
     det.destroy()
 
@@ -154,7 +154,10 @@ def test_uneven_batch_autotuned_and_graph_replay():
 def test_mixed_kronecker_256_refresh(flags):
     """128x128 64-QAM Kronecker channels (N = 256: four-CTA clusters, or the single-CTA kernel
     with the operand streamed) with the FP64 refresh every 10 transitions: step parity, then
-    tracked energies equal to FP64 evaluations right after a refresh point."""
+    tracked energies equal to FP64 evaluations right after a refresh point. The clusters'
+    refresh rounds G to 53 bits below its largest diagonal entry: at most about 2e-14 of the
+    quadratic term, which the cancellation in f = -|y - Hx|^2 / sigma^2 (30 dB) raises to about
+    2e-11 of f, below the 1e-10 asked here."""
     b = workload.kronecker_batch(128, 128, 64, [30.0], 2, 0.5, 77)
     det = H.make_detector(b, chains=32, precision="mixed", split_terms=3, refresh_period=10,
                           seed=5, engine=TC | flags)
@@ -168,7 +171,7 @@ def test_mixed_kronecker_256_refresh(flags):
     for ch in range(b.n_channels):
         for c in range(32):
             fx = oracle.f_value(tg[ch].Hr, tg[ch].yr, tg[ch].sigma2, tg[ch].values(st[ch][c]))
-            assert abs(f[ch * 32 + c] - fx) <= 1e-9 * abs(fx)
+            assert abs(f[ch * 32 + c] - fx) <= 1e-10 * abs(fx)
     assert out["stats"]["refresh_drift"] < 1e-1
     det.destroy()
 
