@@ -1,10 +1,10 @@
-"""Parity at the full benchmark size, in the launch configuration bench.py times: 32x32 64-QAM
+"""Parity at the full benchmark sizes, in the launch configuration bench.py times: 32x32 64-QAM
 Rayleigh, SNR 20..32 dB (7 points x 4096 channels), 64 chains, MIXED precision with two split-BF16
 terms, autotuned engine, seed 0. Sampled channels spread over the batch are checked against the
 FP64 oracle: transition by transition (step mode, MIXED-S2 windows), and after a 200-transition
 launch through properties that hold at any size (tracked and best energies equal FP64
 evaluations of the exported states, LLRs equal the oracle's IS-LLR of the exported final
-states)."""
+states). The same for the 128x128 Kronecker workload (N = 256, thread-block clusters)."""
 import numpy as np
 import pytest
 
@@ -65,4 +65,63 @@ def test_full_size_run_properties(bench_batch):
         ref = t.llr_is(st[ch])
         got = out["llr"][ch * 192:(ch + 1) * 192]
         np.testing.assert_allclose(got, ref, atol=2e-3 * max(1.0, np.abs(ref).max()), rtol=1e-4)
+    det.destroy()
+
+
+# 128x128 64-QAM Kronecker (rho = 0.5), SNR 26..34 dB, 1024 channels, 256 chains, FP64 energy
+# refresh every 50 transitions: the N = 256 workload, which runs on four-CTA thread-block clusters
+# (autotuned chain tile).
+KRON_SAMPLED = [0, 1, 511, 700, 1023]
+
+
+@pytest.fixture(scope="module")
+def kron_batch():
+    w = workload.WORKLOADS["kronecker_128x128_64qam"]
+    return workload.kronecker_batch(w["nt"], w["nr"], w["qam"], w["snr_db"], w["total"], w["rho"], w["seed"])
+
+
+def _kdet(b):
+    return H.make_detector(b, chains=256, precision="mixed", split_terms=2, refresh_period=50, seed=0)
+
+
+def test_kronecker_full_size_step_parity(kron_batch):
+    b = kron_batch
+    assert b.n_channels == 1024
+    det = _kdet(b)
+    tg = H.targets(b, channels=KRON_SAMPLED)
+    r = H.step_parity(det, b, tg, seed=0, steps=2, w_cat=6.4e-3, w_acc=6.4e-2)
+    assert r["steps"] == 2 * 256 * len(KRON_SAMPLED)
+    assert r["bad"] == 0, r
+    assert r["mism"] <= max(4, r["steps"] // 100), r
+    det.destroy()
+
+
+def test_kronecker_full_size_run_properties(kron_batch):
+    b = kron_batch
+    det = _kdet(b)
+    det.run_chains(300)   # the last transition is a refresh point
+    out = det.estimate(stats=True)
+    flat, f = det.get_chains()
+    st = H.split_states(det, b, flat)
+    tg = H.targets(b, channels=KRON_SAMPLED)
+    for ch in KRON_SAMPLED:
+        t = tg[ch]
+        for c in range(0, 256, 17):
+            fx = oracle.f_value(t.Hr, t.yr, t.sigma2, t.values(st[ch][c]))
+            assert abs(f[ch * 256 + c] - fx) <= 1e-10 * abs(fx), (ch, c, f[ch * 256 + c], fx)
+        lab = out["best_idx"][ch * 128:(ch + 1) * 128]
+        kb = H.levels_from_labels(lab, 128, 8)
+        fb = oracle.f_value(t.Hr, t.yr, t.sigma2, t.values(kb))
+        assert abs(out["best_f"][ch] - fb) <= 1e-9 * abs(fb) + 1e-9
+        finals = [oracle.f_value(t.Hr, t.yr, t.sigma2, t.values(st[ch][c])) for c in range(256)]
+        assert fb >= max(finals) - 1e-9 * abs(fb)
+        ref = t.llr_is(st[ch])
+        got = out["llr"][ch * 768:(ch + 1) * 768]
+        np.testing.assert_allclose(got, ref, atol=2e-3 * max(1.0, np.abs(ref).max()), rtol=1e-4)
+    # between refreshes the energies move by FP32 increments whose products carry the split
+    # error 2^-17 of two BF16 terms, relative to the energy scale |y|^2 / sigma^2: the largest
+    # correction a refresh made stays within ten such worst-case increments
+    scale = max(float(np.sum(np.abs(b.y[b.y_off[i]:b.y_off[i] + b.nr[i]]) ** 2)) / float(b.sigma2[i])
+                for i in range(b.n_channels))
+    assert out["stats"]["refresh_drift"] <= 10 * 2.0 ** -17 * scale, (out["stats"]["refresh_drift"], scale)
     det.destroy()
