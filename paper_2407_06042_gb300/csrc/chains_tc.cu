@@ -1412,8 +1412,9 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
             // the FP64 refresh's scratch (states, one 16-row block of digits, sums) lives in the
             // A operand's shared memory
             const long long scratch = (long long)C * (Kp + 16) + 112LL * Kp + 28LL * C;
-            if (L.total <= smem_optin && scratch <= (long long)split_terms * 256 * Kp &&
-                cluster_capacity(CL, L.total, 16 * C) > 0) {
+            const int ncl = L.total <= smem_optin && scratch <= (long long)split_terms * 256 * Kp
+                                ? cluster_capacity(CL, L.total, 16 * C) : 0;
+            if (ncl > 0) {
                 plan->valid = 1;
                 plan->chains_per_cta = C;
                 plan->groups = 1;
@@ -1426,6 +1427,7 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
                 plan->ctas_per_sm = 1;
                 plan->smem = L.total;
                 plan->cluster = CL;
+                plan->max_clusters = ncl;
                 return true;
             }
         }
@@ -1488,9 +1490,11 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e;
     if (plan.cluster > 1) {
-        const int CL = plan.cluster;
-        const int ncl = cluster_capacity(CL, plan.smem, plan.threads);
+        const int CL = plan.cluster, ncl = plan.max_clusters;
         if (ncl <= 0) return cudaErrorInvalidConfiguration;
+        if ((e = cudaFuncSetAttribute(cluster_kernel(CL), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)plan.smem)) != cudaSuccess)
+            return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(CL * std::min(a.n_items, ncl)), 1, 1);
         cfg.blockDim = dim3((unsigned)plan.threads, 1, 1);

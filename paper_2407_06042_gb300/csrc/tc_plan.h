@@ -22,6 +22,8 @@ struct TcPlan {
     size_t smem;            // dynamic shared memory per CTA (bytes)
     int cluster;            // CTAs per thread-block cluster: m_tiles for N > 128 (one resident
                             // tile per CTA, chains_per_cta 16, 32 or 64), else 1
+    int max_clusters;       // clusters that can be resident at once (queried when planning, so
+                            // that launches, also inside a stream capture, need no query)
 };
 
 // Kernel shape for a group of channels with the same K extent (N rounded up to 16) and tile

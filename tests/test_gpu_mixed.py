@@ -150,6 +150,21 @@ def test_uneven_batch_autotuned_and_graph_replay():
     d2.destroy()
 
 
+def test_cluster_graph_replay():
+    """N = 200 and 256 on thread-block clusters, launched directly and replayed from a captured
+    CUDA graph (with the FP64 refresh): bit-identical chains and LLRs."""
+    b = workload.generate([(100, 100, 16, 20.0), (128, 128, 64, 26.0)], 99)
+    outs = []
+    for flags in (TC, TC | GRAPH):
+        det = H.make_detector(b, chains=64, precision="mixed", seed=8, refresh_period=5, engine=flags)
+        det.run_chains(7)
+        det.run_chains(6, 7)
+        outs.append((det.get_chains()[0], det.estimate()["llr"]))
+        det.destroy()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
 @pytest.mark.parametrize("flags", [0, NO_CLUSTER])
 def test_mixed_kronecker_256_refresh(flags):
     """128x128 64-QAM Kronecker channels (N = 256: four-CTA clusters, or the single-CTA kernel
