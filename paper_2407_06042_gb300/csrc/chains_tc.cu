@@ -11,8 +11,10 @@
 //   2. one thread issues D = A * X'^T on the tensor core: A = [Gt | P~ Gt] rows (split into
 //      `split_terms` BF16 terms, FP32 accumulation in TMEM); completion is signalled through an
 //      mbarrier, and the chains' acceptance uniforms are drawn meanwhile. For N <= 128 the A
-//      operand is staged once per work item by a bulk copy; beyond, it is streamed from L2 in
-//      128-row chunks through two buffers (full / empty mbarriers) every transition;
+//      operand is staged once per work item by a bulk copy. Beyond, a thread-block cluster
+//      keeps one 128-row tile resident per CTA (see the cluster section below), or, as a
+//      fallback, one CTA streams the operand from L2 in 128-row chunks through two buffers
+//      (full / empty mbarriers) every transition;
 //   3. every thread reads its TMEM lane (one row of A = one dimension of Gt or P~Gt) for its
 //      8 columns (chains), swaps halves with its partner lane, and evaluates the reverse factor
 //      and the energy difference (Eqs. (3), (18));
@@ -23,11 +25,13 @@
 // Gt (l < 16) or of P~ Gt (l >= 16), so each warp's TMEM quadrant carries both quantities of
 // 16 dimensions; each thread owns one dimension of 4 chains per tile. Channels of N <= 32 hold
 // their rows twice (quadrants 0-1 and 2-3: dimension 16 (q mod 2) + (l & 15)), and each copy
-// serves its own group of chains, so a CTA runs twice the chains with the same threads. Both operands are K-major,
-// no swizzle, in 8 x 16-byte core matrices: K-adjacent core matrices 128 B apart (LBO), 8-row
-// groups (K/8)*128 B apart (SBO).
+// serves its own group of chains, so a CTA runs twice the chains with the same threads. Both
+// operands are K-major, no swizzle, in 8 x 16-byte core matrices. A: K-adjacent core matrices
+// 128 B apart (LBO), 8-row groups (K/8)*128 B apart (SBO). B: 144 B and a stride 32 B past a
+// multiple of 128 B (b_lbo, b_sbo), which keeps the threads' 16-bit stores free of bank conflicts.
 // Every wait is bounded: a wait that runs out sets the timeout status bit, the CTA stops issuing
-// work, waits (bounded) for its copies in flight, frees its TMEM and returns.
+// work, waits (bounded) for its copies in flight, frees its TMEM and returns (in a cluster, after
+// the exit barrier that keeps every CTA's shared memory alive for the others' stores).
 #include "tc_plan.h"
 
 #include <cuda_bf16.h>
@@ -73,8 +77,10 @@ struct TcLayout {
     uint32_t a, b, red, dred, acc, ref, fst, cnt, fref, kb, dg, xs, bar, tmem, total;
 };
 
-// The A operand stays resident for MT <= 2 (N <= 128). Beyond that it no longer fits one SM's
-// shared memory and is streamed from L2 in 128-row x Kp chunks through two buffers.
+// The A operand of a single CTA stays resident for MT <= 2 (N <= 128). Beyond that it no longer
+// fits one SM's shared memory: the cluster kernels (instantiated with MT = 1 per CTA) keep one
+// tile per CTA, and the single-CTA fallback streams it from L2 in 128-row x Kp chunks through
+// two buffers.
 __host__ __device__ constexpr bool tc_streamed(int MT) { return MT >= 3; }
 
 // Chain groups per CTA: channels of N <= 32 use half of the 64 dimension rows of a tile, so the

@@ -38,7 +38,7 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
 long long tc_operand_bytes(int N, int split_terms);
 
 // Packs [Gt | P~Gt] (the FP32 CUDA-core operand, N x NOp per channel) into the BF16 split
-// operand block of every channel with N <= 128, in the canonical tcgen05 layout (each block
+// operand block of every channel with N <= 256, in the canonical tcgen05 layout (each block
 // sized for the channel's own K extent and tile count).
 cudaError_t tc_launch_pack(int split_terms, const ChannelDesc *desc, int n_channels,
                            const float *bt32, uint8_t *tc_ops, cudaStream_t s);
