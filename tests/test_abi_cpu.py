@@ -93,3 +93,35 @@ def test_diag_argument_checks_on_the_host():
     ]
     for args in bad:
         assert call(*args) == 1, args
+
+
+def test_config_validation_on_the_host():
+    """mcmc_detect_create rejects an invalid configuration before any device call (EINVAL). A
+    valid one passes validation and, on a machine without a GPU, stops at the device query
+    (EUNSUPPORTED); with a GPU it creates a handle, which is destroyed again."""
+    import paper_2407_06042_gb300 as pkg
+    lib = pkg.load()
+    TC, AUTO, GRAPH, NOCL = pkg.MCMC_ENGINE_TC, pkg.MCMC_ENGINE_AUTO, pkg.MCMC_ENGINE_GRAPH, pkg.MCMC_ENGINE_NO_CLUSTER
+    MIXED, FP32 = pkg.MCMC_PREC_MIXED, pkg.MCMC_PREC_FP32
+
+    def create(**kw):
+        cfg = pkg.Config()
+        lib.mcmc_config_default(ctypes.byref(cfg))
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        st = lib.mcmc_detect_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st == 0:
+            lib.mcmc_detect_destroy(h)
+        return st
+
+    for kw in [dict(precision=MIXED, engine=TC, tile=64, max_nt=128, max_nr=128),
+               dict(precision=MIXED, engine=TC | NOCL, tile=32),
+               dict(precision=MIXED, engine=TC | GRAPH | NOCL),
+               dict(precision=MIXED, engine=AUTO | NOCL),
+               dict(precision=FP32, engine=pkg.MCMC_ENGINE_SIMT, tile=64)]:
+        assert create(**kw) in (0, 7), kw
+    for kw in [dict(engine=16), dict(engine=3), dict(precision=MIXED, engine=TC, tile=48),
+               dict(precision=MIXED, engine=AUTO, tile=64), dict(precision=FP32, engine=TC),
+               dict(max_nt=129), dict(chains=6), dict(split_terms=4)]:
+        assert create(**kw) == 1, kw
