@@ -15,8 +15,6 @@ namespace {
 
 struct cd { double x, y; };   // complex double
 __device__ __forceinline__ cd cmul(cd a, cd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-__device__ __forceinline__ cd cmulc(cd a, cd b) { return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; } // conj(a) b
-__device__ __forceinline__ cd csub(cd a, cd b) { return {a.x - b.x, a.y - b.y}; }
 
 // Float-float accumulator: s is the FP32 running sum, e gathers the exact rounding errors of the
 // additions (TwoSum) and of the products (FMA split), so s + e carries ~48 significant bits.
