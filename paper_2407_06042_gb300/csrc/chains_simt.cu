@@ -426,11 +426,11 @@ cudaError_t launch_chains_simt(const ChainArgs &a_in, bool fp64, size_t smem, cu
     cudaError_t e;
     if (fp64) {
         auto k = chains_simt_kernel<double, 4, 4>;
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        if ((e = allow_max_dyn_smem(k)) != cudaSuccess) return e;
         k<<<a.n_items, 256, smem, s>>>(a);
     } else {
         auto k = chains_simt_kernel<float, 8, 4>;
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+        if ((e = allow_max_dyn_smem(k)) != cudaSuccess) return e;
         k<<<a.n_items, 256, smem, s>>>(a);
     }
     return cudaGetLastError();

@@ -1382,8 +1382,10 @@ TcKernel cluster_kernel(int CL) { return CL == 3 ? chains_tc_kernel<1, 1, 3> : c
 int cluster_capacity(int CL, size_t smem, int threads)
 {
     const TcKernel k = cluster_kernel(CL);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (allow_max_dyn_smem(k) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)CL, 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1498,9 +1500,7 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
     if (plan.cluster > 1) {
         const int CL = plan.cluster, ncl = plan.max_clusters;
         if (ncl <= 0) return cudaErrorInvalidConfiguration;
-        if ((e = cudaFuncSetAttribute(cluster_kernel(CL), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)plan.smem)) != cudaSuccess)
-            return e;
+        if ((e = allow_max_dyn_smem(cluster_kernel(CL))) != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(CL * std::min(a.n_items, ncl)), 1, 1);
         cfg.blockDim = dim3((unsigned)plan.threads, 1, 1);
@@ -1519,8 +1519,7 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
     }
     const int grid = std::min(a.n_items, std::max(1, sms * plan.ctas_per_sm));
     auto go = [&](auto k) {
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem)) != cudaSuccess)
-            return e;
+        if ((e = allow_max_dyn_smem(k)) != cudaSuccess) return e;
         k<<<grid, plan.threads, plan.smem, s>>>(a, plan.chains_per_cta, plan.split_terms, plan.kdim);
         return cudaSuccess;
     };

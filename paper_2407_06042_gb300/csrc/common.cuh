@@ -25,6 +25,19 @@ namespace mcmcdet {
 constexpr int kMaxN = 256;     // real unknowns per channel (Nt <= 128)
 constexpr int kMaxL = 8;       // PAM levels per real dimension (64-QAM)
 
+// Lets kernel `func` take up to the device's opt-in maximum of dynamic shared memory (each launch
+// then asks for what it needs). Every launch site sets this same value, so handles used from
+// different host threads cannot lower the limit between another thread's setting and its launch.
+template <typename F>
+inline cudaError_t allow_max_dyn_smem(F *func)
+{
+    int dev = 0, mx = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+
 // Per-channel description, built on the host at preprocess time.
 struct ChannelDesc {
     int N;             // real unknowns 2 Nt

@@ -365,8 +365,7 @@ extern "C" mcmc_status mcmc_diag_transition(int32_t n_channels, int32_t nt, int3
     a.tv_steps = tv ? tv_steps : 0;
     const DiagLayout lay = diag_layout(a.M, N, a.S, L, eig != nullptr);
     const size_t smem = sizeof(double) * (size_t)lay.total;
-    if (cudaFuncSetAttribute(diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+    if (allow_max_dyn_smem(diag_kernel) != cudaSuccess) {
         cudaGetLastError();
         return MCMC_ECUDA;
     }

@@ -432,9 +432,7 @@ cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
     if (n_channels <= 0) return cudaSuccess;
     cudaError_t e;
     if (h_stage_bytes > 48 * 1024) {
-        e = cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)h_stage_bytes);
-        if (e != cudaSuccess) return e;
+        if ((e = allow_max_dyn_smem(gram_kernel)) != cudaSuccess) return e;
     }
     gram_kernel<<<n_channels, gram_threads(a.max_nt), a.stage_h ? h_stage_bytes : 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -446,9 +444,7 @@ cudaError_t launch_prep(const PrepArgs &a, int n_channels, size_t h_stage_bytes,
             gj_stage_bytes = 0;
         }
         if (gj_stage_bytes > 48 * 1024) {
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)gj_stage_bytes);
-            if (e != cudaSuccess) return e;
+            if ((e = allow_max_dyn_smem(k)) != cudaSuccess) return e;
         }
         k<<<n_channels, 256, gj_stage_bytes, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
