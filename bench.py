@@ -114,15 +114,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_PEAKS = None
+
+
 def pipe_peaks():
-    """Measured pipe throughputs of this GPU (ops/s): MUFU ex2, FP32 FMA, FP32x2 FMA lanes, FP64."""
+    """Measured pipe throughputs of this GPU (ops/s): MUFU ex2, FP32 FMA, FP32x2 FMA lanes, FP64
+    FMA, integer three-input XOR, 32x32->64 products, and whole Philox4x32-10 blocks (measured
+    once per process)."""
+    global _PEAKS
+    if _PEAKS is not None:
+        return _PEAKS
     import ctypes
     from paper_2407_06042_gb300 import build as _b
     lib = ctypes.CDLL(_b.build_peaks())
-    out = (ctypes.c_double * 4)()
+    out = (ctypes.c_double * 7)()
     if lib.mcmc_pipe_peaks(out) != 0:
         return None
-    return {"ex2": out[0], "fma": out[1], "fma2_lanes": out[2], "dfma": out[3]}
+    _PEAKS = {"ex2": out[0], "fma": out[1], "fma2_lanes": out[2], "dfma": out[3],
+              "xor3": out[4], "mulwide": out[5], "philox": out[6]}
+    return _PEAKS
 
 
 def _kernel_hash(files):
@@ -169,6 +179,9 @@ def chain_roofline(precision, w, units, chain_ms, batch=None):
         dimension: slope, energy term, accumulations), plus the Gram products' N 2N FMAs when
         they run on the CUDA cores (plain FP32 sampler);
       - tensor: 2 N 2N Gram flops (D' = X'[Gt | P~Gt]; 2 N N without the preconditioner);
+      - Philox: (N + 1) / 4 Philox4x32-10 blocks (one 32-bit word per proposal dimension and
+        one for the MH test, four words per block) on the integer pipes, against the measured
+        rate of whole blocks;
       - HBM: the operand block and the states once per work item (no per-transition traffic).
     Each pipe's time is its work over its measured peak on this GPU; the pipe with the largest
     time is the bound, and the line reports that pipe's achieved rate over its peak. The other
@@ -181,12 +194,14 @@ def chain_roofline(precision, w, units, chain_ms, batch=None):
         mufu = float((Ns * (Ls + 1) + 1).mean())
         fp32 = float((5 * Ns * Ls + 4 * Ns).mean())
         gemm = float((2 * Ns * (2 if pre else 1) * Ns).mean())
+        philox = float(((Ns + 1) / 4).mean())
     else:
         N = 2 * w["nt"]
         L = int(np.sqrt(w["qam"]))
         mufu = N * (L + 1) + 1
         fp32 = 5 * N * L + 4 * N
         gemm = 2 * N * (2 if pre else 1) * N
+        philox = (N + 1) / 4
     fp32_label = "5NL+4N"
     if precision != "mixed":
         fp32 += gemm / 2          # the Gram products as FMAs on the CUDA cores
@@ -200,6 +215,9 @@ def chain_roofline(precision, w, units, chain_ms, batch=None):
         "fp32": {"ops": fp32, "peak": peaks.get("fma"),
                  "per_unit": f"{fp32:g} FP32 ops per chain-iteration ({fp32_label}, N={N:g}, L={L:g})",
                  "pipe": "FP32 lanes, measured FMA rate of this GPU"},
+        "philox": {"ops": philox, "peak": peaks.get("philox"),
+                   "per_unit": f"{philox:g} Philox4x32-10 blocks per chain-iteration ((N+1)/4, N={N:g})",
+                   "pipe": "integer pipes (IMAD.WIDE + LOP3), measured rate of whole Philox blocks"},
     }
     for v in pipes.values():
         v["achieved"] = v["ops"] * units / t
@@ -287,10 +305,11 @@ def ber_of(batch, llr, best_idx):
             for k, v in per.items()}
 
 
-def cpu_baseline(batch, w, budget_s: float, rank: int):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload on the host cores:
-    an equal number of channels from every SNR point (or an even spread over the batch when the
-    SNR is continuous), sized from a calibration run so that the sample takes ~budget_s."""
+def cpu_sample(batch, w, budget_s: float):
+    """A bounded sample of the workload for the FP64 oracle on the host cores: whole waves of one
+    channel per core (so no core idles), sized from a one-wave calibration run to take about
+    budget_s, drawn evenly from every SNR point (or spread over the batch when the SNR is
+    continuous). Returns (channel indices, cores)."""
     import oracle
     cores = os.cpu_count() or 1
     T, Np = w["iterations"], w["chains"]
@@ -298,21 +317,109 @@ def cpu_baseline(batch, w, budget_s: float, rank: int):
     if len(snrs) <= 16:
         by = [[i for i in range(batch.n_channels) if batch.snr_db[i] == s] for s in snrs]
     else:
-        by = [list(range(batch.n_channels))[::max(1, batch.n_channels // 64)]]
+        by = [list(range(batch.n_channels))[::max(1, batch.n_channels // 4096)]]
+
+    def pick(n):
+        # round-robin over the SNR groups: n channels, as equal a share per group as n allows
+        out, k = [], 0
+        while len(out) < n and any(k < len(g) for g in by):
+            for g in by:
+                if k < len(g) and len(out) < n:
+                    out.append(g[k])
+            k += 1
+        return out
+    wave = pick(cores)
     t0 = time.perf_counter()
-    idx = [g[0] for g in by]
-    oracle.detect_batch(batch, chains=Np, iterations=T, seed=0, channels=idx, threads=cores)
+    oracle.detect_batch(batch, chains=Np, iterations=T, seed=0, channels=wave, threads=cores)
     dt = time.perf_counter() - t0
-    per = max(1, min(min(len(g) for g in by), int(budget_s / max(dt, 1e-3) * len(idx) / len(by))))
-    idx = [i for g in by for i in g[:per]]
+    waves = max(1, int(budget_s / max(dt, 1e-3)))
+    return pick(cores * waves), cores
+
+
+def cpu_baseline(batch, w, budget_s: float, rank: int, idx=None):
+    """The FP64 oracle, as it stands, timed on a bounded sample of the workload (cpu_sample) on
+    the host cores, one channel per thread."""
+    import oracle
+    cores = os.cpu_count() or 1
+    T, Np = w["iterations"], w["chains"]
+    if idx is None:
+        idx, cores = cpu_sample(batch, w, budget_s)
     t0 = time.perf_counter()
     oracle.detect_batch(batch, chains=Np, iterations=T, seed=0, channels=idx, threads=cores)
     dt = time.perf_counter() - t0
     value = len(idx) * Np * T / dt
+    n_snr = len(set(batch.snr_db[idx].tolist()))
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(idx)} channels ({per} per SNR group) x {Np} chains x {T} "
-                      f"iterations, FP64 C oracle, one channel per thread", "seconds": dt,
+            "sample": f"{len(idx)} channels ({n_snr} SNR points, whole waves of one channel per "
+                      f"core) x {Np} chains x {T} iterations, FP64 C oracle, one channel per "
+                      f"thread", "seconds": dt, "channels": len(idx),
             "detections_per_s": len(idx) / dt}
+
+
+def clopper_pearson(k: int, n: int, conf: float = 0.95):
+    """Exact binomial interval of a proportion k / n."""
+    from scipy.stats import beta
+    a = (1.0 - conf) / 2.0
+    lo = float(beta.ppf(a, k, n - k + 1)) if k > 0 else 0.0
+    hi = float(beta.ppf(1.0 - a, k + 1, n - k)) if k < n else 1.0
+    return lo, hi
+
+
+def equal_ber(ber_a, ber_b):
+    """Per SNR point: is form a's BER of sign(LLR) inside the 95% Clopper-Pearson interval of
+    form b's (same bits, same seed)?"""
+    out = {}
+    for k, vb in ber_b.items():
+        va = ber_a.get(k)
+        if va is None:
+            continue
+        n = vb["bits"]
+        lo, hi = clopper_pearson(int(round(vb["ber_llr"] * n)), n)
+        out[k] = {"ber": va["ber_llr"], "ber_plain_fp32": vb["ber_llr"], "interval": [lo, hi],
+                  "inside": bool(lo <= va["ber_llr"] <= hi)}
+    return {"all_inside": all(v["inside"] for v in out.values()), "points": out}
+
+
+def ber_sweep(args, batch, w, pkg, torch, dev, stream, make):
+    """BER of sign(LLR) against the number of transitions at the workload's highest SNR point
+    (the metric's BER <= 1e-3 qualifier): this form at several T, with its detections/s, and the
+    plain FP32 sampler at one of them for the equal-BER check."""
+    top = max(batch.snr_db.tolist())
+    idx = [i for i in range(batch.n_channels) if batch.snr_db[i] == top]
+    sub = batch.subset(idx)
+    Hs = torch.from_numpy(np.ascontiguousarray(sub.H).view(np.float32).copy()).to(dev)
+    ys = torch.from_numpy(np.ascontiguousarray(sub.y).view(np.float32).copy()).to(dev)
+    ss = torch.from_numpy(sub.sigma2.astype(np.float32)).to(dev)
+    n_ant = int(sub.nt.sum())
+    n_bits = int((sub.nt.astype(np.int64) * np.log2(sub.qam).astype(np.int64)).sum())
+    oi = torch.empty(n_ant, dtype=torch.int8, device=dev)
+    ol = torch.empty(n_bits, dtype=torch.float32, device=dev)
+    ob = torch.empty(sub.n_channels, dtype=torch.float64, device=dev)
+    res = {"snr_db": top, "channels": sub.n_channels, "points": []}
+    for prec, Ts in (("mixed", (w["iterations"], 1000, 5000, 20000)), ("fp32", (5000,))):
+        det = pkg.Detector(max_channels=sub.n_channels, max_nt=int(sub.nt.max()),
+                           max_nr=int(sub.nr.max()), chains=w["chains"], precision=prec, seed=0,
+                           stream=stream)
+        for T in Ts:
+            det.preprocess(sub.nt, sub.nr, sub.qam, Hs, sub.H_off, ys, sub.y_off, ss)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            det.preprocess(sub.nt, sub.nr, sub.qam, Hs, sub.H_off, ys, sub.y_off, ss)
+            det.run_chains(T)
+            det.estimate(oi, ol, ob, host_io=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            b = ber_of(sub, ol.cpu().numpy(), oi.cpu().numpy())[f"{top:g}"]
+            st = det.estimate(stats=True)["stats"]
+            res["points"].append({"precision": prec, "iterations": T, "ber_llr": b["ber_llr"],
+                                  "ber_best": b["ber_best"], "bits": b["bits"],
+                                  "accept_rate": st["accepts"] / max(1, st["transitions"]),
+                                  "ms": e0.elapsed_time(e1),
+                                  "detections_per_s": sub.n_channels / (e0.elapsed_time(e1) * 1e-3)})
+        det.destroy()
+    res["reaches_1e-3"] = [p for p in res["points"] if p["ber_llr"] <= 1e-3]
+    return res
 
 
 def bench_config(args, w, n_channels, world, refresh, l2_note=None):
@@ -338,9 +445,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     batch, w = load_batch(args.scale, 0, args.workload)
+    # one sample for every step (whole waves of the host cores), each step a few seconds at most
+    budget = min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup))
+    idx, _ = cpu_sample(batch, w, budget)
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(batch, w, args.cpu_seconds / max(1, args.steps), 0)
+        r = cpu_baseline(batch, w, budget, 0, idx=idx)
         if i >= args.warmup:
             vals.append(r)
     v = float(np.mean([r["value"] for r in vals]))
@@ -351,10 +461,11 @@ def run_reference(args, rank, world):
             "ms_per_step": 1e3 * float(np.mean([r["seconds"] for r in vals])),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": bench_config(args, w, batch.n_channels, world,
-                                   args.refresh if args.refresh is not None else
-                                   (50 if w["kind"] == "kronecker" else 0),
-                                   "host-resident oracle (no device)"),
+            "config": dict(bench_config(args, w, len(idx), world,
+                                        args.refresh if args.refresh is not None else
+                                        (50 if w["kind"] == "kronecker" else 0),
+                                        "host-resident oracle (no device)"),
+                           sample_of_channels=batch.n_channels),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -632,7 +743,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--compare-fp32", action="store_true", help="also time the plain FP32 sampler")
+    ap.add_argument("--compare-fp32", dest="compare_fp32", action="store_true", default=None,
+                    help="also time the plain FP32 sampler (default for the headline workload)")
+    ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false")
+    ap.add_argument("--no-ber-sweep", action="store_true",
+                    help="skip the BER-vs-iterations sweep at the highest SNR point")
     ap.add_argument("--compare-llr", type=float, default=0.0, metavar="CLIP",
                     help="also time the list-based LLR (Eq. (31), clipped at CLIP) on the final "
                          "states and report its BER beside the IS-LLR's")
@@ -753,6 +868,16 @@ def main():
     idx = o_idx.cpu().numpy()
     ber = ber_of(batch, llr, idx)
     ber_ok = [k for k, v in ber.items() if v["ber_llr"] <= 1e-3]
+    # chain statistics of the last timed step (its preprocess reset them): acceptance rate, the
+    # kernel-counted near-ties of the MH test, the correction the final exact refresh made
+    st = det.estimate(stats=True)["stats"]
+    chain_stats = {"accept_rate": st["accepts"] / max(1, st["transitions"]),
+                   "transitions": st["transitions"],
+                   "near_ties": dict(zip(["lt_1e-6", "lt_1e-4", "lt_1e-2"], st["near_ties"])),
+                   "near_ties_per_1e6": {k: v * 1e6 / max(1, st["transitions"]) for k, v in
+                                         zip(["lt_1e-6", "lt_1e-4", "lt_1e-2"], st["near_ties"])},
+                   "refresh_drift_abs": st["refresh_drift"],
+                   "refresh_drift_rel": st["refresh_drift_rel"]}
 
     # end to end through the C ABI with host buffers: H2D of the inputs and D2H of the outputs
     # inside the timed region, every step
@@ -803,14 +928,24 @@ def main():
                     "ber_is": {k: v["ber_llr"] for k, v in ber.items()}}
 
     fp32_line = None
-    if args.compare_fp32 and precision != "fp32":
+    compare = args.compare_fp32 if args.compare_fp32 is not None else (
+        precision == "mixed" and args.workload == WORKLOAD)
+    if compare and precision != "fp32":
+        # the plain FP32 GPU sampler (CUDA cores, autotuned tile) on the same batch and seed:
+        # the metric's comparison arm
         d32 = make("fp32")
-        ms32, kms32, _, _ = timed(d32, max(1, args.steps // 2), 1)
+        ms32, kms32, _, clk32 = timed(d32, max(1, args.steps // 2), min(args.warmup, 2))
         ber32 = ber_of(batch, o_llr.cpu().numpy(), o_idx.cpu().numpy())
         fp32_line = {"value": units_rank * world / (ms32 * 1e-3), "ms_per_step": ms32,
-                     "chain_kernel_ms": kms32, "ber": ber32,
+                     "chain_kernel_ms": kms32, "detections_per_s": B * world / (ms32 * 1e-3),
+                     "ber": ber32, "clocks": clk32,
+                     "equal_ber": equal_ber(ber, ber32),
                      "roofline": chain_roofline("fp32", w, units_rank, kms32, batch)}
         d32.destroy()
+
+    sweep = None
+    if compare and not args.no_ber_sweep and precision == "mixed":
+        sweep = ber_sweep(args, batch, w, pkg, torch, dev, stream, make)
 
     roofline = chain_roofline(precision, w, units_rank, chain_ms, batch)
 
@@ -829,11 +964,19 @@ def main():
                 "precision": precision, "graph": bool(args.graph), "engine": args.engine,
                 "detections_per_s": det_per_s, "chain_kernel_ms": chain_ms,
                 "readout_ms": readout_ms,
-                "ber": ber, "snr_points_at_ber_le_1e-3": ber_ok,
+                "ber": ber, "snr_points_at_ber_le_1e-3": ber_ok, "chain_stats": chain_stats,
                 "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
                 "e2e": e2e, "cpu_baseline": cb}
         if fp32_line:
             line["plain_fp32"] = fp32_line
+            line["vs_baseline"] = value / fp32_line["value"]
+            line["vs_baseline_definition"] = (
+                "chain-iterations/s of this form over the plain FP32 GPU sampler's on the same "
+                "batch, seed and GPU, measured in this run (the metric's 'vs plain FP32'); both "
+                "reach the same BER within the 95% Clopper-Pearson interval per SNR point "
+                "(plain_fp32.equal_ber)")
+        if sweep:
+            line["ber_vs_iterations"] = sweep
         if llr_line:
             line["list_llr"] = llr_line
         print(json.dumps(line), flush=True)

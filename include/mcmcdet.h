@@ -79,11 +79,16 @@ typedef struct {
     int32_t chains;         /* Np, a multiple of 4, 4..1024 */
     int32_t precision;      /* mcmc_prec */
     int32_t preconditioned; /* 1: Remark 1 proposal (the paper's evaluation setting), 0: plain */
-    int32_t refresh_period; /* R > 0: recompute every chain's energy in FP64 every R transitions
-                               (FP32/MIXED; FP64 mode is exact throughout); 0: never during a run */
+    int32_t refresh_period; /* FP32 / MIXED energies (FP64 mode is exact throughout): the chains
+                               add FP32 energy differences to the last exact value. R >= 0: every
+                               run_chains ends with an exact evaluation of the energies (so the
+                               read-outs see exact values); R > 0 also refreshes them every R
+                               transitions inside the run; R = -1: never (the tracked values
+                               drift; for measuring that drift) */
     int32_t split_terms;    /* MIXED: BF16 terms G is split into (2 = hi+lo, 3 = hi+lo+lo2) */
     int32_t engine;         /* MCMC_ENGINE_AUTO (autotuned per shape class), _SIMT or _TC, optionally
-                               OR-ed with MCMC_ENGINE_GRAPH and MCMC_ENGINE_NO_CLUSTER */
+                               OR-ed with MCMC_ENGINE_GRAPH, MCMC_ENGINE_NO_CLUSTER and
+                               MCMC_ENGINE_TRACE */
     int32_t tile;           /* with an explicit engine: chains per work item (TC: 16 or 32, and 64
                                for channels with N = 2 Nt > 128, which run on thread-block
                                clusters; SIMT: a multiple of 8, at most 64); 0: the engine's
@@ -106,14 +111,24 @@ typedef struct {
                                     which streams the Gram operand from L2 every transition,
                                     instead of a thread-block cluster with one resident operand
                                     tile per CTA */
+#define MCMC_ENGINE_TRACE 16    /* flag: every chain records the log acceptance ratio and the log
+                                   uniform of its latest transition (Eq. (18)), read back with
+                                   mcmc_detect_get_trace (parity diagnostics; one extra store per
+                                   chain and transition) */
 
 /* Per-batch statistics (host struct, filled by mcmc_detect_estimate when non-NULL). */
 typedef struct {
     int64_t transitions;    /* chain transitions performed since preprocess */
     int64_t accepts;        /* accepted proposals since preprocess */
-    int32_t numeric_faults; /* chains that met a non-finite value */
-    int32_t reserved;
-    double refresh_drift;   /* max |f_tracked - f_fp64| seen at FP64 refreshes (FP32/MIXED) */
+    int32_t numeric_faults; /* 1 if a chain met a non-finite value since preprocess, else 0 */
+    int32_t near_tie_windows; /* entries of near_ties (3) */
+    double refresh_drift;   /* max |f_tracked - f_exact| seen at refreshes (FP32/MIXED): the
+                               largest correction an exact evaluation made */
+    int64_t near_ties[3];   /* Metropolis-Hastings decisions (Eq. (18)) since preprocess whose
+                               |log A - log u|, as the chain kernel evaluated it in its own
+                               precision, was below 1e-6, 1e-4 and 1e-2 (natural log): the
+                               decisions a rounding difference of that size could flip */
+    double refresh_drift_rel; /* max |f_tracked - f_exact| / |f_exact| seen at refreshes */
 } mcmc_stats;
 
 /* Fills *cfg with defaults: 1 channel, Nt = Nr = 4, 32 chains, FP32, preconditioned, R = 0,
@@ -172,10 +187,27 @@ mcmc_status mcmc_detect_llr_list(mcmc_detector *d, float *llr, float clip, int32
 
 /* Chain state export: states [sum over channels Np*N_b] int8 level indices, channel-major, then
  * chain-major (chain c of channel b at offset Np*sum_{b'<b} N_b' + c*N_b); f [n_channels*Np]
- * untempered energies of those states, FP64 evaluations (FP32 and MIXED runs track them in FP32
- * steps and they are recomputed in FP64 before they are handed out). Host or device pointers
- * per host_io. Synchronises. */
+ * untempered energies f = -||y - Hx||^2 / sigma^2 (Eq. (3)) of those states, FP64 evaluations.
+ * Either may be NULL. The call changes nothing in the handle: FP32 and MIXED runs track their
+ * energies in FP32 steps (see mcmc_detect_get_tracked), and the FP64 evaluations handed out here
+ * are computed beside them. Host or device pointers per host_io. Synchronises. */
 mcmc_status mcmc_detect_get_chains(mcmc_detector *d, int8_t *states, double *f, int32_t host_io);
+
+/* The energies the chains track, as they hold them: f [n_channels*Np] of the current states and
+ * best_f [n_channels*Np] of each chain's best visited state (the running maximum, Sec. III-A),
+ * untempered, layout as in get_chains; either may be NULL. FP64 handles track them exactly; FP32
+ * and MIXED runs add FP32 energy differences (Algorithm 1's MH ratio) to the value of the last
+ * FP64 evaluation (the first run's initial energies, or the latest refresh, see refresh_period).
+ * These are the values the IS-LLR of mcmc_detect_estimate and the hard decision read. Before the
+ * first run the initial states' FP64 evaluations are returned. Changes nothing in the handle.
+ * Host or device pointers per host_io. Synchronises. */
+mcmc_status mcmc_detect_get_tracked(mcmc_detector *d, double *f, double *best_f, int32_t host_io);
+
+/* Handles created with MCMC_ENGINE_TRACE: trace [2*n_channels*Np] doubles, per chain (layout as
+ * get_chains' f) the log acceptance ratio log(pi(x')q(x|x') / (pi(x)q(x'|x))) and log u of its
+ * latest Metropolis-Hastings test (Eq. (18), tempered target, natural log) as the chain kernel
+ * computed them (0, 0 before the first run). MCMC_ESTATE without the flag. Synchronises. */
+mcmc_status mcmc_detect_get_trace(mcmc_detector *d, double *trace, int32_t host_io);
 
 /* Chain state import (checkpoint restore, or any start point): same layout as get_chains; every
  * level must lie in [0, L_b). Energies are recomputed in FP64. */
@@ -215,8 +247,9 @@ int64_t mcmc_detect_kernel_launches(const mcmc_detector *d);
  *  or NULL for the default stream. The call synchronises that stream before returning.
  * Errors: MCMC_EINVAL for bad arguments and for a batch whose intermediate buffers need more than
  * MCMC_NOALLOC_SCRATCH_BYTES (checked before any work is enqueued); device faults as in estimate.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current: make that first call before any stream capture begins.
+ * The first call in a CUDA context (per device, and again after cudaDeviceReset) looks up the
+ * array's device address (cudaGetSymbolAddress) with that context current: make that first call
+ * before any stream capture begins.
  * Every call shares the array and leaves its contents behind; each call re-initialises what it
  * reads, and calls that overlap on the GPU (other threads, other streams) race with each other. */
 mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt, const int32_t *nr,

@@ -20,13 +20,14 @@ from . import build as _build
 __all__ = [
     "Detector", "Config", "Stats", "lib", "load", "MCMC_PREC_FP64", "MCMC_PREC_FP32",
     "MCMC_PREC_MIXED", "MCMC_ENGINE_AUTO", "MCMC_ENGINE_SIMT", "MCMC_ENGINE_TC",
-    "MCMC_ENGINE_GRAPH", "MCMC_ENGINE_NO_CLUSTER", "McmcError", "Mlp",
+    "MCMC_ENGINE_GRAPH", "MCMC_ENGINE_NO_CLUSTER", "MCMC_ENGINE_TRACE", "McmcError", "Mlp",
     "ABI_FUNCTIONS", "ABI_FUNCTIONS_LEARNED", "ABI_FUNCTIONS_DIAG", "transition_diagnostics",
 ]
 
 MCMC_PREC_FP64, MCMC_PREC_FP32, MCMC_PREC_MIXED = 0, 1, 2
 MCMC_ENGINE_AUTO, MCMC_ENGINE_SIMT, MCMC_ENGINE_TC, MCMC_ENGINE_GRAPH = 0, 1, 2, 4
 MCMC_ENGINE_NO_CLUSTER = 8
+MCMC_ENGINE_TRACE = 16
 _PREC = {"fp64": MCMC_PREC_FP64, "fp32": MCMC_PREC_FP32, "mixed": MCMC_PREC_MIXED}
 STATUS = {0: "MCMC_OK", 1: "MCMC_EINVAL", 2: "MCMC_ENOMEM", 3: "MCMC_ECUDA", 4: "MCMC_ETIMEOUT",
           5: "MCMC_ENUMERIC", 6: "MCMC_ESTATE", 7: "MCMC_EUNSUPPORTED"}
@@ -37,7 +38,8 @@ ABI_FUNCTIONS = [
     "mcmc_detect_run_chains", "mcmc_detect_estimate", "mcmc_detect_get_chains",
     "mcmc_detect_set_chains", "mcmc_detect_synchronize", "mcmc_detect_destroy",
     "mcmc_status_string", "mcmc_detect_last_error", "mcmc_detect_kernel_launches",
-    "mcmc_detect_noalloc", "mcmc_detect_llr_list",
+    "mcmc_detect_noalloc", "mcmc_detect_llr_list", "mcmc_detect_get_tracked",
+    "mcmc_detect_get_trace",
 ]
 
 # Every entry point of include/mcmcdet_learned.h.
@@ -73,8 +75,9 @@ class Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     """Mirror of ``mcmc_stats``."""
     _fields_ = [("transitions", ctypes.c_int64), ("accepts", ctypes.c_int64),
-                ("numeric_faults", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("refresh_drift", ctypes.c_double)]
+                ("numeric_faults", ctypes.c_int32), ("near_tie_windows", ctypes.c_int32),
+                ("refresh_drift", ctypes.c_double), ("near_ties", ctypes.c_int64 * 3),
+                ("refresh_drift_rel", ctypes.c_double)]
 
 
 _lib = None
@@ -103,6 +106,10 @@ def load(path: Optional[str] = None):
     l.mcmc_detect_llr_list.argtypes = [vp, vp, ctypes.c_float, i32]
     l.mcmc_detect_llr_list.restype = ctypes.c_int
     l.mcmc_detect_get_chains.restype = ctypes.c_int
+    l.mcmc_detect_get_tracked.argtypes = [vp, vp, vp, i32]
+    l.mcmc_detect_get_tracked.restype = ctypes.c_int
+    l.mcmc_detect_get_trace.argtypes = [vp, vp, i32]
+    l.mcmc_detect_get_trace.restype = ctypes.c_int
     l.mcmc_detect_set_chains.argtypes = [vp, vp, i32]
     l.mcmc_detect_set_chains.restype = ctypes.c_int
     l.mcmc_detect_synchronize.argtypes = [vp]
@@ -261,7 +268,11 @@ class Detector:
         out = dict(best_idx=best_idx, llr=llr, best_f=best_f)
         if stats:
             out["stats"] = dict(transitions=s.transitions, accepts=s.accepts,
-                                refresh_drift=s.refresh_drift)
+                                refresh_drift=s.refresh_drift,
+                                refresh_drift_rel=s.refresh_drift_rel,
+                                numeric_faults=s.numeric_faults,
+                                near_ties=[int(v) for v in s.near_ties],
+                                near_tie_windows=[1e-6, 1e-4, 1e-2])
         return out
 
     def llr_list(self, clip: float, llr=None, *, host_io: Optional[bool] = None):
@@ -284,6 +295,28 @@ class Detector:
             host_io = _is_host(states if states is not None else f)
         self._check(self._l.mcmc_detect_get_chains(self._h, _ptr(states), _ptr(f), int(host_io)))
         return states, f
+
+    def get_tracked(self, f=None, best_f=None, *, host_io: Optional[bool] = None):
+        """Tracked energies of the current states and of each chain's best visited state, as
+        the chains hold them (no FP64 re-evaluation); new host arrays when none are given."""
+        if f is None and best_f is None:
+            n = self.batch_meta["n_channels"] * self.cfg.chains
+            f = np.zeros(n, np.float64)
+            best_f = np.zeros(n, np.float64)
+        if host_io is None:
+            host_io = _is_host(f if f is not None else best_f)
+        self._check(self._l.mcmc_detect_get_tracked(self._h, _ptr(f), _ptr(best_f), int(host_io)))
+        return f, best_f
+
+    def get_trace(self, trace=None, *, host_io: Optional[bool] = None):
+        """Per chain [log acceptance ratio, log u] of its latest transition (handles created with
+        MCMC_ENGINE_TRACE); a new host array [n_channels * chains, 2] when none is given."""
+        if trace is None:
+            trace = np.zeros((self.batch_meta["n_channels"] * self.cfg.chains, 2), np.float64)
+        if host_io is None:
+            host_io = _is_host(trace)
+        self._check(self._l.mcmc_detect_get_trace(self._h, _ptr(trace), int(host_io)))
+        return trace
 
     def set_chains(self, states, *, host_io: Optional[bool] = None):
         if host_io is None:

@@ -86,7 +86,7 @@ struct mcmc_detector {
     // device workspace
     DevBuf d_desc, d_Gc, d_zc, d_Mc, d_gj, d_yy, d_G64, d_GM64, d_z64, d_w64, d_z32,
         d_w32, d_bt32, d_bt64, d_tc, d_states, d_best_states, d_f, d_best_f, d_accepts,
-        d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp;
+        d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp, d_fx, d_trace;
     HostBuf h_stage;
     // pinned staging ring for the per-batch tables (descriptors, work items): a slot is rewritten
     // only after the copy that last read it has completed
@@ -202,7 +202,9 @@ cudaError_t h2d(mcmc_detector *d, void *dst, const void *src, size_t bytes, size
                            cudaMemcpyHostToDevice, d->stream);
 }
 
-mcmc_status ensure_energies(mcmc_detector *d, bool exact = true);
+mcmc_status ensure_energies(mcmc_detector *d);
+mcmc_status fp64_energies(mcmc_detector *d, const double **out);
+mcmc_status refresh_energies(mcmc_detector *d, double *f, bool reset_best, bool measure);
 
 mcmc_status read_status(mcmc_detector *d)
 {
@@ -216,9 +218,12 @@ mcmc_status read_status(mcmc_detector *d)
     return MCMC_OK;
 }
 
-// misc block layout: [0] status (unsigned), [8] drift bits (u64), [16] accept total (u64)
+// misc block layout: [0] status (unsigned), [8] drift bits (u64), [16] relative drift bits (u64),
+// [32] near-tie counts (3 x u64)
 unsigned *status_ptr(mcmc_detector *d) { return P<unsigned>(d->d_misc); }
 unsigned long long *drift_ptr(mcmc_detector *d) { return reinterpret_cast<unsigned long long *>(P<char>(d->d_misc) + 8); }
+unsigned long long *drift_rel_ptr(mcmc_detector *d) { return reinterpret_cast<unsigned long long *>(P<char>(d->d_misc) + 16); }
+unsigned long long *ties_ptr(mcmc_detector *d) { return reinterpret_cast<unsigned long long *>(P<char>(d->d_misc) + 32); }
 
 __global__ void finalize_desc_kernel(ChannelDesc *desc, const float *noise_var, int n,
                                      double alpha_scale, double tau, int preconditioned,
@@ -255,50 +260,58 @@ __global__ void finalize_desc_kernel(ChannelDesc *desc, const float *noise_var, 
 
 namespace {
 
-// FP64 energies of the current states (and a restart of the running best) when the tracked
-// energies are not valid yet: FP32 / MIXED handles read after preprocess or set_chains without a
-// run in between.
-mcmc_status ensure_energies(mcmc_detector *d, bool exact)
+// Energies of the current states, evaluated exactly (refresh.cu) into `f`: the tracked energies
+// (d_f) or a scratch buffer. reset_best restarts every chain's running best at its current state;
+// measure records the correction made to the tracked values in the drift statistics.
+mcmc_status refresh_energies(mcmc_detector *d, double *f, bool reset_best, bool measure)
 {
-    if (d->f_valid && !d->f_exact && exact) {
-        // energies handed out are FP64 evaluations of the current states; the running best
-        // (a state, re-evaluated in FP64 by the read-out) is kept
-        RefreshArgs ra{};
-        ra.desc = P<ChannelDesc>(d->d_desc);
-        ra.states = P<int8_t>(d->d_states);
-        ra.G64 = P<double>(d->d_G64);
-        ra.z64 = P<double>(d->d_z64);
-        ra.yy = P<double>(d->d_yy);
-        ra.f = P<double>(d->d_f);
-        ra.best_f = P<double>(d->d_best_f);
-        ra.best_states = P<int8_t>(d->d_best_states);
-        ra.status = status_ptr(d);
-        ra.n_channels = d->n_channels;
-        ra.chains = d->cfg.chains;
-        ra.reset_best = 0;
-        CK(launch_refresh(ra, d->stream), "energies");
-        d->launches++;
-        d->f_exact = true;
-        return MCMC_OK;
-    }
-    if (d->f_valid) return MCMC_OK;
     RefreshArgs ra{};
     ra.desc = P<ChannelDesc>(d->d_desc);
     ra.states = P<int8_t>(d->d_states);
     ra.G64 = P<double>(d->d_G64);
     ra.z64 = P<double>(d->d_z64);
     ra.yy = P<double>(d->d_yy);
-    ra.f = P<double>(d->d_f);
-    ra.best_f = P<double>(d->d_best_f);
-    ra.best_states = P<int8_t>(d->d_best_states);
+    ra.f = f;
+    ra.best_f = reset_best ? P<double>(d->d_best_f) : nullptr;
+    ra.best_states = reset_best ? P<int8_t>(d->d_best_states) : nullptr;
     ra.status = status_ptr(d);
     ra.n_channels = d->n_channels;
     ra.chains = d->cfg.chains;
-    ra.reset_best = 1;
+    ra.reset_best = reset_best ? 1 : 0;
+    ra.max_n = d->max_n;
+    ra.drift_bits = measure ? drift_ptr(d) : nullptr;
+    ra.drift_rel_bits = measure ? drift_rel_ptr(d) : nullptr;
     CK(launch_refresh(ra, d->stream), "energies");
     d->launches++;
+    return MCMC_OK;
+}
+
+// Exact energies of the current states (and a restart of the running best) when the tracked
+// energies are not valid: after a warm start without a run in between.
+mcmc_status ensure_energies(mcmc_detector *d)
+{
+    if (d->f_valid) return MCMC_OK;
+    mcmc_status st = refresh_energies(d, P<double>(d->d_f), true, false);
+    if (st != MCMC_OK) return st;
     d->f_valid = true;
     d->f_exact = true;
+    return MCMC_OK;
+}
+
+// Exact evaluations of the current states' energies for read-outs that need them. When the tracked
+// energies are exact they are handed out directly; otherwise the values are computed into a
+// scratch buffer and the tracked energies (which the IS-LLR and the running best read) stay as the
+// chains left them.
+mcmc_status fp64_energies(mcmc_detector *d, const double **out)
+{
+    if (d->f_valid && d->f_exact) {
+        *out = P<double>(d->d_f);
+        return MCMC_OK;
+    }
+    CK(ensure(d->d_fx, 8 * (size_t)d->n_channels * d->cfg.chains), "alloc FP64 energies");
+    mcmc_status st = refresh_energies(d, P<double>(d->d_fx), false, false);
+    if (st != MCMC_OK) return st;
+    *out = P<double>(d->d_fx);
     return MCMC_OK;
 }
 
@@ -431,6 +444,8 @@ ChainArgs chain_args(mcmc_detector *d, int32_t iterations, int64_t t_offset)
     ca.split_terms = d->cfg.split_terms;
     ca.init_f = d->f_valid ? 0 : 1;
     ca.dexp = fp64 ? nullptr : P<float>(d->d_dexp);
+    ca.near_ties = ties_ptr(d);
+    ca.trace = (d->cfg.engine & MCMC_ENGINE_TRACE) ? P<double>(d->d_trace) : nullptr;
     return ca;
 }
 
@@ -509,6 +524,8 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
                                cudaMemcpyHostToDevice, d->stream), "copy probe items");
             ChainArgs ca = chain_args(d, 2, 0);
             ca.init_f = 1;
+            ca.near_ties = nullptr;   // probe transitions are not the batch's
+            ca.trace = nullptr;
             cudaError_t e = launch_group(d, g, ca);                 // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
             ca.iterations = 24;   // long enough to amortise per-item set-up (streamed operands)
@@ -598,9 +615,10 @@ mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out)
     if (cfg->max_channels < 1 || cfg->max_nt < 1 || 2 * cfg->max_nt > kMaxN || cfg->max_nr < 1 ||
         cfg->max_nr > 4096 || cfg->chains < 4 || cfg->chains > 1024 || (cfg->chains % 4) != 0 ||
         cfg->precision < MCMC_PREC_FP64 || cfg->precision > MCMC_PREC_MIXED ||
-        (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < 0 ||
+        (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < -1 ||
         cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 ||
-        (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH | MCMC_ENGINE_NO_CLUSTER)) != 0 || (cfg->engine & 3) == 3 ||
+        (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH | MCMC_ENGINE_NO_CLUSTER | MCMC_ENGINE_TRACE)) != 0 ||
+        (cfg->engine & 3) == 3 ||
         cfg->tile < 0 || (cfg->tile != 0 && (cfg->engine & 3) == MCMC_ENGINE_AUTO) ||
         ((cfg->engine & 3) == MCMC_ENGINE_TC && cfg->tile != 0 && cfg->tile != 16 && cfg->tile != 32 &&
          cfg->tile != 64) ||
@@ -651,6 +669,7 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
                       &d->d_bt32, &d->d_bt64, &d->d_tc, &d->d_states, &d->d_best_states, &d->d_f,
                       &d->d_best_f, &d->d_accepts, &d->d_misc, &d->d_in_H, &d->d_in_y,
                       &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf, &d->d_dexp,
+                      &d->d_fx, &d->d_trace,
                       &d->d_mx_gx, &d->d_mx_px, &d->d_mx_gxp, &d->d_mx_pxp, &d->d_mx_prop,
                       &d->d_mx_X, &d->d_mx_logits, &d->d_mx_lqf};
     for (DevBuf *b : bufs)
@@ -802,6 +821,10 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
     CK(ensure(d->d_best_f, 8 * (size_t)n_channels * Np), "alloc best f");
     CK(ensure(d->d_accepts, 8 * (size_t)n_channels * Np), "alloc accepts");
     if (!fp64) CK(ensure(d->d_dexp, 4 * (size_t)st), "alloc Gt x export");
+    if (d->cfg.engine & MCMC_ENGINE_TRACE) {
+        CK(ensure(d->d_trace, 16 * (size_t)n_channels * Np), "alloc trace");
+        CK(cudaMemsetAsync(d->d_trace.p, 0, 16 * (size_t)n_channels * Np, d->stream), "reset trace");
+    }
 
     // inputs
     const float2 *Hd = static_cast<const float2 *>(H);
@@ -892,25 +915,13 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
         if (gs != MCMC_OK) return gs;
     }
 
-    RefreshArgs ra{};
-    ra.desc = P<ChannelDesc>(d->d_desc);
-    ra.states = P<int8_t>(d->d_states);
-    ra.G64 = P<double>(d->d_G64);
-    ra.z64 = P<double>(d->d_z64);
-    ra.yy = P<double>(d->d_yy);
-    ra.f = P<double>(d->d_f);
-    ra.best_f = P<double>(d->d_best_f);
-    ra.best_states = P<int8_t>(d->d_best_states);
-    ra.status = status_ptr(d);
-    ra.n_channels = n_channels;
-    ra.chains = Np;
-    ra.reset_best = 1;
-    if (fp64) {
-        CK(launch_refresh(ra, d->stream), "initial energies");
-        d->launches++;
+    // exact energies of the initial states (every precision); the running best starts there
+    {
+        mcmc_status es = refresh_energies(d, P<double>(d->d_f), true, false);
+        if (es != MCMC_OK) return es;
     }
-    // FP32 / MIXED: the first run derives the energies from its first GEMM
-    d->f_valid = fp64;
+    d->f_valid = true;
+    d->f_exact = true;
     d->d_valid = false;
     d->transitions = 0;
     d->prepared = true;
@@ -927,12 +938,32 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
     if (iterations == 0) return MCMC_OK;
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
     const ChainArgs ca = chain_args(d, iterations, t_offset);
+    // FP32 / MIXED: the energies the chains tracked in FP32 steps are replaced by exact
+    // evaluations when the run ends (refresh_period >= 0), and the correction is recorded
+    const bool final_refresh = !fp64 && d->cfg.refresh_period >= 0;
+    RefreshArgs fr{};
+    if (final_refresh) {
+        fr.desc = P<ChannelDesc>(d->d_desc);
+        fr.states = P<int8_t>(d->d_states);
+        fr.G64 = P<double>(d->d_G64);
+        fr.z64 = P<double>(d->d_z64);
+        fr.yy = P<double>(d->d_yy);
+        fr.f = P<double>(d->d_f);
+        fr.status = status_ptr(d);
+        fr.n_channels = d->n_channels;
+        fr.chains = d->cfg.chains;
+        fr.max_n = d->max_n;
+        fr.drift_bits = drift_ptr(d);
+        fr.drift_rel_bits = drift_rel_ptr(d);
+    }
     if (d->cfg.engine & MCMC_ENGINE_GRAPH) {
-        // every group's launch captured into one graph, replayed on the handle's stream
+        // every group's launch (and the final refresh) captured into one graph, replayed on the
+        // handle's stream
         CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t le = cudaSuccess;
         for (const Group &g : d->groups)
             if (le == cudaSuccess) le = launch_group(d, g, ca);
+        if (le == cudaSuccess && final_refresh) le = launch_refresh(fr, d->stream);
         cudaGraph_t graph = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(d->stream, &graph);
         if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(d, le, "chain kernel"); }
@@ -953,15 +984,19 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         }
         cudaGraphDestroy(graph);
         CK(cudaGraphLaunch(d->graph, d->stream), "graph launch");
-        d->launches += (long long)d->groups.size();
+        d->launches += (long long)d->groups.size() + (final_refresh ? 1 : 0);
     } else {
         for (const Group &g : d->groups) {
             CK(launch_group(d, g, ca), g.engine == MCMC_ENGINE_TC ? "tensor-core chain kernel" : "chain kernel");
             d->launches++;
         }
+        if (final_refresh) {
+            CK(launch_refresh(fr, d->stream), "final energies");
+            d->launches++;
+        }
     }
     d->f_valid = true;
-    d->f_exact = fp64;
+    d->f_exact = fp64 || final_refresh;
     d->d_valid = !fp64;
     d->transitions += (long long)iterations * d->n_channels * d->cfg.chains;
     return MCMC_OK;
@@ -976,7 +1011,7 @@ mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr,
     if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
     {
-        mcmc_status es = ensure_energies(d, false);
+        mcmc_status es = ensure_energies(d);
         if (es != MCMC_OK) return es;
     }
     int8_t *o_idx = best_idx;
@@ -1027,6 +1062,16 @@ mcmc_status mcmc_detect_estimate(mcmc_detector *d, int8_t *best_idx, float *llr,
         double dr;
         std::memcpy(&dr, &db, 8);
         stats->refresh_drift = dr;
+        CK(cudaMemcpy(&db, drift_rel_ptr(d), 8, cudaMemcpyDeviceToHost), "copy drift");
+        std::memcpy(&dr, &db, 8);
+        stats->refresh_drift_rel = dr;
+        unsigned long long ties[3] = {0, 0, 0};
+        CK(cudaMemcpy(ties, ties_ptr(d), sizeof ties, cudaMemcpyDeviceToHost), "copy near ties");
+        for (int k = 0; k < 3; ++k) stats->near_ties[k] = (int64_t)ties[k];
+        unsigned stw = 0;
+        CK(cudaMemcpy(&stw, status_ptr(d), sizeof stw, cudaMemcpyDeviceToHost), "copy status");
+        stats->numeric_faults = (stw & kStatusNumeric) ? 1 : 0;
+        stats->near_tie_windows = 3;
     }
     return s;
 }
@@ -1039,8 +1084,9 @@ mcmc_status mcmc_detect_llr_list(mcmc_detector *d, float *llr, float clip, int32
     if (!llr) return fail(d, MCMC_EINVAL, "null llr");
     if (!(clip > 0.f) || !std::isfinite(clip)) return fail(d, MCMC_EINVAL, "clip must be > 0 and finite");
     if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    const double *fx = nullptr;   // FP64 energies of the current states
     {
-        mcmc_status es = ensure_energies(d, true);   // FP64 energies of the current states
+        mcmc_status es = fp64_energies(d, &fx);
         if (es != MCMC_OK) return es;
     }
     float *o_llr = llr;
@@ -1051,7 +1097,7 @@ mcmc_status mcmc_detect_llr_list(mcmc_detector *d, float *llr, float clip, int32
     ListLlrArgs la{};
     la.desc = P<ChannelDesc>(d->d_desc);
     la.states = P<int8_t>(d->d_states);
-    la.f = P<double>(d->d_f);
+    la.f = fx;
     la.n_channels = d->n_channels;
     la.chains = d->cfg.chains;
     la.clip = clip;
@@ -1069,13 +1115,51 @@ mcmc_status mcmc_detect_get_chains(mcmc_detector *d, int8_t *states, double *f, 
     d->err.clear();
     if (!d->prepared) return fail(d, MCMC_ESTATE, "get_chains before preprocess");
     if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
-    {
-        mcmc_status es = ensure_energies(d);
+    const double *fx = nullptr;
+    if (f) {
+        mcmc_status es = fp64_energies(d, &fx);
         if (es != MCMC_OK) return es;
     }
     const cudaMemcpyKind k = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (states) CK(cudaMemcpyAsync(states, d->d_states.p, d->tot_states, k, d->stream), "copy states");
-    if (f) CK(cudaMemcpyAsync(f, d->d_f.p, 8 * (size_t)d->n_channels * d->cfg.chains, k, d->stream), "copy f");
+    if (f) CK(cudaMemcpyAsync(f, fx, 8 * (size_t)d->n_channels * d->cfg.chains, k, d->stream), "copy f");
+    return read_status(d);
+}
+
+mcmc_status mcmc_detect_get_tracked(mcmc_detector *d, double *f, double *best_f, int32_t host_io)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "get_tracked before preprocess");
+    if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    const size_t bytes = 8 * (size_t)d->n_channels * d->cfg.chains;
+    const cudaMemcpyKind k = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (!d->f_valid) {
+        // no run yet: the chains have no tracked energies; hand out FP64 evaluations of the
+        // initial states (the running best is the initial state) and leave the handle as it is
+        const double *fx = nullptr;
+        mcmc_status es = fp64_energies(d, &fx);
+        if (es != MCMC_OK) return es;
+        if (f) CK(cudaMemcpyAsync(f, fx, bytes, k, d->stream), "copy f");
+        if (best_f) CK(cudaMemcpyAsync(best_f, fx, bytes, k, d->stream), "copy best f");
+        return read_status(d);
+    }
+    if (f) CK(cudaMemcpyAsync(f, d->d_f.p, bytes, k, d->stream), "copy f");
+    if (best_f) CK(cudaMemcpyAsync(best_f, d->d_best_f.p, bytes, k, d->stream), "copy best f");
+    return read_status(d);
+}
+
+mcmc_status mcmc_detect_get_trace(mcmc_detector *d, double *trace, int32_t host_io)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!d->prepared) return fail(d, MCMC_ESTATE, "get_trace before preprocess");
+    if (!(d->cfg.engine & MCMC_ENGINE_TRACE)) return fail(d, MCMC_ESTATE, "handle created without MCMC_ENGINE_TRACE");
+    if (!trace) return fail(d, MCMC_EINVAL, "null trace");
+    if (host_io != 0 && host_io != 1) return fail(d, MCMC_EINVAL, "host_io must be 0 or 1");
+    const cudaMemcpyKind k = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(trace, d->d_trace.p, 16 * (size_t)d->n_channels * d->cfg.chains, k, d->stream),
+       "copy trace");
     return read_status(d);
 }
 
@@ -1100,21 +1184,10 @@ mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32
     } else {
         CK(cudaMemcpyAsync(d->d_states.p, states, d->tot_states, cudaMemcpyDeviceToDevice, d->stream), "copy states");
     }
-    RefreshArgs ra{};
-    ra.desc = P<ChannelDesc>(d->d_desc);
-    ra.states = P<int8_t>(d->d_states);
-    ra.G64 = P<double>(d->d_G64);
-    ra.z64 = P<double>(d->d_z64);
-    ra.yy = P<double>(d->d_yy);
-    ra.f = P<double>(d->d_f);
-    ra.best_f = P<double>(d->d_best_f);
-    ra.best_states = P<int8_t>(d->d_best_states);
-    ra.status = status_ptr(d);
-    ra.n_channels = d->n_channels;
-    ra.chains = d->cfg.chains;
-    ra.reset_best = 1;
-    CK(launch_refresh(ra, d->stream), "refresh energies");
-    d->launches++;
+    {
+        mcmc_status es = refresh_energies(d, P<double>(d->d_f), true, false);
+        if (es != MCMC_OK) return es;
+    }
     d->f_valid = true;
     d->f_exact = true;
     d->d_valid = false;
@@ -1260,9 +1333,11 @@ mcmc_status mcmc_detect_init_learned(mcmc_detector *d)
     CK(net_forward(d, rows, P<float>(d->d_mx_X), P<float>(d->d_mx_logits)), "network forward");
     CK(launch_mix(2, step_args(d), d->n_channels, d->max_nt, d->stream), "warm start kernel");
     d->launches++;
-    // the energies of the new states come from the chain kernel's first GEMM (as after the
-    // random initial states), or from the FP64 refresh if they are read before a run
-    d->f_valid = false;
+    // exact energies of the warm-start states; the running best restarts there
+    st = refresh_energies(d, P<double>(d->d_f), true, false);
+    if (st != MCMC_OK) return st;
+    d->f_valid = true;
+    d->f_exact = true;
     d->d_valid = false;
     return MCMC_OK;
 }
@@ -1275,7 +1350,7 @@ mcmc_status mcmc_detect_mix_step(mcmc_detector *d, int64_t t)
     if (st != MCMC_OK) return st;
     if (!d->mlp) return fail(d, MCMC_ESTATE, "no network attached");
     if (t < 1 || t > 0xFFFFFFFFll) return fail(d, MCMC_EINVAL, "t out of range");
-    st = ensure_energies(d, false);
+    st = ensure_energies(d);
     if (st != MCMC_OK) return st;
     const long long rows = d->tot_states / 2;
     for (DevBuf *b : {&d->d_mx_gx, &d->d_mx_px, &d->d_mx_gxp, &d->d_mx_pxp, &d->d_mx_lqf})
@@ -1300,6 +1375,12 @@ mcmc_status mcmc_detect_mix_step(mcmc_detector *d, int64_t t)
     d->launches += 4;
     d->d_valid = false;
     d->f_exact = false;
+    if (d->cfg.refresh_period >= 0) {
+        // exact energies after the move, as at the end of a run
+        st = refresh_energies(d, P<double>(d->d_f), false, true);
+        if (st != MCMC_OK) return st;
+        d->f_exact = true;
+    }
     long long moved = 0;
     for (const ChannelDesc &c : d->desc)
         if (c.L == L) moved += d->cfg.chains;

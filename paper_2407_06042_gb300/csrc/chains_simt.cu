@@ -35,7 +35,7 @@ __host__ __device__ constexpr size_t align_up(size_t v, size_t a) { return (v + 
 
 // Shared-memory layout (byte offsets), identical for every work item of a launch.
 struct Layout {
-    size_t bt, zt, wt, a, D, Dp, xsT, term, dterm, fcur, fbest, acc, impr, cnt, k, kp, kb, total;
+    size_t bt, zt, wt, a, D, Dp, xsT, term, dterm, fcur, fbest, acc, impr, cnt, tie, k, kp, kb, total;
 };
 
 __host__ __device__ inline Layout make_layout(int es, int cg, int N, int NOp, bool bt_smem)
@@ -57,6 +57,7 @@ __host__ __device__ inline Layout make_layout(int es, int cg, int N, int NOp, bo
     L.acc = take((size_t)cg * 4);
     L.impr = take((size_t)cg * 4);
     L.cnt = take((size_t)cg * 4);
+    L.tie = take(3 * 4);                        // near-tie counts of the work item, three windows
     L.k = take((size_t)cg * N);
     L.kp = take((size_t)cg * N);
     L.kb = take((size_t)cg * N);
@@ -220,6 +221,7 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
     int *acc = reinterpret_cast<int *>(smem + lay.acc);
     int *impr = reinterpret_cast<int *>(smem + lay.impr);
     unsigned *cnt = reinterpret_cast<unsigned *>(smem + lay.cnt);
+    unsigned *ties = reinterpret_cast<unsigned *>(smem + lay.tie);
     int8_t *sk = reinterpret_cast<int8_t *>(smem + lay.k);
     int8_t *skp = reinterpret_cast<int8_t *>(smem + lay.kp);
     int8_t *skb = reinterpret_cast<int8_t *>(smem + lay.kb);
@@ -248,6 +250,7 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
         fbest[c] = c < nC ? A.best_f[ci] : 0.0;
         cnt[c] = 0;
     }
+    if (threadIdx.x < 3) ties[threadIdx.x] = 0u;
     __syncthreads();
     // Gt x and the drift slope of the current states
     gemm<T, TCH, TO>(bt, NOp, xsT, xld, N, Dp, nC);
@@ -337,6 +340,17 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
                 const T logu = sizeof(T) == 8 ? M<T>::lg(u) : (T)lg2_approx((float)u);
                 int ok = logu < loga;
                 if (!isfinite((double)logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
+                // near-tie bands |log A - log u| < 1e-6, 1e-4, 1e-2 (natural log; the kernel's
+                // units are log2 in FP32, natural in FP64)
+                const T gap = loga > logu ? loga - logu : logu - loga;
+                if (gap < T(1e-2) * unit) {
+                    atomicAdd(&ties[2], 1u);
+                    if (gap < T(1e-4) * unit) atomicAdd(&ties[1], 1u);
+                    if (gap < T(1e-6) * unit) atomicAdd(&ties[0], 1u);
+                }
+                if (A.trace)
+                    reinterpret_cast<double2 *>(A.trace)[(long long)it.b * A.chains + cc] =
+                        make_double2((double)logr / (double)unit, (double)logu / (double)unit);
                 acc[c] = ok;
                 int im = 0;
                 if (ok) {
@@ -397,6 +411,8 @@ __device__ void simt_item(const ChainArgs &A, const WorkItem &it, const ChannelD
         A.best_f[ci] = fbest[c];
         A.accepts[ci] += cnt[c];
     }
+    if (threadIdx.x < 3 && A.near_ties && ties[threadIdx.x])
+        atomicAdd(&A.near_ties[threadIdx.x], (unsigned long long)ties[threadIdx.x]);
 }
 
 template <typename T, int TCH, int TO>

@@ -74,7 +74,7 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 
 // Shared-memory layout of the kernel (bytes).
 struct TcLayout {
-    uint32_t a, b, red, dred, acc, ref, fst, cnt, fref, kb, dg, xs, bar, tmem, total;
+    uint32_t a, b, red, dred, acc, ref, fst, cnt, tie, fref, kb, dg, xs, bar, tmem, total;
 };
 
 // The A operand of a single CTA stays resident for MT <= 2 (N <= 128). Beyond that it no longer
@@ -106,6 +106,7 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C, int 
     L.ref = take((uint32_t)C * 16, 16);      // FP64 refresh results per chain
     L.fst = take((uint32_t)C * 16, 16);      // tracked and best energies per chain
     L.cnt = take((uint32_t)C * 4, 16);       // accepted moves per chain
+    L.tie = take((uint32_t)C * 12, 16);      // near-tie counts per chain slot, three windows
     // states for the FP64 refresh (a cluster CTA reads them from its B operand instead) and the
     // best visited state of every chain (a cluster CTA: its own 64 dimensions)
     L.fref = take(CL > 1 ? 0u : (uint32_t)C * kMaxN, 16);
@@ -137,6 +138,7 @@ struct TcCtx {
     double *sref;
     double *sfc, *sfb;            // tracked and best energies of the CTA's chains
     unsigned *scnt;
+    unsigned *stie;               // [3][C] near-tie counts of the CTA's chain slots (all items)
     int8_t *sfs;
     int8_t *skb;
     uint64_t *sdg;                // Gt x pairs in shared memory (streamed kernels)
@@ -532,22 +534,6 @@ __device__ __forceinline__ void tc_stage_a(const TcCtx &x, const unsigned char *
     }
 }
 
-// round(g 2^sh) for |g 2^sh| < 2^62, from the bits of g (integer operations only: this GPU's FP64
-// pipe runs at a small fraction of its integer and FP32 rates). Ties round away from zero.
-__device__ __forceinline__ long long fixed_of(double g, int sh)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(g);
-    const int ex = (int)((b >> 52) & 0x7FFull);
-    if (ex == 0) return 0;                                  // zero or subnormal
-    const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-    const int p = ex - 1075 + sh;                           // g 2^sh = mant 2^p
-    long long v;
-    if (p >= 0) v = p < 10 ? mant << p : 0;                 // p > 0 is outside the contract
-    else if (p > -64) v = (mant + (1ll << (-p - 1))) >> (-p);
-    else v = 0;
-    return (b >> 63) ? -v : v;
-}
-
 // One work item (chains [c0, c0 + nC) of one channel). FULL: every dimension of every tile and
 // every chain column is live, so no per-(dimension, chain) validity test is needed. Levels are
 // held as exact small floats.
@@ -875,6 +861,16 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             const float loga = logr < 0.f ? logr : 0.f;
             int ok = logu < loga;
             if (!isfinite(logr)) { ok = 0; set_status(A.status, kStatusNumeric); }
+            if (CL == 1 || x.rank == 0) {
+                // near-tie bands |log A - log u| < 1e-6, 1e-4, 1e-2 (natural log; log2 units here)
+                const float gap = fabsf(loga - logu);
+                x.stie[c] += gap < 1e-6f * kLog2e ? 1u : 0u;
+                x.stie[C + c] += gap < 1e-4f * kLog2e ? 1u : 0u;
+                x.stie[2 * C + c] += gap < 1e-2f * kLog2e ? 1u : 0u;
+                if (A.trace)
+                    reinterpret_cast<double2 *>(A.trace)[(long long)it.b * A.chains + it.c0 + c] =
+                        make_double2((double)logr * (double)kLn2, (double)logu * (double)kLn2);
+            }
             int im = 0;
             if (ok) {
                 const double fc = x.sfc[c] + d.inv_s2 * (double)sd;
@@ -1200,6 +1196,7 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     x.sfc = reinterpret_cast<double *>(smem + lay.fst);
     x.sfb = x.sfc + C;
     x.scnt = reinterpret_cast<unsigned *>(smem + lay.cnt);
+    x.stie = reinterpret_cast<unsigned *>(smem + lay.tie);
     x.sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
     x.skb = reinterpret_cast<int8_t *>(smem + lay.kb);
     x.sdg = reinterpret_cast<uint64_t *>(smem + lay.dg);
@@ -1267,6 +1264,7 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     // zero the B operand once: padding columns / chains stay zero, the rest is rewritten
     for (int e = x.tid; e < (int)(lay.red - lay.b) / 16; e += blockDim.x)
         reinterpret_cast<uint4 *>(x.sB)[e] = make_uint4(0, 0, 0, 0);
+    for (int e = x.tid; e < 3 * C; e += blockDim.x) x.stie[e] = 0u;
     bool alive = true;
     // a cluster's CTAs start exchanging only once every CTA's barriers and B operand are set up
     if constexpr (CL > 1) cl_sync();
@@ -1309,8 +1307,25 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
-    // no CTA leaves while another may still store into its shared memory
-    if constexpr (CL > 1) cl_sync();
+    // near-tie counts of the CTA (every item it ran): one sum per window
+    __syncthreads();
+    if (x.warp == 0 && A.near_ties && (CL == 1 || x.rank == 0)) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            unsigned v = 0;
+            for (int c = x.lane; c < C; c += 32) v += x.stie[k * C + c];
+            v = __reduce_add_sync(0xffffffffu, v);
+            if (x.lane == 0 && v) atomicAdd(&A.near_ties[k], (unsigned long long)v);
+        }
+    }
+    // no CTA leaves while another may still store into its shared memory: after a wait that ran
+    // out, the B-slice phase this CTA armed last may still receive the other CTAs' bulk copies,
+    // so thread 0 waits (bounded) for it before the exit barrier (on the normal path it has
+    // completed and the wait returns at once)
+    if constexpr (CL > 1) {
+        if (x.tid == 0 && !alive) mbar_wait(x.bar_b, x.b_phase ^ 1u);
+        cl_sync();
+    }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (x.warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(x.tmem),

@@ -18,6 +18,10 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace mcmcdet {
@@ -25,16 +29,38 @@ namespace mcmcdet {
 constexpr int kMaxN = 256;     // real unknowns per channel (Nt <= 128)
 constexpr int kMaxL = 8;       // PAM levels per real dimension (64-QAM)
 
-// Lets kernel `func` take up to the device's opt-in maximum of dynamic shared memory (each launch
-// then asks for what it needs). Every launch site sets this same value, so handles used from
-// different host threads cannot lower the limit between another thread's setting and its launch.
+// Lets kernel `func` take up to the device's opt-in maximum of dynamic shared memory, less its
+// static shared memory (each launch then asks for what it needs). Every launch site sets this
+// same value, so handles used from different host threads cannot lower the limit between another
+// thread's setting and its launch. The attribute is set once per kernel and device (a table of
+// the (kernel, device) pairs done, shared by every kernel); later calls only look it up.
+inline bool dyn_smem_done(const void *func, int dev, bool mark)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &e : done)
+        if (e.first == func && e.second == dev) return true;
+    if (mark) done.emplace_back(func, dev);
+    return false;
+}
+
 template <typename F>
 inline cudaError_t allow_max_dyn_smem(F *func)
 {
-    int dev = 0, mx = 0;
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e != cudaSuccess) return e;
+    const void *key = reinterpret_cast<const void *>(func);
+    if (dyn_smem_done(key, dev, false)) return cudaSuccess;
+    int mx = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 mx - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) dyn_smem_done(key, dev, true);
     return e;
 }
 
@@ -153,6 +179,22 @@ __device__ __forceinline__ int level_of_gray(int g) { int k = g; k ^= k >> 1; k 
 __device__ __forceinline__ void set_status(unsigned *status, unsigned bit)
 {
     atomicOr(status, bit);
+}
+
+// round(g 2^sh) for |g 2^sh| < 2^62, from the bits of g (integer operations only: this GPU's FP64
+// pipe runs at a small fraction of its integer and FP32 rates). Ties round away from zero.
+__device__ __forceinline__ long long fixed_of(double g, int sh)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(g);
+    const int ex = (int)((b >> 52) & 0x7FFull);
+    if (ex == 0) return 0;                                  // zero or subnormal
+    const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    const int p = ex - 1075 + sh;                           // g 2^sh = mant 2^p
+    long long v;
+    if (p >= 0) v = p < 10 ? mant << p : 0;                 // p > 0 is outside the contract
+    else if (p > -64) v = (mant + (1ll << (-p - 1))) >> (-p);
+    else v = 0;
+    return (b >> 63) ? -v : v;
 }
 
 // FP64 x^T G x and x^T z for one state (G symmetric N x N), one share of the work: the row pairs

@@ -52,6 +52,11 @@ struct RefreshArgs {
     int n_channels;
     int chains;
     int reset_best;
+    int max_n;              // largest N of the batch (sizes the launch; 0: kMaxN)
+    // or null: max |f_old - f| and max |f_old - f| / |f| over the chains (ordered bits), the
+    // correction this refresh makes to the energies the chains tracked
+    unsigned long long *drift_bits;
+    unsigned long long *drift_rel_bits;
 };
 
 // One chain-kernel work item: chains [c0, c0 + nc) of channel b.
@@ -91,6 +96,10 @@ struct ChainArgs {
     int init_f;             // derive the tracked energies of the current states from the first
                             // GEMM (FP32 / MIXED) and restart the running best from them
     float *dexp;            // Gt x of the final states (FP32), same layout as the states
+    unsigned long long *near_ties;   // [3] MH decisions with |log A - log u| below 1e-6, 1e-4 and
+                                     // 1e-2 (natural log), as the kernel evaluated them
+    double *trace;          // or null: per chain (channel-major) the log acceptance ratio and log u
+                            // (natural log) of its latest transition, as pairs
     // tcgen05 engine only
     const uint8_t *tc_ops;  // per-channel packed BF16 operand blocks
     int split_terms;

@@ -13,6 +13,8 @@
 // the chain states), and calls that overlap on the GPU race with each other.
 #include "../../include/mcmcdet.h"
 
+#include <cuda.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,22 +31,67 @@ namespace {
 // The fixed scratch of the no-allocation entry point (size: MCMC_NOALLOC_SCRATCH_BYTES).
 __device__ __align__(256) unsigned char g_noalloc_scratch[MCMC_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device. In host code the symbol's name is only a
-// host-side stand-in, never a device address: the real address is looked up once per device.
-constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};
+// Device address of g_noalloc_scratch per CUDA context. In host code the symbol's name is only a
+// host-side stand-in, never a device address: the real address is looked up (with the context
+// current) the first time a call runs in a context, and kept for that context. A context that is
+// destroyed (cudaDeviceReset) and a new one created at the same handle value has a new unique
+// id, so entries are matched on both and the new context gets its own lookup.
+struct ScratchEntry {
+    CUcontext ctx;
+    unsigned long long ctx_id;
+    void *addr;
+};
+std::vector<ScratchEntry> g_scratch_addr;
 std::mutex g_scratch_mu;
 
-cudaError_t scratch_address(int dev, unsigned char **out)
+// The two driver calls used to identify the current context, looked up through the runtime (the
+// library does not link against the driver, so it also loads on machines without one).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+cudaError_t current_context(CUcontext *ctx, unsigned long long *id)
 {
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *p0 = nullptr, *p1 = nullptr;
+        cudaDriverEntryPointQueryResult q0{}, q1{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p0, 4000, cudaEnableDefault, &q0);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &p1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess || !p0 || !p1) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(p0);
+        get_id = reinterpret_cast<CtxGetIdFn>(p1);
     }
-    *out = static_cast<unsigned char *>(g_scratch_addr[dev]);
+    *ctx = nullptr;
+    if (get_current(ctx) != CUDA_SUCCESS || !*ctx) return cudaErrorInvalidDevice;
+    return get_id(*ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidDevice;
+}
+
+cudaError_t scratch_address(unsigned char **out)
+{
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (current_context(&ctx, &id) != cudaSuccess) {
+        // no context current yet: the runtime call makes the current device's primary context
+        // current (and loads this library's module on it)
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        const cudaError_t c = current_context(&ctx, &id);
+        if (c != cudaSuccess) return c;
+    }
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    for (const ScratchEntry &e : g_scratch_addr)
+        if (e.ctx == ctx && e.ctx_id == id) {
+            *out = static_cast<unsigned char *>(e.addr);
+            return cudaSuccess;
+        }
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr.push_back(ScratchEntry{ctx, id, p});
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 
@@ -153,7 +200,7 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
     }
     // CUDA-core FP32 chain kernel plan (shared-memory budget as in the handle-based path)
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return MCMC_EUNSUPPORTED;
     }
@@ -177,7 +224,7 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
 
     // carve the fixed scratch; requests that do not fit are rejected before any work
     unsigned char *scratch = nullptr;
-    if (scratch_address(dev, &scratch) != cudaSuccess) {
+    if (scratch_address(&scratch) != cudaSuccess) {
         cudaGetLastError();
         return MCMC_ECUDA;
     }
@@ -251,6 +298,7 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
     pa.stage_h = h_stage <= std::min<size_t>((size_t)optin, 128 * 1024);
     pa.stage_gj = stage_gj;
     pa.precond_fp32 = 1;
+    pa.max_nt = maxnt;   // the register-tiled Gauss-Jordan for Nt <= 64, as the handle path picks
     NA_CK(launch_prep(pa, n_channels, h_stage, stage_gj ? gj_stage : (size_t)(2 * maxnt) * 8, pre, s));
 
     InitArgs ia{};
@@ -262,6 +310,23 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
     ia.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
     ia.key1 = (uint32_t)(seed >> 32);
     NA_CK(launch_init_states(ia, s));
+
+    // exact energies of the initial states; the running best starts there
+    RefreshArgs ra{};
+    ra.desc = d_desc;
+    ra.states = d_states;
+    ra.G64 = d_G64;
+    ra.z64 = d_z64;
+    ra.yy = d_yy;
+    ra.f = d_f;
+    ra.best_f = d_best_f;
+    ra.best_states = d_best_states;
+    ra.status = status;
+    ra.n_channels = n_channels;
+    ra.chains = Np;
+    ra.reset_best = 1;
+    ra.max_n = maxn;
+    NA_CK(launch_refresh(ra, s));
 
     if (iterations > 0) {
         ChainArgs ca{};
@@ -291,23 +356,13 @@ extern "C" mcmc_status mcmc_detect_noalloc(int32_t n_channels, const int32_t *nt
         ca.accepts = d_acc;
         ca.drift_bits = drift;
         ca.status = status;
-        ca.init_f = 1;
+        ca.init_f = 0;
         ca.dexp = d_dexp;
         NA_CK(launch_chains_simt(ca, false, chain_smem_bytes_simt(4, cg, maxn, maxnop, bt_smem), s));
-    } else {
-        RefreshArgs ra{};
-        ra.desc = d_desc;
-        ra.states = d_states;
-        ra.G64 = d_G64;
-        ra.z64 = d_z64;
-        ra.yy = d_yy;
-        ra.f = d_f;
-        ra.best_f = d_best_f;
-        ra.best_states = d_best_states;
-        ra.status = status;
-        ra.n_channels = n_channels;
-        ra.chains = Np;
-        ra.reset_best = 1;
+        // exact energies of the final states (the chains tracked them in FP32 steps)
+        ra.reset_best = 0;
+        ra.best_f = nullptr;
+        ra.best_states = nullptr;
         NA_CK(launch_refresh(ra, s));
     }
 

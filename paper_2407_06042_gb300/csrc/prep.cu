@@ -1,7 +1,7 @@
 // prep.cu -- per-channel preparation (Sec. II-A, Eq. (10); Remark 1, Eq. (19); Sec. III-D):
 // the complex Gram matrix G = H^H H, the matched filter z = H^H y and ||y||^2 in FP64, the
 // damped inverse (G + gamma I)^{-1} for the preconditioned proposal, the scaled real-valued
-// operands every chain kernel reads, the random initial states (t = 0) and their FP64 energies.
+// operands every chain kernel reads and the random initial states (t = 0).
 //
 // One CTA per channel; the work is O(Nr Nt^2 + Nt^3) per channel, done once per batch.
 #include "common.cuh"
@@ -369,44 +369,6 @@ __global__ void init_states_kernel(InitArgs a)
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// FP64 energies of the current states: f = -(||y||^2 - 2 xt^T zt + xt^T Gt xt) / sigma^2.
-// One warp per chain. Optionally also resets the running best to the current state.
-// ------------------------------------------------------------------------------------------
-__global__ void refresh_kernel(RefreshArgs a)
-{
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= (long long)a.n_channels * a.chains) return;
-    const int b = (int)(warp / a.chains), c = (int)(warp % a.chains);
-    const ChannelDesc d = a.desc[b];
-    const int N = d.N, L = d.L;
-    const int8_t *k = a.states + d.state_off + (long long)c * N;
-    const double *G = a.G64 + d.mat_off;
-    const double *z = a.z64 + d.vec_off;
-    bool bad = false;
-    for (int n = lane; n < N; n += 32) bad |= (k[n] < 0 || k[n] >= L);
-    double quad, lin;
-    quad_lin_fp64(G, z, N, lane, [&](int n) { return (double)odd_of(k[n], L); }, quad, lin);
-    for (int o = 16; o; o >>= 1) {
-        quad += __shfl_xor_sync(0xffffffffu, quad, o);
-        lin += __shfl_xor_sync(0xffffffffu, lin, o);
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) {
-        const double f = -(a.yy[b] - 2.0 * lin + quad) * d.inv_s2;
-        if (bad) set_status(a.status, kStatusBadState);
-        if (!isfinite(f)) set_status(a.status, kStatusNumeric);
-        const long long ci = (long long)b * a.chains + c;
-        a.f[ci] = f;
-        if (a.reset_best) a.best_f[ci] = f;
-    }
-    if (a.reset_best) {
-        int8_t *bk = a.best_states + d.state_off + (long long)c * N;
-        for (int n = lane; n < N; n += 32) bk[n] = k[n];
-    }
-}
-
-// ------------------------------------------------------------------------------------------
 // Host launchers
 // ------------------------------------------------------------------------------------------
 // Threads of the Gram kernel: its work items are the nb (nb + 1) / 2 upper-triangle 2 x 2 blocks
@@ -459,15 +421,6 @@ cudaError_t launch_init_states(const InitArgs &a, cudaStream_t s)
     if (total <= 0) return cudaSuccess;
     const int bs = 256;
     init_states_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_refresh(const RefreshArgs &a, cudaStream_t s)
-{
-    const long long warps = (long long)a.n_channels * a.chains;
-    if (warps <= 0) return cudaSuccess;
-    const int bs = 256;
-    refresh_kernel<<<(unsigned)((warps * 32 + bs - 1) / bs), bs, 0, s>>>(a);
     return cudaGetLastError();
 }
 

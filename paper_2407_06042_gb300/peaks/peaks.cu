@@ -1,7 +1,8 @@
 // peaks.cu -- pipe-throughput microbenchmarks used as roofline denominators by bench.py:
 // MUFU ex2 (the transcendental unit that evaluates every proposal weight), FP32 FMA, packed
-// FP32x2 FMA and FP64 FMA, each as sustained operations per second over the whole GPU with
-// enough independent chains per thread to hide latency.
+// FP32x2 FMA, FP64 FMA, the integer ALU (three-input XOR) and wide-multiply rates, and whole
+// Philox4x32-10 blocks (the method's random numbers), each as sustained operations per second
+// over the whole GPU with enough independent chains per thread to hide latency.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -84,6 +85,79 @@ __global__ void dfma_kernel(float *out, int iters)
     if (s == 12345.0) out[0] = (float)s;
 }
 
+// Integer ALU: three-input XORs (one LOP3 each), the logic half of a Philox round.
+__global__ void xor3_kernel(float *out, int iters)
+{
+    uint32_t v[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) v[i] = threadIdx.x * 2654435761u + (uint32_t)i;
+    const uint32_t a = 0x9E3779B9u ^ blockIdx.x, b = 0xBB67AE85u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) v[i] = v[i] ^ (a + (uint32_t)i) ^ (b >> (i & 3));
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s ^= v[i];
+    if (s == 12345u) out[0] = (float)s;
+}
+
+// 32 x 32 -> 64-bit products (low and high words), the arithmetic half of a Philox round.
+__global__ void mulwide_kernel(float *out, int iters)
+{
+    uint32_t v[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) v[i] = threadIdx.x * 2654435761u + (uint32_t)i + 1u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) {
+            const uint64_t p = (uint64_t)v[i] * 0xD2511F53u;
+            v[i] = (uint32_t)p + (uint32_t)(p >> 32);
+        }
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s ^= v[i];
+    if (s == 12345u) out[0] = (float)s;
+}
+
+// Whole Philox4x32-10 blocks (Salmon et al., SC'11), two independent counters per thread, ten
+// rounds each: the generator's own throughput, in blocks of four words per second.
+__global__ void philox_kernel(float *out, int iters)
+{
+    uint32_t c[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        c[j][0] = threadIdx.x;
+        c[j][1] = blockIdx.x;
+        c[j][2] = (uint32_t)j;
+        c[j][3] = 0u;
+    }
+    uint32_t acc = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            uint32_t x0 = c[j][0], x1 = c[j][1], x2 = c[j][2], x3 = c[j][3] + (uint32_t)it;
+            uint32_t k0 = 0x12345678u, k1 = 0x9ABCDEF0u;
+#pragma unroll
+            for (int r = 0; r < 10; ++r) {
+                const uint64_t p0 = (uint64_t)x0 * 0xD2511F53u;
+                const uint64_t p1 = (uint64_t)x2 * 0xCD9E8D57u;
+                const uint32_t n0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+                const uint32_t n2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+                x1 = (uint32_t)p1;
+                x3 = (uint32_t)p0;
+                x0 = n0;
+                x2 = n2;
+                k0 += 0x9E3779B9u;
+                k1 += 0xBB67AE85u;
+            }
+            acc ^= x0 ^ x1 ^ x2 ^ x3;
+        }
+    }
+    if (acc == 12345u) out[0] = (float)acc;
+}
+
 template <typename K>
 double rate(K kern, int blocks, int threads, int iters, double ops_per_thread_iter)
 {
@@ -108,7 +182,8 @@ double rate(K kern, int blocks, int threads, int iters, double ops_per_thread_it
 
 }  // namespace
 
-// out[0] ex2/s, out[1] FP32 FMA/s (one FMA = 1 op), out[2] FP32x2 FMA lanes/s, out[3] FP64 FMA/s.
+// out[0] ex2/s, out[1] FP32 FMA/s (one FMA = 1 op), out[2] FP32x2 FMA lanes/s, out[3] FP64 FMA/s,
+// out[4] three-input XORs/s, out[5] 32 x 32 -> 64-bit products/s, out[6] Philox4x32-10 blocks/s.
 extern "C" int mcmc_pipe_peaks(double *out)
 {
     int dev = 0, sms = 0;
@@ -119,5 +194,8 @@ extern "C" int mcmc_pipe_peaks(double *out)
     out[1] = rate(fma_kernel, blocks, threads, 16384, kChains);
     out[2] = rate(fma2_kernel, blocks, threads, 8192, 2.0 * kChains);
     out[3] = rate(dfma_kernel, blocks, threads, 256, kChains);
+    out[4] = rate(xor3_kernel, blocks, threads, 8192, kChains);
+    out[5] = rate(mulwide_kernel, blocks, threads, 4096, kChains);
+    out[6] = rate(philox_kernel, blocks, threads, 256, 2.0);
     return 0;
 }

@@ -62,13 +62,16 @@ def test_host_only_entry_points():
     assert lib.mcmc_detect_llr_list(None, None, 1.0, 0) == 1
     assert lib.mcmc_detect_run_chains(None, 1, 0) == 1
     assert lib.mcmc_detect_create(None, None) == 1
+    assert lib.mcmc_detect_get_tracked(None, None, None, 0) == 1
+    assert lib.mcmc_detect_get_trace(None, None, 0) == 1
 
 
 def test_config_struct_matches_header():
     import paper_2407_06042_gb300 as pkg
     # int32 x 10 + uint64 + pointer
     assert ctypes.sizeof(pkg.Config) == 10 * 4 + 8 + 8
-    assert ctypes.sizeof(pkg.Stats) == 8 + 8 + 4 + 4 + 8
+    # int64 x 2 + int32 x 2 + double + int64 x 3 (near-tie counts) + double
+    assert ctypes.sizeof(pkg.Stats) == 8 + 8 + 4 + 4 + 8 + 3 * 8 + 8
 
 
 def test_diag_argument_checks_on_the_host():
@@ -121,7 +124,8 @@ def test_config_validation_on_the_host():
                dict(precision=MIXED, engine=AUTO | NOCL),
                dict(precision=FP32, engine=pkg.MCMC_ENGINE_SIMT, tile=64)]:
         assert create(**kw) in (0, 7), kw
-    for kw in [dict(engine=16), dict(engine=3), dict(precision=MIXED, engine=TC, tile=48),
+    for kw in [dict(engine=32), dict(engine=3), dict(precision=MIXED, engine=TC, tile=48),
                dict(precision=MIXED, engine=AUTO, tile=64), dict(precision=FP32, engine=TC),
-               dict(max_nt=129), dict(chains=6), dict(split_terms=4)]:
+               dict(max_nt=129), dict(chains=6), dict(split_terms=4),
+               dict(refresh_period=-2)]:
         assert create(**kw) == 1, kw

@@ -16,6 +16,7 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 
 TC = 2            # MCMC_ENGINE_TC: these tests pin the tensor-core kernel itself
+TRACE = 16        # MCMC_ENGINE_TRACE: log A and log u of every chain's latest test
 GRAPH = 4         # MCMC_ENGINE_GRAPH
 NO_CLUSTER = 8    # MCMC_ENGINE_NO_CLUSTER: N > 128 on the single-CTA kernel (operand streamed)
 
@@ -27,10 +28,16 @@ def _small(n=16, snr=12.0, seed=1001):
 @pytest.mark.parametrize("terms,w_cat,w_acc", [(3, 2e-4, 2e-3), (2, 6.4e-3, 6.4e-2)])
 def test_mixed_step_parity(terms, w_cat, w_acc):
     b = _small(16)
-    det = H.make_detector(b, chains=32, precision="mixed", split_terms=terms, seed=0, engine=TC)
-    r = H.step_parity(det, b, H.targets(b), seed=0, steps=25, w_cat=w_cat, w_acc=w_acc)
+    det = H.make_detector(b, chains=32, precision="mixed", split_terms=terms, seed=0,
+                          engine=TC | TRACE)
+    r = H.step_parity(det, b, H.targets(b), seed=0, steps=25, w_cat=w_cat, w_acc=w_acc,
+                      energies=True, label=f"mixed_s{terms}_4x4")
     assert r["bad"] == 0, r
     assert r["mism"] <= max(4, r["steps"] // 1000), r
+    assert r["max_dloga"] <= w_acc, r
+    # the energies the chains hold after each launch (exact evaluations at the end of a run),
+    # against the oracle's f of their states
+    assert r["energy_rel_max"] <= 1e-10, r
     det.destroy()
 
 
@@ -110,20 +117,29 @@ def test_mixed_ber_within_binomial_interval_of_oracle():
 
 
 def test_mixed_energies_refresh():
-    """FP64 refresh every R transitions: the tracked energies equal FP64 evaluations of the
-    states right after a refresh point, and the reported drift is small."""
+    """Exact refresh every R transitions and at the end of every run: the energies the chains
+    hold (exported as they are) equal the oracle's f of the states after a run that ends on a
+    refresh point and after one that ends between refresh points; the largest correction a
+    refresh made stays small."""
     b = _small(4, snr=20.0)
     det = H.make_detector(b, chains=32, precision="mixed", refresh_period=10, engine=TC)
-    det.run_chains(30)
-    out = det.estimate(stats=True)
-    flat, f = det.get_chains()
-    st = H.split_states(det, b, flat)
     tg = H.targets(b)
-    for ch in range(b.n_channels):
-        for c in range(32):
-            fx = oracle.f_value(tg[ch].Hr, tg[ch].yr, tg[ch].sigma2, tg[ch].values(st[ch][c]))
-            assert abs(f[ch * 32 + c] - fx) <= 1e-10 * abs(fx)
+
+    def check(tol):
+        st = H.states_now(det, b)
+        f, _ = det.get_tracked()
+        for ch in range(b.n_channels):
+            for c in range(32):
+                fx = H.fp64_energy(tg[ch], st[ch][c])
+                assert abs(f[ch * 32 + c] - fx) <= tol * abs(fx), (ch, c, f[ch * 32 + c], fx)
+
+    det.run_chains(30)
+    check(1e-10)             # transition 30 is a refresh point
+    det.run_chains(5, 30)
+    check(1e-10)             # five FP32 increments past it, then the end-of-run refresh
+    out = det.estimate(stats=True)
     assert out["stats"]["refresh_drift"] < 1e-2
+    assert out["stats"]["refresh_drift_rel"] < 1e-3
     det.destroy()
 
 
@@ -183,11 +199,14 @@ def test_mixed_kronecker_256_refresh(flags):
     flat, f = det.get_chains()
     st = H.split_states(det, b, flat)
     tg = H.targets(b)
+    ftr, _ = det.get_tracked()
     for ch in range(b.n_channels):
         for c in range(32):
             fx = oracle.f_value(tg[ch].Hr, tg[ch].yr, tg[ch].sigma2, tg[ch].values(st[ch][c]))
             assert abs(f[ch * 32 + c] - fx) <= 1e-10 * abs(fx)
-    assert out["stats"]["refresh_drift"] < 1e-1
+            assert abs(ftr[ch * 32 + c] - fx) <= 1e-10 * abs(fx)
+    # the largest correction a refresh made to the FP32-tracked energies (ten transitions apart)
+    assert out["stats"]["refresh_drift_rel"] < 1e-3, out["stats"]
     det.destroy()
 
 

@@ -37,12 +37,18 @@ def test_initial_states_and_energies(precision):
     det.destroy()
 
 
+TRACE = 16   # MCMC_ENGINE_TRACE: the kernels record log A and log u of every chain's latest test
+
+
 def test_fp64_step_parity():
     b = _small(16)
-    det = H.make_detector(b, chains=32, precision="fp64", seed=0)
-    r = H.step_parity(det, b, H.targets(b), seed=0, steps=25)
+    det = H.make_detector(b, chains=32, precision="fp64", seed=0, engine=TRACE)
+    r = H.step_parity(det, b, H.targets(b), seed=0, steps=25, energies=True, label="fp64_4x4")
     assert r["bad"] == 0, r
     assert r["mism"] <= 2, r
+    # FP64 chains track energies and log A (Eq. (18)) to rounding
+    assert r["energy_rel_max"] <= 1e-10, r
+    assert r["max_dloga"] <= 1e-9, r
     det.destroy()
 
 
@@ -89,10 +95,16 @@ def test_one_launch_equals_single_step_launches(precision):
 
 def test_fp32_step_parity():
     b = _small(16)
-    det = H.make_detector(b, chains=32, precision="fp32", seed=0)
-    r = H.step_parity(det, b, H.targets(b), seed=0, steps=25, w_cat=2e-4, w_acc=2e-3)
+    det = H.make_detector(b, chains=32, precision="fp32", seed=0, engine=TRACE)
+    r = H.step_parity(det, b, H.targets(b), seed=0, steps=25, w_cat=2e-4, w_acc=2e-3,
+                      energies=True, label="fp32_4x4")
     assert r["bad"] == 0, r
     assert r["mism"] <= max(3, r["steps"] // 2000), r
+    # the energies the chains hold after each launch: FP32 increments from exact initial values,
+    # replaced by exact evaluations when the launch ends (refresh_period 0)
+    assert r["energy_rel_max"] <= 1e-10, r
+    # the kernel's log A against the oracle's: well inside the accept window
+    assert r["max_dloga"] <= 2e-3, r
     det.destroy()
 
 

@@ -87,6 +87,32 @@ def test_uniform_is_exact_in_fp32():
         assert float(np.float32(u)) == u
 
 
+@pytest.mark.parametrize("qam", [4, 16, 64])
+def test_initial_states_are_uniform_and_independent(qam):
+    """Sec. IV-A starts every chain from a random state: the t = 0 levels of oracle_init_state
+    are uniform over the L PAM levels (chi-square over 2048 chains x N dimensions), the levels of
+    neighbouring dimensions and of neighbouring chains are independent (chi-square of the L^2
+    pairs), and other chains, channels and seeds draw other states."""
+    from scipy.stats import chi2
+    H, y, s2 = _channel(3, 3, 5, qam=qam)
+    t = oracle.Target.from_channel(H, y, s2, qam)
+    L, N, C = int(round(np.sqrt(qam))), t.N, 2048
+    K = np.stack([t.init_state(3, 0, c) for c in range(C)])
+    assert K.min() >= 0 and K.max() <= L - 1
+
+    def stat(x, bins):
+        cnt = np.bincount(x.ravel(), minlength=bins)
+        e = x.size / bins
+        return float(((cnt - e) ** 2 / e).sum())
+    assert stat(K, L) < chi2.ppf(0.999, L - 1)
+    assert stat(K[:, :-1] * L + K[:, 1:], L * L) < chi2.ppf(0.999, L * L - 1)      # dimensions
+    assert stat(K[:-1, :] * L + K[1:, :], L * L) < chi2.ppf(0.999, L * L - 1)      # chains
+    assert not np.array_equal(t.init_state(3, 1, 0), K[0])
+    assert not np.array_equal(t.init_state(4, 0, 0), K[0])
+    S = float(L) ** N                                # distinct states among 64 draws
+    assert len({tuple(r) for r in K[:64]}) >= 0.8 * S * (1.0 - (1.0 - 1.0 / S) ** 64)
+
+
 # ------------------------------------------------------------------------------------------
 # System model, metric, gradient, preconditioner
 # ------------------------------------------------------------------------------------------

@@ -19,18 +19,18 @@ from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
-CHAINS, ITERS, SEED = 32, 60, 7
+CHAINS, SEED = 32, 7
 
 
-def _handle_path(batch):
-    det = H.make_detector(batch, chains=CHAINS, precision="fp32", seed=SEED)
-    det.run_chains(ITERS)
+def _handle_path(batch, pre, iters):
+    det = H.make_detector(batch, chains=CHAINS, precision="fp32", seed=SEED, preconditioned=pre)
+    det.run_chains(iters)
     out = det.estimate()
     det.destroy()
     return out
 
 
-def _noalloc(batch):
+def _noalloc(batch, pre, iters):
     import torch
     import paper_2407_06042_gb300 as pkg
     lib = pkg.lib()
@@ -47,8 +47,8 @@ def _noalloc(batch):
     yo = np.ascontiguousarray(batch.y_off, np.int64)
     p = lambda a: ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
     st = lib.mcmc_detect_noalloc(batch.n_channels, p(nt), p(nr), p(qam), p(Hd), p(ho), p(yd),
-                                 p(yo), p(s2), CHAINS, ITERS, SEED, 1, 1.0, 2.0, p(idx), p(llr),
-                                 p(bf), None)
+                                 p(yo), p(s2), CHAINS, iters, SEED, int(pre), 1.0, 2.0, p(idx),
+                                 p(llr), p(bf), None)
     return st, dict(best_idx=idx.cpu().numpy(), llr=llr.cpu().numpy(), best_f=bf.cpu().numpy())
 
 
@@ -58,17 +58,21 @@ def _compare(a, b):
     np.testing.assert_allclose(a["best_f"], b["best_f"], rtol=1e-10, atol=0)
 
 
-def test_noalloc_matches_handle_path_on_two_calls_in_a_row():
+@pytest.mark.parametrize("pre", [True, False])
+@pytest.mark.parametrize("iters", [60, 0])
+def test_noalloc_matches_handle_path_on_two_calls_in_a_row(pre, iters):
     b1 = workload.rayleigh_batch(4, 4, 16, [12.0], 24, 1001)
-    b2 = workload.generate([(3, 5, 64, 22.0), (8, 8, 4, 9.0), (6, 6, 16, 15.0)] * 4, 77)
-    ref1, ref2 = _handle_path(b1), _handle_path(b2)
-    st, out1 = _noalloc(b1)
+    # Nt = 40 takes the 4 x 4 register-tiled Gauss-Jordan (Nt in 33..64) in both paths
+    b2 = workload.generate([(3, 5, 64, 22.0), (8, 8, 4, 9.0), (6, 6, 16, 15.0)] * 4
+                           + [(40, 44, 16, 18.0)], 77)
+    ref1, ref2 = _handle_path(b1, pre, iters), _handle_path(b2, pre, iters)
+    st, out1 = _noalloc(b1, pre, iters)
     assert st == 0
     _compare(out1, ref1)
-    st, out2 = _noalloc(b2)
+    st, out2 = _noalloc(b2, pre, iters)
     assert st == 0
     _compare(out2, ref2)
-    st, again = _noalloc(b2)
+    st, again = _noalloc(b2, pre, iters)
     assert st == 0
     _compare(again, out2)
 
