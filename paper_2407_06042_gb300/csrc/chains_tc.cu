@@ -74,7 +74,7 @@ __device__ __forceinline__ float reduce_scatter16(const float (&v)[4], int dl)
 
 // Shared-memory layout of the kernel (bytes).
 struct TcLayout {
-    uint32_t a, b, red, dred, acc, ref, fst, cnt, tie, fref, kb, dg, xs, bar, tmem, total;
+    uint32_t a, b, red, dred, acc, ref, fst, cnt, tie, fref, kb, dg, xs, dsc, bar, tmem, total;
 };
 
 // The A operand of a single CTA stays resident for MT <= 2 (N <= 128). Beyond that it no longer
@@ -115,6 +115,8 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C, int 
     L.dg = take(tc_streamed(MT) ? (uint32_t)(2 * MT) * (16u * C) * 8u : 0u, 16);
     // cluster exchange slots: [2 alternating buffers][CL ranks][C chains] x 16 bytes
     L.xs = take(CL > 1 ? 2u * (uint32_t)CL * (uint32_t)C * 16u : 0u, 16);
+    // MMA descriptor pairs of a transition (resident operand: split terms x tiles x K steps)
+    L.dsc = take(tc_streamed(MT) ? 0u : (uint32_t)(S * MT * (Kp / 16)) * 16u, 16);
     // TMA, MMA, streamed chunks full[2] / empty[2], cluster B slices and exchange
     L.bar = take(8 * 8, 8);
     L.tmem = take(4, 4);
@@ -142,6 +144,8 @@ struct TcCtx {
     int8_t *sfs;
     int8_t *skb;
     uint64_t *sdg;                // Gt x pairs in shared memory (streamed kernels)
+    uint4 *sdsc;                  // (A, B) descriptor pairs of a transition's MMAs, in issue order
+                                  // (resident operand; written by thread 0 for each work item)
     int nthr;
     uint32_t bar_mma;
     uint32_t tmem;
@@ -376,6 +380,28 @@ __device__ __forceinline__ bool tc_stream_drain(TcCtx &x)
     return ok;
 }
 
+// Thread 0, for each work item of a resident-operand kernel: the (A, B) shared-memory descriptors
+// of a transition's MMAs (tile t: split terms s, K steps ks, in accumulation order), so that the
+// transitions only load and issue them.
+template <int MT>
+__device__ __forceinline__ void tc_mma_descs(TcCtx &x)
+{
+    if constexpr (!tc_streamed(MT)) {
+        const uint32_t a0 = smem_u32(x.sA), b0 = smem_u32(x.sB);
+        const int nk = x.Kp / 16;
+        int e = 0;
+        for (int t = 0; t < MT; ++t)
+            for (int s = 0; s < x.S; ++s) {
+                const uint32_t ab = a0 + (uint32_t)((s * MT + t) * 128 * x.Kp * 2);
+                for (int ks = 0; ks < nk; ++ks, ++e) {
+                    const uint64_t da = smem_desc(ab + ks * 256u, 128u, x.sbo_a);
+                    const uint64_t db = smem_desc(b0 + ks * 2u * b_lbo(), b_lbo(), x.sbo_b);
+                    x.sdsc[e] = make_uint4((uint32_t)da, (uint32_t)(da >> 32), (uint32_t)db, (uint32_t)(db >> 32));
+                }
+            }
+    }
+}
+
 template <int MT, int CL = 1>
 __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
 {
@@ -397,17 +423,16 @@ __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
             cl_send_b<CL>(x);
             if (!mbar_wait(x.bar_b, x.b_phase)) { x.fail = true; go = false; }
         }
-        const uint32_t a0 = smem_u32(x.sA), b0 = smem_u32(x.sB);
+        // the descriptors were laid out for this work item by tc_mma_descs: only the issue is left
+        const int per_tile = x.S * (x.Kp / 16);
+        const uint32_t idesc = x.idesc;
         for (int t = 0; t < MT && go; ++t) {
-            uint32_t first = 1;
-            for (int s = 0; s < x.S; ++s) {
-                const uint32_t ab = a0 + (uint32_t)((s * MT + t) * 128 * x.Kp * 2);
-                for (int ks = 0; ks < x.Kp / 16; ++ks) {
-                    const uint64_t da = smem_desc(ab + ks * 256u, 128u, x.sbo_a);
-                    const uint64_t db = smem_desc(b0 + ks * 2u * b_lbo(), b_lbo(), x.sbo_b);
-                    mma_bf16(x.tmem + (uint32_t)(t * x.C), da, db, x.idesc, first ? 0u : 1u);
-                    first = 0;
-                }
+            const uint32_t d = x.tmem + (uint32_t)(t * x.C);
+            const uint4 *dl = x.sdsc + t * per_tile;
+#pragma unroll 4
+            for (int e = 0; e < per_tile; ++e) {
+                const uint4 v = dl[e];
+                mma_bf16(d, ((uint64_t)v.y << 32) | v.x, ((uint64_t)v.w << 32) | v.z, idesc, e ? 1u : 0u);
             }
         }
         asm volatile(
@@ -615,7 +640,10 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     constexpr bool kCache = !tc_streamed(MT);
     const uint32_t tcache =
         x.tmem + ((32u * (uint32_t)x.q) << 16) + (uint32_t)(MT * C + 48 * MT * x.cgi);
-    bool stale = true;
+    // per chain pair: the carried tables are not those of the current states (a chain of the
+    // pair moved, or the work item just started); a warp rebuilds a pair's tables when any of
+    // its lanes needs it, the other pair's it reloads
+    bool stale[2] = {true, true};
     // chain x.tid's tracked and best energies and accept count live in shared memory (read and
     // written by that thread only)
     if (x.tid < nC) {
@@ -657,6 +685,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         return __uint_as_float((uint32_t)bits << 16);
     };
     write_b(k2);
+    if (x.tid == 0) tc_mma_descs<MT>(x);
     bool lf0 = false;   // cluster: a failed first MMA wait, reported through the first exchange
     if (alive) {
         tc_gemm_issue<MT, CL>(x);
@@ -755,8 +784,12 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         uint64_t part2[2] = {0ull, 0ull}, dpart2[2] = {0ull, 0ull};
         uint64_t kp2[MT][2];
         // 1. proposal draw (log2 q(x'|x) accumulated with a minus sign) from the carried factors
-        const bool fresh = !kCache || __any_sync(0xffffffffu, stale);
-        stale = false;
+        bool fresh[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            fresh[p] = !kCache || __any_sync(0xffffffffu, stale[p]);
+            stale[p] = false;
+        }
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             const int n = nd[t];
@@ -768,7 +801,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             for (int p = 0; p < 2; ++p) {
                 Table2<L> tb;
                 const uint32_t ta = tcache + 48u * t + 16u * p, te = tcache + 48u * t + 32u + 8u * p;
-                if (fresh) {
+                if (fresh[p]) {
                     factor_table_f2<L>(sl2[t][p], c2, inv2c, k2[t][p], tb);
                     if constexpr (kCache) table_store<L>(ta, te, tb);
                 } else {
@@ -917,7 +950,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             for (int h = 0; h < 2; ++h) {
                 const int c = cbase + 2 * p + h;
                 fl[h] = (FULL || c < nC) ? x.sacc[c] : 0;
-                if (fl[h] & 1) stale = true;   // x' taken: its factors are not the carried ones
+                if (fl[h] & 1) stale[p] = true;   // x' taken: its factors are not the carried ones
             }
             if constexpr (kReread) continue;
 #pragma unroll
@@ -1200,6 +1233,7 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     x.sfs = reinterpret_cast<int8_t *>(smem + lay.fref);
     x.skb = reinterpret_cast<int8_t *>(smem + lay.kb);
     x.sdg = reinterpret_cast<uint64_t *>(smem + lay.dg);
+    x.sdsc = reinterpret_cast<uint4 *>(smem + lay.dsc);
     x.nthr = blockDim.x;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.tmem);
