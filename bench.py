@@ -754,6 +754,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workload.WORKLOADS),
                     help="bench a parity-test configuration instead of the headline one")
     ap.add_argument("--graph", action="store_true", help="replay run_chains from a CUDA graph")
+    ap.add_argument("--no-pack", action="store_true",
+                    help="one launch per shape class, enqueued directly (no packed launch, no graph)")
     ap.add_argument("--engine", default="auto", choices=["auto", "tc", "simt"],
                     help="chain-kernel engine (auto: the library's per-class autotuner)")
     ap.add_argument("--refresh", type=int, default=None, help="FP64 energy refresh period")
@@ -817,7 +819,8 @@ def main():
                             engine=({"auto": pkg.MCMC_ENGINE_AUTO, "tc": pkg.MCMC_ENGINE_TC,
                                      "simt": pkg.MCMC_ENGINE_SIMT}[args.engine] if prec == precision
                                     else pkg.MCMC_ENGINE_AUTO)
-                            | (pkg.MCMC_ENGINE_GRAPH if args.graph else 0),
+                            | (pkg.MCMC_ENGINE_GRAPH if args.graph else 0)
+                            | ((pkg.MCMC_ENGINE_NO_PACK | pkg.MCMC_ENGINE_NO_GRAPH) if args.no_pack else 0),
                             tile=args.tile if (prec == precision and args.engine != "auto") else 0)
 
     def step(det):
@@ -962,6 +965,7 @@ def main():
                 "config": bench_config(args, w, B, world, refresh,
                                        "inputs larger than L2 (H = %d MB)" % (Hd.numel() * 4 // 2**20)),
                 "precision": precision, "graph": bool(args.graph), "engine": args.engine,
+                "launch_groups": det.launch_groups(),
                 "detections_per_s": det_per_s, "chain_kernel_ms": chain_ms,
                 "readout_ms": readout_ms,
                 "ber": ber, "snr_points_at_ber_le_1e-3": ber_ok, "chain_stats": chain_stats,

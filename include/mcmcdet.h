@@ -87,8 +87,8 @@ typedef struct {
                                drift; for measuring that drift) */
     int32_t split_terms;    /* MIXED: BF16 terms G is split into (2 = hi+lo, 3 = hi+lo+lo2) */
     int32_t engine;         /* MCMC_ENGINE_AUTO (autotuned per shape class), _SIMT or _TC, optionally
-                               OR-ed with MCMC_ENGINE_GRAPH, MCMC_ENGINE_NO_CLUSTER and
-                               MCMC_ENGINE_TRACE */
+                               OR-ed with the flags MCMC_ENGINE_GRAPH, _NO_CLUSTER, _TRACE,
+                               _NO_PACK and _NO_GRAPH */
     int32_t tile;           /* with an explicit engine: chains per work item (TC: 16 or 32, and 64
                                for channels with N = 2 Nt > 128, which run on thread-block
                                clusters; SIMT: a multiple of 8, at most 64); 0: the engine's
@@ -101,8 +101,11 @@ typedef struct {
  * autotuner found fastest when the class was first seen in the process (probe launches timed on
  * that batch at preprocess): for MIXED precision the tcgen05 kernel at 16 or 32 chains per CTA
  * (also 64 for N > 128) or the CUDA-core kernel (FP32 products, at least as accurate as the split-BF16 ones); for FP32 the
- * CUDA-core kernel's chain tile. SIMT / TC force an engine (TC requires MIXED). GRAPH: each
- * run_chains captures its launches (one per shape class) into a CUDA graph and replays it. */
+ * CUDA-core kernel's chain tile. SIMT / TC force an engine (TC requires MIXED). Tensor-core
+ * channels of N <= 64 of several shape classes with the same tile form one launch group (the
+ * packed kernel); every other shape class is a group of its own. A run with several groups
+ * enqueues them on parallel streams and, unless NO_GRAPH, replays them from one CUDA graph;
+ * GRAPH asks for the graph replay for any batch. */
 #define MCMC_ENGINE_AUTO 0
 #define MCMC_ENGINE_SIMT 1      /* CUDA-core chain kernel (FP64 / FP32 / MIXED) */
 #define MCMC_ENGINE_TC 2        /* tcgen05 chain kernel (MIXED, N <= 256) */
@@ -111,6 +114,12 @@ typedef struct {
                                     which streams the Gram operand from L2 every transition,
                                     instead of a thread-block cluster with one resident operand
                                     tile per CTA */
+#define MCMC_ENGINE_NO_PACK 32  /* flag: tensor-core channels of N <= 64 from several shape classes
+                                   run as one launch per class instead of one packed launch (a
+                                   persistent kernel pulling every class's work items, largest
+                                   first, from a device queue) */
+#define MCMC_ENGINE_NO_GRAPH 64 /* flag: a batch of several launch groups is enqueued directly
+                                   instead of being replayed from a CUDA graph */
 #define MCMC_ENGINE_TRACE 16    /* flag: every chain records the log acceptance ratio and the log
                                    uniform of its latest transition (Eq. (18)), read back with
                                    mcmc_detect_get_trace (parity diagnostics; one extra store per
@@ -212,6 +221,14 @@ mcmc_status mcmc_detect_get_trace(mcmc_detector *d, double *trace, int32_t host_
 /* Chain state import (checkpoint restore, or any start point): same layout as get_chains; every
  * level must lie in [0, L_b). Energies are recomputed in FP64. */
 mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32_t host_io);
+
+/* The launch groups of the current batch (after preprocess): returns their number and, for the
+ * first `cap` of them, six int32 per group in info: engine (MCMC_ENGINE_SIMT / _TC), chain tile
+ * (chains per group of threads or per work item), 1 if it is the packed launch of several shape
+ * classes, the largest N of its channels, its work items, and CTAs resident per SM (tcgen05:
+ * CTAs per cluster for thread-block clusters). The choices of the autotuner, per shape class,
+ * are what they show. 0 for NULL or before preprocess; info may be NULL. */
+int32_t mcmc_detect_launch_groups(const mcmc_detector *d, int32_t *info, int32_t cap);
 
 /* Waits for every call enqueued on the handle's stream; reports device faults. */
 mcmc_status mcmc_detect_synchronize(mcmc_detector *d);

@@ -20,7 +20,8 @@ from . import build as _build
 __all__ = [
     "Detector", "Config", "Stats", "lib", "load", "MCMC_PREC_FP64", "MCMC_PREC_FP32",
     "MCMC_PREC_MIXED", "MCMC_ENGINE_AUTO", "MCMC_ENGINE_SIMT", "MCMC_ENGINE_TC",
-    "MCMC_ENGINE_GRAPH", "MCMC_ENGINE_NO_CLUSTER", "MCMC_ENGINE_TRACE", "McmcError", "Mlp",
+    "MCMC_ENGINE_GRAPH", "MCMC_ENGINE_NO_CLUSTER", "MCMC_ENGINE_TRACE", "MCMC_ENGINE_NO_PACK",
+    "MCMC_ENGINE_NO_GRAPH", "McmcError", "Mlp",
     "ABI_FUNCTIONS", "ABI_FUNCTIONS_LEARNED", "ABI_FUNCTIONS_DIAG", "transition_diagnostics",
 ]
 
@@ -28,6 +29,8 @@ MCMC_PREC_FP64, MCMC_PREC_FP32, MCMC_PREC_MIXED = 0, 1, 2
 MCMC_ENGINE_AUTO, MCMC_ENGINE_SIMT, MCMC_ENGINE_TC, MCMC_ENGINE_GRAPH = 0, 1, 2, 4
 MCMC_ENGINE_NO_CLUSTER = 8
 MCMC_ENGINE_TRACE = 16
+MCMC_ENGINE_NO_PACK = 32
+MCMC_ENGINE_NO_GRAPH = 64
 _PREC = {"fp64": MCMC_PREC_FP64, "fp32": MCMC_PREC_FP32, "mixed": MCMC_PREC_MIXED}
 STATUS = {0: "MCMC_OK", 1: "MCMC_EINVAL", 2: "MCMC_ENOMEM", 3: "MCMC_ECUDA", 4: "MCMC_ETIMEOUT",
           5: "MCMC_ENUMERIC", 6: "MCMC_ESTATE", 7: "MCMC_EUNSUPPORTED"}
@@ -39,7 +42,7 @@ ABI_FUNCTIONS = [
     "mcmc_detect_set_chains", "mcmc_detect_synchronize", "mcmc_detect_destroy",
     "mcmc_status_string", "mcmc_detect_last_error", "mcmc_detect_kernel_launches",
     "mcmc_detect_noalloc", "mcmc_detect_llr_list", "mcmc_detect_get_tracked",
-    "mcmc_detect_get_trace",
+    "mcmc_detect_get_trace", "mcmc_detect_launch_groups",
 ]
 
 # Every entry point of include/mcmcdet_learned.h.
@@ -108,6 +111,8 @@ def load(path: Optional[str] = None):
     l.mcmc_detect_get_chains.restype = ctypes.c_int
     l.mcmc_detect_get_tracked.argtypes = [vp, vp, vp, i32]
     l.mcmc_detect_get_tracked.restype = ctypes.c_int
+    l.mcmc_detect_launch_groups.argtypes = [vp, vp, i32]
+    l.mcmc_detect_launch_groups.restype = ctypes.c_int32
     l.mcmc_detect_get_trace.argtypes = [vp, vp, i32]
     l.mcmc_detect_get_trace.restype = ctypes.c_int
     l.mcmc_detect_set_chains.argtypes = [vp, vp, i32]
@@ -317,6 +322,14 @@ class Detector:
             host_io = _is_host(trace)
         self._check(self._l.mcmc_detect_get_trace(self._h, _ptr(trace), int(host_io)))
         return trace
+
+    def launch_groups(self):
+        """The batch's launch groups: dicts of engine, tile, packed, max_n, items, ctas_per_sm."""
+        n = int(self._l.mcmc_detect_launch_groups(self._h, None, 0))
+        buf = (ctypes.c_int32 * (6 * max(n, 1)))()
+        self._l.mcmc_detect_launch_groups(self._h, buf, n)
+        keys = ("engine", "tile", "packed", "max_n", "items", "ctas_per_sm")
+        return [dict(zip(keys, buf[6 * i:6 * i + 6])) for i in range(n)]
 
     def set_chains(self, states, *, host_io: Optional[bool] = None):
         if host_io is None:

@@ -43,6 +43,7 @@ struct Group {
     bool bt_smem = false;      // SIMT: GEMM operand staged in shared memory
     size_t smem = 0;           // SIMT: dynamic shared memory
     int max_n = 0, max_nop = 0;
+    bool packed = false;       // TC: the packed kernel over several one-tile shape classes
     std::vector<WorkItem> items;
     DevBuf d_items;
 };
@@ -59,6 +60,10 @@ struct mcmc_detector {
     mcmc_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // a run with several launch groups forks them onto these streams (parallel graph branches)
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
     int device = 0;
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
@@ -86,7 +91,8 @@ struct mcmc_detector {
     // device workspace
     DevBuf d_desc, d_Gc, d_zc, d_Mc, d_gj, d_yy, d_G64, d_GM64, d_z64, d_w64, d_z32,
         d_w32, d_bt32, d_bt64, d_tc, d_states, d_best_states, d_f, d_best_f, d_accepts,
-        d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp, d_fx, d_trace;
+        d_misc, d_in_H, d_in_y, d_in_s2, d_out_idx, d_out_llr, d_out_bf, d_dexp, d_fx, d_trace,
+        d_queue;
     HostBuf h_stage;
     // pinned staging ring for the per-batch tables (descriptors, work items): a slot is rewritten
     // only after the copy that last read it has completed
@@ -359,7 +365,10 @@ Choice default_choice(const mcmc_detector *d, const ChannelDesc &c)
     return Choice{MCMC_ENGINE_SIMT, simt_default_tile(d, c.N, c.NOp)};
 }
 
-// Groups of channels with one engine and one launch shape; items cover every chain.
+// Groups of channels with one engine and one launch shape; items cover every chain. Tensor-core
+// channels of N <= 64 (one 128-row operand tile) of several shape classes with the same tile are
+// packed into one group run by the packed kernel, which pulls their work items, largest first,
+// from a device queue (unless MCMC_ENGINE_NO_PACK).
 mcmc_status build_groups(mcmc_detector *d)
 {
     const int Np = d->cfg.chains;
@@ -378,10 +387,52 @@ mcmc_status build_groups(mcmc_detector *d)
         }
         last_v->push_back(b);
     }
+    // one-tile tensor-core classes per tile: packed when there are two or more
+    std::map<int, std::vector<GroupKey>> one_tile;
+    if (!(d->cfg.engine & MCMC_ENGINE_NO_PACK))
+        for (auto &kv : by)
+            if (std::get<0>(kv.first) == MCMC_ENGINE_TC && std::get<2>(kv.first) <= 64)
+                one_tile[std::get<1>(kv.first)].push_back(kv.first);
     // keep the work-item buffers: freeing device memory would synchronise the device
     for (auto &g : d->groups)
         if (g.d_items.p) d->spare_items.push_back(g.d_items);
     d->groups.clear();
+    auto finish = [&](Group &g) -> mcmc_status {
+        if (!d->spare_items.empty()) {
+            g.d_items = d->spare_items.back();
+            d->spare_items.pop_back();
+        }
+        CK(ensure(g.d_items, sizeof(WorkItem) * g.items.size()), "alloc items");
+        CK(upload(d, g.d_items.p, g.items.data(), sizeof(WorkItem) * g.items.size()), "copy items");
+        d->groups.push_back(std::move(g));
+        return MCMC_OK;
+    };
+    for (auto &tk : one_tile) {
+        if (tk.second.size() < 2) continue;
+        Group g;
+        g.engine = MCMC_ENGINE_TC;
+        g.tile = tk.first;
+        g.packed = true;
+        if (!tc_make_plan_packed(g.tile, d->cfg.split_terms, d->smem_optin, &g.plan)) continue;
+        for (const GroupKey &k : tk.second) {
+            for (int b : by[k]) {
+                const ChannelDesc &c = d->desc[b];
+                g.max_n = std::max(g.max_n, c.N);
+                g.max_nop = std::max(g.max_nop, c.NOp);
+                const int per = (c.N <= 32 ? 2 : 1) * g.tile;
+                for (int c0 = 0; c0 < Np; c0 += per)
+                    g.items.push_back(WorkItem{b, c0, std::min(per, Np - c0), 0});
+            }
+            by.erase(k);
+        }
+        // largest work first (chains x dimensions x levels), so that the queue ends on small items
+        std::stable_sort(g.items.begin(), g.items.end(), [&](const WorkItem &a, const WorkItem &b) {
+            const ChannelDesc &ca = d->desc[a.b], &cb = d->desc[b.b];
+            return (long long)a.nc * ca.N * ca.L > (long long)b.nc * cb.N * cb.L;
+        });
+        mcmc_status st = finish(g);
+        if (st != MCMC_OK) return st;
+    }
     for (auto &kv : by) {
         Group g;
         g.engine = std::get<0>(kv.first);
@@ -405,13 +456,21 @@ mcmc_status build_groups(mcmc_detector *d)
         for (int b : kv.second)
             for (int c0 = 0; c0 < Np; c0 += per)
                 g.items.push_back(WorkItem{b, c0, std::min(per, Np - c0), 0});
-        if (!d->spare_items.empty()) {
-            g.d_items = d->spare_items.back();
-            d->spare_items.pop_back();
-        }
-        CK(ensure(g.d_items, sizeof(WorkItem) * g.items.size()), "alloc items");
-        CK(upload(d, g.d_items.p, g.items.data(), sizeof(WorkItem) * g.items.size()), "copy items");
-        d->groups.push_back(std::move(g));
+        mcmc_status st = finish(g);
+        if (st != MCMC_OK) return st;
+    }
+    // one queue counter per group (the packed kernel's), and the streams / events that let a
+    // run's groups proceed in parallel
+    CK(ensure(d->d_queue, 4 * d->groups.size()), "alloc queues");
+    const size_t need = d->groups.size() > 1 ? d->groups.size() - 1 : 0;
+    if (need && !d->ev_fork) CK(cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming), "event");
+    while (d->aux.size() < need) {
+        cudaStream_t s = nullptr;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "aux stream");
+        d->aux.push_back(s);
+        cudaEvent_t e = nullptr;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        d->ev_join.push_back(e);
     }
     return MCMC_OK;
 }
@@ -449,7 +508,7 @@ ChainArgs chain_args(mcmc_detector *d, int32_t iterations, int64_t t_offset)
     return ca;
 }
 
-cudaError_t launch_group(mcmc_detector *d, const Group &g, ChainArgs ca)
+cudaError_t launch_group(mcmc_detector *d, const Group &g, ChainArgs ca, cudaStream_t s, int *queue)
 {
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
     ca.items = static_cast<const WorkItem *>(g.d_items.p);
@@ -458,8 +517,15 @@ cudaError_t launch_group(mcmc_detector *d, const Group &g, ChainArgs ca)
     ca.max_n = g.max_n;
     ca.max_nop = g.max_nop;
     ca.bt_in_smem = g.bt_smem;
-    if (g.engine == MCMC_ENGINE_TC) return tc_launch_chains(ca, g.plan, d->stream);
-    return launch_chains_simt(ca, fp64, g.smem, d->stream);
+    if (g.engine == MCMC_ENGINE_TC) {
+        if (g.packed) {
+            cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+            if (e != cudaSuccess) return e;
+            ca.queue = queue;
+        }
+        return tc_launch_chains(ca, g.plan, s);
+    }
+    return launch_chains_simt(ca, fp64, g.smem, s);
 }
 
 // Autotuner: for every shape class not seen before (in this process, for this configuration),
@@ -526,10 +592,10 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
             ca.init_f = 1;
             ca.near_ties = nullptr;   // probe transitions are not the batch's
             ca.trace = nullptr;
-            cudaError_t e = launch_group(d, g, ca);                 // warm-up
+            cudaError_t e = launch_group(d, g, ca, d->stream, nullptr);   // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, d->stream);
             ca.iterations = 24;   // long enough to amortise per-item set-up (streamed operands)
-            if (e == cudaSuccess) e = launch_group(d, g, ca);
+            if (e == cudaSuccess) e = launch_group(d, g, ca, d->stream, nullptr);
             if (e == cudaSuccess) e = cudaEventRecord(e1, d->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -617,7 +683,8 @@ mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out)
         cfg->precision < MCMC_PREC_FP64 || cfg->precision > MCMC_PREC_MIXED ||
         (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < -1 ||
         cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 ||
-        (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH | MCMC_ENGINE_NO_CLUSTER | MCMC_ENGINE_TRACE)) != 0 ||
+        (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH | MCMC_ENGINE_NO_CLUSTER | MCMC_ENGINE_TRACE |
+                         MCMC_ENGINE_NO_PACK | MCMC_ENGINE_NO_GRAPH)) != 0 ||
         (cfg->engine & 3) == 3 ||
         cfg->tile < 0 || (cfg->tile != 0 && (cfg->engine & 3) == MCMC_ENGINE_AUTO) ||
         ((cfg->engine & 3) == MCMC_ENGINE_TC && cfg->tile != 0 && cfg->tile != 16 && cfg->tile != 32 &&
@@ -669,7 +736,7 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
                       &d->d_bt32, &d->d_bt64, &d->d_tc, &d->d_states, &d->d_best_states, &d->d_f,
                       &d->d_best_f, &d->d_accepts, &d->d_misc, &d->d_in_H, &d->d_in_y,
                       &d->d_in_s2, &d->d_out_idx, &d->d_out_llr, &d->d_out_bf, &d->d_dexp,
-                      &d->d_fx, &d->d_trace,
+                      &d->d_fx, &d->d_trace, &d->d_queue,
                       &d->d_mx_gx, &d->d_mx_px, &d->d_mx_gxp, &d->d_mx_pxp, &d->d_mx_prop,
                       &d->d_mx_X, &d->d_mx_logits, &d->d_mx_lqf};
     for (DevBuf *b : bufs)
@@ -684,6 +751,9 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
         if (d->up_done[k]) cudaEventDestroy(d->up_done[k]);
         if (d->h_up[k].p) cudaFreeHost(d->h_up[k].p);
     }
+    for (cudaStream_t a : d->aux) cudaStreamDestroy(a);
+    for (cudaEvent_t e : d->ev_join) cudaEventDestroy(e);
+    if (d->ev_fork) cudaEventDestroy(d->ev_fork);
     if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
     cudaGetLastError();
     delete d;
@@ -956,22 +1026,40 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         fr.drift_bits = drift_ptr(d);
         fr.drift_rel_bits = drift_rel_ptr(d);
     }
-    if (d->cfg.engine & MCMC_ENGINE_GRAPH) {
-        // every group's launch (and the final refresh) captured into one graph, replayed on the
-        // handle's stream
+    // every group's launch, forked onto its own stream when there are several (parallel
+    // branches: the groups' kernels share the GPU instead of running one after the other), then
+    // the final refresh once all have joined
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        const size_t ng = d->groups.size();
+        int *queues = P<int>(d->d_queue);
+        if (ng > 1) e = cudaEventRecord(d->ev_fork, d->stream);
+        for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+            cudaStream_t s = gi == 0 ? d->stream : d->aux[gi - 1];
+            if (gi > 0) e = cudaStreamWaitEvent(s, d->ev_fork, 0);
+            if (e == cudaSuccess) e = launch_group(d, d->groups[gi], ca, s, queues + gi);
+            if (e == cudaSuccess && gi > 0) e = cudaEventRecord(d->ev_join[gi - 1], s);
+        }
+        for (size_t gi = 1; gi < ng && e == cudaSuccess; ++gi)
+            e = cudaStreamWaitEvent(d->stream, d->ev_join[gi - 1], 0);
+        if (e == cudaSuccess && final_refresh) e = launch_refresh(fr, d->stream);
+        return e;
+    };
+    // one CUDA graph per run (replayed; updated in place when only the arguments changed) when
+    // asked for, and by default for a batch of several launch groups
+    const bool graph = (d->cfg.engine & MCMC_ENGINE_GRAPH) ||
+                       (d->groups.size() > 1 && !(d->cfg.engine & MCMC_ENGINE_NO_GRAPH));
+    if (graph) {
         CK(cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        cudaError_t le = cudaSuccess;
-        for (const Group &g : d->groups)
-            if (le == cudaSuccess) le = launch_group(d, g, ca);
-        if (le == cudaSuccess && final_refresh) le = launch_refresh(fr, d->stream);
-        cudaGraph_t graph = nullptr;
-        const cudaError_t ce = cudaStreamEndCapture(d->stream, &graph);
-        if (le != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(d, le, "chain kernel"); }
+        const cudaError_t le = enqueue();
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(d->stream, &g);
+        if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(d, le, "chain kernel"); }
         CK(ce, "end capture");
         bool updated = false;
         if (d->graph) {
             cudaGraphExecUpdateResultInfo info{};
-            updated = cudaGraphExecUpdate(d->graph, graph, &info) == cudaSuccess;
+            updated = cudaGraphExecUpdate(d->graph, g, &info) == cudaSuccess;
             if (!updated) {
                 cudaGetLastError();
                 cudaGraphExecDestroy(d->graph);
@@ -979,22 +1067,15 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
             }
         }
         if (!updated) {
-            const cudaError_t ie = cudaGraphInstantiate(&d->graph, graph, 0);
-            if (ie != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(d, ie, "instantiate graph"); }
+            const cudaError_t ie = cudaGraphInstantiate(&d->graph, g, 0);
+            if (ie != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(d, ie, "instantiate graph"); }
         }
-        cudaGraphDestroy(graph);
+        cudaGraphDestroy(g);
         CK(cudaGraphLaunch(d->graph, d->stream), "graph launch");
-        d->launches += (long long)d->groups.size() + (final_refresh ? 1 : 0);
     } else {
-        for (const Group &g : d->groups) {
-            CK(launch_group(d, g, ca), g.engine == MCMC_ENGINE_TC ? "tensor-core chain kernel" : "chain kernel");
-            d->launches++;
-        }
-        if (final_refresh) {
-            CK(launch_refresh(fr, d->stream), "final energies");
-            d->launches++;
-        }
+        CK(enqueue(), "chain kernel");
     }
+    d->launches += (long long)d->groups.size() + (final_refresh ? 1 : 0);
     d->f_valid = true;
     d->f_exact = fp64 || final_refresh;
     d->d_valid = !fp64;
@@ -1192,6 +1273,23 @@ mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32
     d->f_exact = true;
     d->d_valid = false;
     return read_status(d);
+}
+
+int32_t mcmc_detect_launch_groups(const mcmc_detector *d, int32_t *info, int32_t cap)
+{
+    if (!d || !d->prepared) return 0;
+    const int32_t n = (int32_t)d->groups.size();
+    for (int32_t i = 0; i < n && info && i < cap; ++i) {
+        const Group &g = d->groups[(size_t)i];
+        int32_t *r = info + 6 * i;
+        r[0] = g.engine;
+        r[1] = g.tile;
+        r[2] = g.packed ? 1 : 0;
+        r[3] = g.max_n;
+        r[4] = (int32_t)g.items.size();
+        r[5] = g.engine == MCMC_ENGINE_TC ? (g.plan.cluster > 1 ? g.plan.cluster : g.plan.ctas_per_sm) : 0;
+    }
+    return n;
 }
 
 mcmc_status mcmc_detect_synchronize(mcmc_detector *d)

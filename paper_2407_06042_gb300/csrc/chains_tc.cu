@@ -83,6 +83,10 @@ struct TcLayout {
 // two buffers.
 __host__ __device__ constexpr bool tc_streamed(int MT) { return MT >= 3; }
 
+// Row stride (bytes) of the per-chain state copies in shared memory (best visited state, the
+// states of an FP64 refresh): the CTA's dimensions, 64 per tile (a cluster CTA: its own 64).
+__host__ __device__ constexpr int tc_state_stride(int MT, int CL) { return CL > 1 ? 64 : 64 * MT; }
+
 // Chain groups per CTA: channels of N <= 32 use half of the 64 dimension rows of a tile, so the
 // tile holds their rows twice and each copy serves its own group of chains.
 __host__ __device__ inline int tc_groups(int N) { return (N + 15) / 16 * 16 <= 32 ? 2 : 1; }
@@ -109,8 +113,8 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C, int 
     L.tie = take((uint32_t)C * 12, 16);      // near-tie counts per chain slot, three windows
     // states for the FP64 refresh (a cluster CTA reads them from its B operand instead) and the
     // best visited state of every chain (a cluster CTA: its own 64 dimensions)
-    L.fref = take(CL > 1 ? 0u : (uint32_t)C * kMaxN, 16);
-    L.kb = take((uint32_t)C * (CL > 1 ? 64u : (uint32_t)kMaxN), 16);
+    L.fref = take(CL > 1 ? 0u : (uint32_t)C * tc_state_stride(MT, CL), 16);
+    L.kb = take((uint32_t)C * tc_state_stride(MT, CL), 16);
     // streamed kernels: Gt x of every thread's (tile, chain pair), [2 MT][threads] packed pairs
     L.dg = take(tc_streamed(MT) ? (uint32_t)(2 * MT) * (16u * C) * 8u : 0u, 16);
     // cluster exchange slots: [2 alternating buffers][CL ranks][C chains] x 16 bytes
@@ -119,7 +123,7 @@ __host__ __device__ inline TcLayout tc_layout(int S, int MT, int Kp, int C, int 
     L.dsc = take(tc_streamed(MT) ? 0u : (uint32_t)(S * MT * (Kp / 16)) * 16u, 16);
     // TMA, MMA, streamed chunks full[2] / empty[2], cluster B slices and exchange
     L.bar = take(8 * 8, 8);
-    L.tmem = take(4, 4);
+    L.tmem = take(8, 4);                     // TMEM base address, work-queue item (packed kernel)
     L.total = (o + 127) / 128 * 128;
     return L;
 }
@@ -604,8 +608,9 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         if constexpr (kDgSmem) x.sdg[(2 * t + p) * x.nthr + x.tid] = v;
         else Dg2r[t][p] = v;
     };
-    int8_t *skb = x.skb;   // best visited states [C][kMaxN] (cluster CTAs: [C][64], own dimensions)
-    auto kbi = [&](int c, int n) { return CL > 1 ? c * 64 + (n & 63) : c * kMaxN + n; };
+    int8_t *skb = x.skb;   // best visited states [C][64 MT] (cluster CTAs: [C][64], own dimensions)
+    constexpr int kKs = tc_state_stride(MT, CL);
+    auto kbi = [&](int c, int n) { return CL > 1 ? c * 64 + (n & 63) : c * kKs + n; };
     const float *gz = reinterpret_cast<const float *>(A.z) + d.vec_off;
     const float *gw = reinterpret_cast<const float *>(A.w) + d.vec_off;
     uint32_t boff[MT];                             // byte offset of this thread's B element, chain cbase
@@ -1154,7 +1159,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 f2_unpack(k2[t][1], kv[2], kv[3]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (live[t][j]) x.sfs[(cbase + j) * kMaxN + nd[t]] = (int8_t)kv[j];
+                    if (live[t][j]) x.sfs[(cbase + j) * kKs + nd[t]] = (int8_t)kv[j];
             }
             __syncthreads();
             const double *Gm = A.G64 + d.mat_off;
@@ -1162,7 +1167,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
             for (int c = x.warp; c < nC; c += blockDim.x >> 5) {
                 double quad, lin;
                 quad_lin_fp64(Gm, z, N, x.lane,
-                              [&](int n) { return (double)odd_of(x.sfs[c * kMaxN + n], L); }, quad, lin);
+                              [&](int n) { return (double)odd_of(x.sfs[c * kKs + n], L); }, quad, lin);
 #pragma unroll
                 for (int o = 16; o; o >>= 1) {
                     quad += __shfl_xor_sync(0xffffffffu, quad, o);
@@ -1213,6 +1218,10 @@ __device__ __forceinline__ void tc_item_dispatch(const ChainArgs &A, TcCtx &x, c
 
 // G: chain groups per CTA (2 for N <= 32, one tile); C: chains per CTA over all groups.
 // CL > 1: one CTA of a cluster of CL (MT = 1 local tile of a channel with CL tiles).
+// G = 0: the packed kernel for a batch of uneven one-tile channels (N <= 64): every CTA pulls
+// work items from a device queue (largest first) and takes each item's chain groups (1 or 2,
+// by N), K extent and operand layouts from its channel; C is then the largest chains per CTA
+// (two groups of C / 2) and Kp = 64, the extents the shared memory and TMEM are sized for.
 template <int MT, int G, int CL>
 __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL == 1 ? TC_MIN_BLOCKS : 1)
     chains_tc_kernel(const ChainArgs A, const int C, const int S, const int Kp)
@@ -1247,8 +1256,10 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     x.cgi = x.warp >> 2;
     x.h = x.lane >> 4;
     x.dl = x.lane & 15;
+    constexpr bool kPacked = G == 0;
+    static_assert(!kPacked || (MT == 1 && CL == 1), "the packed kernel runs one-tile items");
     x.C = C;
-    x.gofs = G == 1 ? 0 : (x.q >> 1) * (C / G);   // first chain of this thread's group
+    x.gofs = G == 2 ? (x.q >> 1) * (C / 2) : 0;   // first chain of this thread's group
     x.S = S;
     x.Kp = Kp;
     x.sbo_a = (uint32_t)(Kp / 8) * 128u;
@@ -1304,11 +1315,35 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
     if constexpr (CL > 1) cl_sync();
     const int item0 = CL > 1 ? (int)cl_id() : (int)blockIdx.x;
     const int istep = CL > 1 ? (int)cl_count() : (int)gridDim.x;
+    volatile int *qslot = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
-    for (int item = item0; item < A.n_items && alive; item += istep) {
+    for (int item = item0; alive; item += istep) {
+        if constexpr (kPacked) {
+            // the next item of the batch's queue (every CTA of the launch draws from it)
+            if (x.tid == 0) *qslot = atomicAdd(A.queue, 1);
+            __syncthreads();
+            item = *qslot;
+            __syncthreads();
+        }
+        if (item >= A.n_items) break;
         const WorkItem it = A.items[item];
         const ChannelDesc d = A.desc[it.b];
         x.asrc = A.tc_ops + d.tc_off;
+        if constexpr (kPacked) {
+            // this item's chain groups and K extent, and the operand layouts that follow from them
+            const int g = tc_groups(d.N), tile = C / 2, kp = (d.N + 15) / 16 * 16;
+            x.C = g * tile;
+            x.gofs = g == 1 ? 0 : (x.q >> 1) * tile;
+            x.Kp = kp;
+            x.sbo_a = (uint32_t)(kp / 8) * 128u;
+            x.sbo_b = b_sbo(kp);
+            x.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(x.C >> 3) << 17) |
+                      ((uint32_t)(128 >> 4) << 24);
+            // the B operand's layout follows K: clear it, so that padding stays zero (the
+            // previous item's MMAs have completed; the staging barrier below orders the rest)
+            for (int e = x.tid; e < (int)(lay.red - lay.b) / 16; e += blockDim.x)
+                reinterpret_cast<uint4 *>(x.sB)[e] = make_uint4(0, 0, 0, 0);
+        }
         if constexpr (tc_streamed(MT)) {
             // chunks are streamed by the transitions themselves
             switch (d.L) {
@@ -1333,10 +1368,26 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
         }
         x.tma_phase ^= 1u;
         if (!alive) break;
-        switch (d.L) {
-        case 2: tc_item_dispatch<MT, 2, G, CL>(A, x, it, d, alive); break;
-        case 4: tc_item_dispatch<MT, 4, G, CL>(A, x, it, d, alive); break;
-        default: tc_item_dispatch<MT, 8, G, CL>(A, x, it, d, alive); break;
+        if constexpr (kPacked) {
+            if (tc_groups(d.N) == 2) {
+                switch (d.L) {
+                case 2: tc_item_dispatch<1, 2, 2, 1>(A, x, it, d, alive); break;
+                case 4: tc_item_dispatch<1, 4, 2, 1>(A, x, it, d, alive); break;
+                default: tc_item_dispatch<1, 8, 2, 1>(A, x, it, d, alive); break;
+                }
+            } else {
+                switch (d.L) {
+                case 2: tc_item_dispatch<1, 2, 1, 1>(A, x, it, d, alive); break;
+                case 4: tc_item_dispatch<1, 4, 1, 1>(A, x, it, d, alive); break;
+                default: tc_item_dispatch<1, 8, 1, 1>(A, x, it, d, alive); break;
+                }
+            }
+        } else {
+            switch (d.L) {
+            case 2: tc_item_dispatch<MT, 2, G, CL>(A, x, it, d, alive); break;
+            case 4: tc_item_dispatch<MT, 4, G, CL>(A, x, it, d, alive); break;
+            default: tc_item_dispatch<MT, 8, G, CL>(A, x, it, d, alive); break;
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -1521,6 +1572,33 @@ bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_op
     return true;
 }
 
+bool tc_make_plan_packed(int tile, int split_terms, size_t smem_optin, TcPlan *plan)
+{
+    *plan = TcPlan{};
+    if (tile < 16 || tile > 32 || tile % 16 || 16 * tile > TC_MAX_THREADS) return false;
+    const int Kp = 64, Ct = 2 * tile, S = split_terms;
+    const TcLayout L = tc_layout(S, 1, Kp, Ct);
+    if (L.total > smem_optin) return false;
+    plan->valid = 1;
+    plan->packed = 1;
+    plan->chains_per_cta = Ct;
+    plan->groups = 0;
+    plan->m_tiles = 1;
+    plan->kdim = Kp;
+    plan->max_n = 64;
+    plan->split_terms = S;
+    plan->threads = 16 * tile;
+    // accumulators of two groups and the carried factors of the threads' chains
+    plan->tmem_cols = pow2_at_least(Ct + tc_table_cols(1, tile));
+    const int regs = std::min(255, 65536 / (TC_MIN_BLOCKS * TC_MAX_THREADS) / 8 * 8);
+    const int by_smem = (int)(228 * 1024 / (L.total + 1024));
+    const int by_thr = std::min(2048 / plan->threads, 65536 / (plan->threads * regs));
+    plan->ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_thr), 512 / plan->tmem_cols));
+    plan->smem = L.total;
+    plan->cluster = 1;
+    return true;
+}
+
 long long tc_operand_bytes(int N, int split_terms)
 {
     if (N > kMaxN) return 0;
@@ -1573,7 +1651,10 @@ cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStre
         return cudaSuccess;
     };
     switch (plan.m_tiles) {
-    case 1: e = plan.groups == 2 ? go(chains_tc_kernel<1, 2, 1>) : go(chains_tc_kernel<1, 1, 1>); break;
+    case 1:
+        e = plan.packed ? go(chains_tc_kernel<1, 0, 1>)
+                        : plan.groups == 2 ? go(chains_tc_kernel<1, 2, 1>) : go(chains_tc_kernel<1, 1, 1>);
+        break;
     case 2: e = go(chains_tc_kernel<2, 1, 1>); break;
     case 3: e = go(chains_tc_kernel<3, 1, 1>); break;
     default: e = go(chains_tc_kernel<4, 1, 1>); break;

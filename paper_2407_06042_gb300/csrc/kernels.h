@@ -104,6 +104,7 @@ struct ChainArgs {
     const uint8_t *tc_ops;  // per-channel packed BF16 operand blocks
     int split_terms;
     int tc_tmem_cols;       // TMEM columns each CTA allocates
+    int *queue;             // packed kernel: the next work item to hand out (zero at launch)
     uint32_t philox_rk[2 * kPhiloxRounds];   // round keys of (key0, key1), set at launch
 };
 

@@ -24,6 +24,8 @@ struct TcPlan {
                             // tile per CTA, chains_per_cta 16, 32 or 64), else 1
     int max_clusters;       // clusters that can be resident at once (queried when planning, so
                             // that launches, also inside a stream capture, need no query)
+    int packed;             // 1: the packed kernel (one-tile items of every N <= 64 from a work
+                            // queue); chains_per_cta is then two groups of the tile
 };
 
 // Kernel shape for a group of channels with the same K extent (N rounded up to 16) and tile
@@ -33,6 +35,11 @@ struct TcPlan {
 // 64 chains per CTA are allowed too), else the single-CTA kernel that streams the operand from L2.
 bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, bool allow_cluster,
                   TcPlan *plan);
+
+// Kernel shape of the packed launch: one persistent kernel for every channel of N <= 64 in a
+// batch (one or two chain groups of `tile` chains per item, by N; K extent up to 64), whose CTAs
+// pull work items from a device queue. False if it does not fit.
+bool tc_make_plan_packed(int tile, int split_terms, size_t smem_optin, TcPlan *plan);
 
 // Bytes of one channel's packed BF16 operand block (depends on its N only).
 long long tc_operand_bytes(int N, int split_terms);

@@ -64,6 +64,7 @@ def test_host_only_entry_points():
     assert lib.mcmc_detect_create(None, None) == 1
     assert lib.mcmc_detect_get_tracked(None, None, None, 0) == 1
     assert lib.mcmc_detect_get_trace(None, None, 0) == 1
+    assert lib.mcmc_detect_launch_groups(None, None, 0) == 0
 
 
 def test_config_struct_matches_header():
@@ -124,7 +125,7 @@ def test_config_validation_on_the_host():
                dict(precision=MIXED, engine=AUTO | NOCL),
                dict(precision=FP32, engine=pkg.MCMC_ENGINE_SIMT, tile=64)]:
         assert create(**kw) in (0, 7), kw
-    for kw in [dict(engine=32), dict(engine=3), dict(precision=MIXED, engine=TC, tile=48),
+    for kw in [dict(engine=128), dict(engine=3), dict(precision=MIXED, engine=TC, tile=48),
                dict(precision=MIXED, engine=AUTO, tile=64), dict(precision=FP32, engine=TC),
                dict(max_nt=129), dict(chains=6), dict(split_terms=4),
                dict(refresh_period=-2)]:
