@@ -119,19 +119,18 @@ _PEAKS = None
 
 def pipe_peaks():
     """Measured pipe throughputs of this GPU (ops/s): MUFU ex2, FP32 FMA, FP32x2 FMA lanes, FP64
-    FMA, integer three-input XOR, 32x32->64 products, and whole Philox4x32-10 blocks (measured
-    once per process)."""
+    FMA, 32x32->64 products, and whole Philox4x32-10 blocks (measured once per process)."""
     global _PEAKS
     if _PEAKS is not None:
         return _PEAKS
     import ctypes
     from paper_2407_06042_gb300 import build as _b
     lib = ctypes.CDLL(_b.build_peaks())
-    out = (ctypes.c_double * 7)()
+    out = (ctypes.c_double * 6)()
     if lib.mcmc_pipe_peaks(out) != 0:
         return None
     _PEAKS = {"ex2": out[0], "fma": out[1], "fma2_lanes": out[2], "dfma": out[3],
-              "xor3": out[4], "mulwide": out[5], "philox": out[6]}
+              "mulwide": out[4], "philox": out[5]}
     return _PEAKS
 
 

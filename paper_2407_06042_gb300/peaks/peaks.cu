@@ -1,6 +1,6 @@
 // peaks.cu -- pipe-throughput microbenchmarks used as roofline denominators by bench.py:
 // MUFU ex2 (the transcendental unit that evaluates every proposal weight), FP32 FMA, packed
-// FP32x2 FMA, FP64 FMA, the integer ALU (three-input XOR) and wide-multiply rates, and whole
+// FP32x2 FMA, FP64 FMA, the wide-multiply rate of the integer pipe, and whole
 // Philox4x32-10 blocks (the method's random numbers), each as sustained operations per second
 // over the whole GPU with enough independent chains per thread to hide latency.
 #include <cstdint>
@@ -85,23 +85,6 @@ __global__ void dfma_kernel(float *out, int iters)
     if (s == 12345.0) out[0] = (float)s;
 }
 
-// Integer ALU: three-input XORs (one LOP3 each), the logic half of a Philox round.
-__global__ void xor3_kernel(float *out, int iters)
-{
-    uint32_t v[kChains];
-#pragma unroll
-    for (int i = 0; i < kChains; ++i) v[i] = threadIdx.x * 2654435761u + (uint32_t)i;
-    const uint32_t a = 0x9E3779B9u ^ blockIdx.x, b = 0xBB67AE85u;
-    for (int it = 0; it < iters; ++it) {
-#pragma unroll
-        for (int i = 0; i < kChains; ++i) v[i] = v[i] ^ (a + (uint32_t)i) ^ (b >> (i & 3));
-    }
-    uint32_t s = 0;
-#pragma unroll
-    for (int i = 0; i < kChains; ++i) s ^= v[i];
-    if (s == 12345u) out[0] = (float)s;
-}
-
 // 32 x 32 -> 64-bit products (low and high words), the arithmetic half of a Philox round.
 __global__ void mulwide_kernel(float *out, int iters)
 {
@@ -183,7 +166,7 @@ double rate(K kern, int blocks, int threads, int iters, double ops_per_thread_it
 }  // namespace
 
 // out[0] ex2/s, out[1] FP32 FMA/s (one FMA = 1 op), out[2] FP32x2 FMA lanes/s, out[3] FP64 FMA/s,
-// out[4] three-input XORs/s, out[5] 32 x 32 -> 64-bit products/s, out[6] Philox4x32-10 blocks/s.
+// out[4] 32 x 32 -> 64-bit products/s, out[5] Philox4x32-10 blocks/s.
 extern "C" int mcmc_pipe_peaks(double *out)
 {
     int dev = 0, sms = 0;
@@ -194,8 +177,7 @@ extern "C" int mcmc_pipe_peaks(double *out)
     out[1] = rate(fma_kernel, blocks, threads, 16384, kChains);
     out[2] = rate(fma2_kernel, blocks, threads, 8192, 2.0 * kChains);
     out[3] = rate(dfma_kernel, blocks, threads, 256, kChains);
-    out[4] = rate(xor3_kernel, blocks, threads, 8192, kChains);
-    out[5] = rate(mulwide_kernel, blocks, threads, 4096, kChains);
-    out[6] = rate(philox_kernel, blocks, threads, 256, 2.0);
+    out[4] = rate(mulwide_kernel, blocks, threads, 4096, kChains);
+    out[5] = rate(philox_kernel, blocks, threads, 256, 2.0);
     return 0;
 }
