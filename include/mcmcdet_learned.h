@@ -65,6 +65,15 @@ mcmc_status mcmc_mlp_create(int32_t qam, int32_t max_rows, void *stream, mcmc_ml
 mcmc_status mcmc_mlp_destroy(mcmc_mlp *m);
 const char *mcmc_mlp_last_error(const mcmc_mlp *m);
 
+/* Engine of the matrix products of training (loss_grad, train_step) and of the CUDA-core
+ * forward: the three layers' products, the input gradients and the weight gradients summed over
+ * the rows. tensor_cores = 1 (the default on sm_103): tcgen05 tiles of 128 x 64, 128 or 256 with
+ * each FP32 operand split into two BF16 terms (hi + lo, about 2^-17 relative) and the products
+ * hi*hi + hi*lo + lo*hi accumulated in FP32; 0: the FP32 CUDA-core kernel. The bias gradients
+ * (column sums) run on CUDA cores either way. Both engines are deterministic.
+ * MCMC_EUNSUPPORTED for 1 without sm_103. */
+mcmc_status mcmc_mlp_set_train_engine(mcmc_mlp *m, int32_t tensor_cores);
+
 /* Copies the flat parameter vector in or out (host_io = 1: host pointer, synchronous). Setting
  * the parameters resets the Adam state. */
 mcmc_status mcmc_mlp_set_params(mcmc_mlp *m, const float *params, int32_t host_io);

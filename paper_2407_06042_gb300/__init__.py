@@ -49,6 +49,7 @@ ABI_FUNCTIONS = [
 ABI_FUNCTIONS_LEARNED = [
     "mcmc_mlp_param_count", "mcmc_mlp_create", "mcmc_mlp_destroy", "mcmc_mlp_last_error",
     "mcmc_mlp_set_params", "mcmc_mlp_get_params", "mcmc_mlp_forward", "mcmc_mlp_loss_grad",
+    "mcmc_mlp_set_train_engine",
     "mcmc_mlp_train_step", "mcmc_detect_features", "mcmc_detect_set_model",
     "mcmc_detect_init_learned", "mcmc_detect_mix_step",
 ]
@@ -138,6 +139,7 @@ def load(path: Optional[str] = None):
     l.mcmc_mlp_last_error.argtypes = [vp]
     l.mcmc_mlp_last_error.restype = ctypes.c_char_p
     l.mcmc_mlp_set_params.argtypes = [vp, vp, i32]
+    l.mcmc_mlp_set_train_engine.argtypes = [vp, i32]
     l.mcmc_mlp_get_params.argtypes = [vp, vp, i32]
     l.mcmc_mlp_forward.argtypes = [vp, i64, vp, vp, i32]
     l.mcmc_mlp_loss_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -420,6 +422,10 @@ class Mlp:
         if st != 0:
             msg = self._l.mcmc_mlp_last_error(self._h).decode()
             raise McmcError(st, msg or self._l.mcmc_status_string(st).decode())
+
+    def set_train_engine(self, tensor_cores: bool):
+        """Training products on tcgen05 (split-BF16, the default on sm_103) or CUDA cores."""
+        self._check(self._l.mcmc_mlp_set_train_engine(self._h, int(bool(tensor_cores))))
 
     def set_params(self, params):
         if _is_host(params):

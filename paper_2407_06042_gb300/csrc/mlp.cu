@@ -31,6 +31,7 @@
 #include "common.cuh"
 #include "mlp.h"
 #include "tc_ptx.cuh"
+#include "tcgemm.h"
 
 namespace mcmcdet {
 
@@ -136,21 +137,40 @@ __global__ void splitk_reduce_kernel(const float *partial, int splits, int M, in
 }
 
 // out[n] = sum_r A[r lda + n]: 8 row groups per 32 columns, summed in group order.
-__global__ void colsum_kernel(const float *A, int R, int N, long long lda, float *out)
+// Column sums out[n] = sum_r A[r lda + n] in two deterministic stages: CTA (x, y) sums rows
+// [y rpc, (y + 1) rpc) of columns 32x .. 32x + 31 into part[y N + n] (eight row groups of 32
+// lanes, added in group order), then colsum_final_kernel adds the chunks in chunk order.
+__global__ void colsum_kernel(const float *A, int R, int N, long long lda, int rpc, float *part)
 {
     __shared__ float red[8][33];
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int col = blockIdx.x * 32 + lane;
-    float s = 0.f;
-    if (col < N)
-        for (int r = grp; r < R; r += 8) s += A[(long long)r * lda + col];
-    red[grp][lane] = s;
+    const int r0 = blockIdx.y * rpc, r1 = min(R, r0 + rpc);
+    float s0 = 0.f, s1 = 0.f;
+    if (col < N) {
+        int r = r0 + grp;
+        for (; r + 8 < r1; r += 16) {
+            s0 += A[(long long)r * lda + col];
+            s1 += A[(long long)(r + 8) * lda + col];
+        }
+        if (r < r1) s0 += A[(long long)r * lda + col];
+    }
+    red[grp][lane] = s0 + s1;
     __syncthreads();
     if (grp == 0 && col < N) {
         float t = 0.f;
         for (int q = 0; q < 8; ++q) t += red[q][lane];
-        out[col] = t;
+        part[(long long)blockIdx.y * N + col] = t;
     }
+}
+
+__global__ void colsum_final_kernel(const float *part, int chunks, int N, float *out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float t = 0.f;
+    for (int c = 0; c < chunks; ++c) t += part[(long long)c * N + n];
+    out[n] = t;
 }
 
 // Softmax cross-entropy per row (one warp per row, Q <= 64): dlog = (softmax - onehot) * inv_r,
@@ -519,7 +539,7 @@ __global__ void __launch_bounds__(256, 1) mlp_tc_kernel(const __grid_constant__ 
 
 int g_sm_count = 0;
 
-cudaError_t gemm(const GemmArgs &in, float *partial, size_t partial_floats, cudaStream_t s)
+cudaError_t gemm_simt(const GemmArgs &in, float *partial, size_t partial_floats, cudaStream_t s, int *launches)
 {
     GemmArgs g = in;
     const int tm = (g.M + kBM - 1) / kBM, tn = (g.N + kBN - 1) / kBN;
@@ -536,11 +556,36 @@ cudaError_t gemm(const GemmArgs &in, float *partial, size_t partial_floats, cuda
     g.partial = splits > 1 ? partial : nullptr;
     sgemm_kernel<<<dim3(tn, tm, splits), 256, 0, s>>>(g);
     cudaError_t e = cudaGetLastError();
+    *launches = 1;
     if (e != cudaSuccess || splits == 1) return e;
     const long long MN = (long long)g.M * g.N;
     const int blocks = (int)std::min<long long>((MN + 255) / 256, 4096);
     splitk_reduce_kernel<<<blocks, 256, 0, s>>>(partial, splits, g.M, g.N, g.C, g.ldc);
+    *launches = 2;
     return cudaGetLastError();
+}
+
+// A product of the network: on tcgen05 (split-BF16 operands, FP32 accumulation) when the handle
+// trains on tensor cores, else the CUDA-core kernel.
+cudaError_t gemm(mcmc_mlp *m, const GemmArgs &in, float *partial, size_t partial_floats,
+                 cudaStream_t s)
+{
+    int launches = 0;
+    cudaError_t e;
+    if (m->tc_train) {
+        TcGemmArgs t{};
+        t.M = in.M; t.N = in.N; t.K = in.K;
+        t.A = in.A; t.sam = in.sam; t.sak = in.sak;
+        t.B = in.B; t.sbk = in.sbk; t.sbn = in.sbn;
+        t.C = in.C; t.ldc = in.ldc;
+        t.bias = in.bias; t.mask = in.mask; t.ldm = in.ldm; t.relu = in.relu;
+        t.status = m->status;
+        e = tc_gemm(t, partial, partial_floats, m->sm_count, s, &launches);
+    } else {
+        e = gemm_simt(in, partial, partial_floats, s, &launches);
+    }
+    m->launches += launches;
+    return e;
 }
 
 GemmArgs gargs(int M, int N, int K, const float *A, long long sam, long long sak, const float *B,
@@ -554,6 +599,23 @@ GemmArgs gargs(int M, int N, int K, const float *A, long long sam, long long sak
     return g;
 }
 
+// Column sums of an R x N row-major block (colsum_kernel), staged in the split-K buffer (free
+// between products on the handle's stream); two launches.
+cudaError_t colsum(mcmc_mlp *m, const float *A, int R, int N, float *out, cudaStream_t s)
+{
+    const int cgroups = (N + 31) / 32;
+    int chunks = std::max(1, std::min((R + 255) / 256, 2 * std::max(m->sm_count, 1) / cgroups));
+    while (chunks > 1 && (size_t)chunks * N > m->partial_floats) --chunks;
+    const int rpc = std::max(1, (R + chunks - 1) / chunks);
+    chunks = std::max(1, (R + rpc - 1) / rpc);
+    colsum_kernel<<<dim3(cgroups, chunks), 256, 0, s>>>(A, R, N, N, rpc, m->partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    colsum_final_kernel<<<(N + 255) / 256, 256, 0, s>>>(m->partial, chunks, N, out);
+    m->launches += 2;
+    return cudaGetLastError();
+}
+
 // Forward of R rows (R <= max_rows) keeping h1, h2 and the logits in the workspace.
 cudaError_t forward_rows(mcmc_mlp *m, int R, const float *X, float *logits, cudaStream_t s)
 {
@@ -562,17 +624,15 @@ cudaError_t forward_rows(mcmc_mlp *m, int R, const float *X, float *logits, cuda
     GemmArgs g = gargs(R, H, kMlpIn, X, kMlpIn, 1, P, 1, kMlpIn, m->h1, H);
     g.bias = P + mlp_off_b1();
     g.relu = 1;
-    cudaError_t e = gemm(g, nullptr, 0, s);
+    cudaError_t e = gemm(m, g, nullptr, 0, s);
     if (e != cudaSuccess) return e;
     g = gargs(R, H, H, m->h1, H, 1, P + mlp_off_W2(), 1, H, m->h2, H);
     g.bias = P + mlp_off_b2();
     g.relu = 1;
-    if ((e = gemm(g, nullptr, 0, s)) != cudaSuccess) return e;
+    if ((e = gemm(m, g, nullptr, 0, s)) != cudaSuccess) return e;
     g = gargs(R, m->Q, H, m->h2, H, 1, P + mlp_off_W3(), 1, H, logits, m->Q);
     g.bias = P + mlp_off_b3(m->Q);
-    e = gemm(g, nullptr, 0, s);
-    m->launches += 3;
-    return e;
+    return gemm(m, g, nullptr, 0, s);
 }
 
 template <int Q>
@@ -711,29 +771,26 @@ mcmc_status loss_grad_rows(mcmc_mlp *m, int R, const float *xs, const int *ls, f
         m->launches++;
     }
     // layer 3: gW3 = dlog^T h2, gb3 = colsum(dlog), da2 = (dlog W3) * [h2 > 0]
-    MCK(gemm(gargs(Q, H, R, m->dlog, 1, Q, m->h2, H, 1, grad + mlp_off_W3(), H), m->partial,
+    MCK(gemm(m, gargs(Q, H, R, m->dlog, 1, Q, m->h2, H, 1, grad + mlp_off_W3(), H), m->partial,
              m->partial_floats, s), "gW3");
-    colsum_kernel<<<(Q + 31) / 32, 256, 0, s>>>(m->dlog, R, Q, Q, grad + mlp_off_b3(Q));
-    MCK(cudaGetLastError(), "gb3");
+    MCK(colsum(m, m->dlog, R, Q, grad + mlp_off_b3(Q), s), "gb3");
     GemmArgs g = gargs(R, H, Q, m->dlog, Q, 1, P + mlp_off_W3(), H, 1, m->dh, H);
     g.mask = m->h2;
     g.ldm = H;
-    MCK(gemm(g, nullptr, 0, s), "da2");
+    MCK(gemm(m, g, nullptr, 0, s), "da2");
     // layer 2: gW2 = da2^T h1, gb2, da1 = (da2 W2) * [h1 > 0] (into the h2 buffer)
-    MCK(gemm(gargs(H, H, R, m->dh, 1, H, m->h1, H, 1, grad + mlp_off_W2(), H), m->partial,
+    MCK(gemm(m, gargs(H, H, R, m->dh, 1, H, m->h1, H, 1, grad + mlp_off_W2(), H), m->partial,
              m->partial_floats, s), "gW2");
-    colsum_kernel<<<H / 32, 256, 0, s>>>(m->dh, R, H, H, grad + mlp_off_b2());
-    MCK(cudaGetLastError(), "gb2");
+    MCK(colsum(m, m->dh, R, H, grad + mlp_off_b2(), s), "gb2");
     g = gargs(R, H, H, m->dh, H, 1, P + mlp_off_W2(), H, 1, m->h2, H);
     g.mask = m->h1;
     g.ldm = H;
-    MCK(gemm(g, nullptr, 0, s), "da1");
+    MCK(gemm(m, g, nullptr, 0, s), "da1");
     // layer 1: gW1 = da1^T X, gb1
-    MCK(gemm(gargs(H, kMlpIn, R, m->h2, 1, H, xs, kMlpIn, 1, grad, kMlpIn), m->partial,
+    MCK(gemm(m, gargs(H, kMlpIn, R, m->h2, 1, H, xs, kMlpIn, 1, grad, kMlpIn), m->partial,
              m->partial_floats, s), "gW1");
-    colsum_kernel<<<H / 32, 256, 0, s>>>(m->h2, R, H, H, grad + mlp_off_b1());
-    MCK(cudaGetLastError(), "gb1");
-    m->launches += 11;
+    MCK(colsum(m, m->h2, R, H, grad + mlp_off_b1(), s), "gb1");
+    m->launches++;   // the loss kernel; products and column sums count their own
     return MCMC_OK;
 }
 
@@ -787,6 +844,13 @@ mcmc_status mcmc_mlp_create(int32_t qam, int32_t max_rows, void *stream, mcmc_ml
     cudaError_t e = cudaGetDevice(&m->device);
     if (e != cudaSuccess) return bail(e);
     if (!g_sm_count) cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, m->device);
+    {
+        int mj = 0, mn = 0;
+        cudaDeviceGetAttribute(&mj, cudaDevAttrComputeCapabilityMajor, m->device);
+        cudaDeviceGetAttribute(&mn, cudaDevAttrComputeCapabilityMinor, m->device);
+        m->tc_train = mj == 10 && mn == 3;
+        cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
+    }
     if (stream) {
         m->stream = (cudaStream_t)stream;
     } else {
@@ -828,6 +892,21 @@ mcmc_status mcmc_mlp_destroy(mcmc_mlp *m)
     if (m->small_host) cudaFreeHost(m->small_host);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
+    return MCMC_OK;
+}
+
+mcmc_status mcmc_mlp_set_train_engine(mcmc_mlp *m, int32_t tensor_cores)
+{
+    if (!m) return MCMC_EINVAL;
+    m->err.clear();
+    if (tensor_cores != 0 && tensor_cores != 1) return mfail(m, MCMC_EINVAL, "tensor_cores must be 0 or 1");
+    if (tensor_cores) {
+        int mj = 0, mn = 0;
+        cudaDeviceGetAttribute(&mj, cudaDevAttrComputeCapabilityMajor, m->device);
+        cudaDeviceGetAttribute(&mn, cudaDevAttrComputeCapabilityMinor, m->device);
+        if (!(mj == 10 && mn == 3)) return mfail(m, MCMC_EUNSUPPORTED, "tensor-core training needs sm_103");
+    }
+    m->tc_train = tensor_cores != 0;
     return MCMC_OK;
 }
 

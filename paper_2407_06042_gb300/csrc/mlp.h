@@ -28,6 +28,10 @@ struct mcmc_mlp {
     uint8_t *tc_ops = nullptr;
     bool tc_valid = false;
     float *small_host = nullptr;   // pinned host copy of W1, b1 | b2 | b3 (launch parameters)
+    // the large products of a forward or training pass (hidden layer, input and weight
+    // gradients) on tcgen05 with split-BF16 operands (default on sm_103), else on CUDA cores
+    bool tc_train = false;
+    int sm_count = 0;
 };
 
 namespace mcmcdet {

@@ -28,23 +28,35 @@ def _features(rows, seed=0):
     return X.astype(np.float32).astype(np.float64)
 
 
-def _mlp(qam, params, max_rows=4096):
+def _mlp(qam, params, max_rows=4096, train_tc=None):
     from paper_2407_06042_gb300 import Mlp
     m = Mlp(qam, max_rows=max_rows)
     m.set_params(params.astype(np.float32))
+    if train_tc is not None:
+        m.set_train_engine(train_tc)
     return m
 
 
+# Products of the forward and training passes on tcgen05 with each FP32 operand split into three
+# BF16 terms (to 2^-26 of itself) and the six leading term products accumulated in FP32: each
+# product is as accurate as an FP32 one, but the tensor core adds several products per step
+# into its FP32 accumulator with a rounding of its own rather than one FMA at a time, and it
+# accumulates 18 term products per 16 values of k; the tensor-core path gets twice the room
+# (the QPSK weight gradient over 1000 rows, the tightest case, measured 1.2e-4 of max |g|).
+TC_SLACK = {False: 1.0, True: 2.0}
+
+
+@pytest.mark.parametrize("train_tc", [False, True])
 @pytest.mark.parametrize("qam", [4, 16, 64])
-def test_forward_fp32_matches_oracle(qam):
+def test_forward_fp32_matches_oracle(qam, train_tc):
     import torch
     p = _params(qam)
     X = _features(1000 + qam)
-    m = _mlp(qam, p, max_rows=384)        # several chunks and a ragged one
+    m = _mlp(qam, p, max_rows=384, train_tc=train_tc)   # several chunks and a ragged one
     out = m.forward(torch.tensor(X, dtype=torch.float32, device="cuda")).cpu().numpy()
     ref = omlp.forward(p, X, qam)[0]
     scale = np.abs(ref).max()
-    np.testing.assert_allclose(out, ref, atol=2e-5 * scale, rtol=0)
+    np.testing.assert_allclose(out, ref, atol=2e-5 * TC_SLACK[train_tc] * scale, rtol=0)
     m.destroy()
 
 
@@ -72,32 +84,46 @@ def test_forward_tensor_cores_match_quantised_oracle(qam):
     m.destroy()
 
 
-@pytest.mark.parametrize("qam,rows", [(16, 300), (4, 1000), (64, 257)])
-def test_loss_and_gradient_match_oracle(qam, rows):
+def _decided_rows(p, X, qam, idx, margin=1e-5):
+    """The rows of idx whose ReLU decisions FP32 arithmetic takes as FP64 does: every hidden
+    pre-activation at least `margin` of its layer's largest from zero. A pre-activation closer to
+    zero than an FP32 sum's rounding (about 1e-7 of the terms for K = 256) may land on either
+    side in any FP32 evaluation order; the mask it sets then moves a weight gradient by a whole
+    row's term (up to 2e-3 of max |g| in the QPSK case), which says nothing about the kernel."""
+    _, (_, a1, _, a2, _) = omlp.forward(p, X[idx], qam)
+    ok = ((np.abs(a1) >= margin * np.abs(a1).max()).all(axis=1)
+          & (np.abs(a2) >= margin * np.abs(a2).max()).all(axis=1))
+    return idx[ok]
+
+
+@pytest.mark.parametrize("train_tc", [False, True])
+@pytest.mark.parametrize("qam,rows", [(16, 300), (4, 1000), (64, 257), (16, 4096)])
+def test_loss_and_gradient_match_oracle(qam, rows, train_tc):
     import torch
     p = _params(qam, seed=7)
     X = _features(rows + 50, seed=2)
     rng = np.random.default_rng(3)
     labels = rng.integers(0, qam, rows + 50).astype(np.int32)
-    idx = rng.permutation(rows + 50)[:rows].astype(np.int32)
-    m = _mlp(qam, p)
+    idx = _decided_rows(p, X, qam, rng.permutation(rows + 50)[:rows]).astype(np.int32)
+    m = _mlp(qam, p, train_tc=train_tc)
     dX = torch.tensor(X, dtype=torch.float32, device="cuda")
     dl = torch.tensor(labels, device="cuda")
     di = torch.tensor(idx, device="cuda")
     loss, grad = m.loss_grad(dX, dl, di)
     ref_loss, ref_grad = omlp.loss_and_grad(p, X[idx], labels[idx], qam)
-    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * abs(ref_loss)
+    k = TC_SLACK[train_tc]
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * k * abs(ref_loss)
     g = grad.cpu().numpy()
     o = 0
     for name, shp in omlp.shapes(qam):
         n = int(np.prod(shp))
         gs, rs = g[o:o + n], ref_grad[o:o + n]
-        assert np.abs(gs - rs).max() <= 1e-4 * np.abs(rs).max() + 1e-7, name
+        assert np.abs(gs - rs).max() <= 1e-4 * k * np.abs(rs).max() + 1e-7, (name, np.abs(gs - rs).max() / np.abs(rs).max())
         o += n
     # without an index list: rows 0 .. rows-1
     loss2, grad2 = m.loss_grad(dX, dl, None, rows=rows)
     ref_loss2, _ = omlp.loss_and_grad(p, X[:rows], labels[:rows], qam)
-    assert abs(float(loss2.item()) - ref_loss2) <= 1e-5 * abs(ref_loss2)
+    assert abs(float(loss2.item()) - ref_loss2) <= 1e-5 * k * abs(ref_loss2)
     # determinism: a second evaluation is bit-identical
     _, grad3 = m.loss_grad(dX, dl, di)
     assert torch.equal(grad, grad3)
