@@ -134,6 +134,18 @@ def pipe_peaks():
     return _PEAKS
 
 
+def bf16_tensor_peak():
+    """Dense BF16 tensor peak (TFLOP/s) of this machine's GPUs and where it comes from: the burst
+    cuBLAS figure of MEASURED_PEAKS.json (the kernels it is set against are timed alone), else
+    the recipe's earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["bf16_tflops"])
+        return v, "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone), of measured"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16 burst (earlier GB300 measurement), of fallback"
+
+
 def _kernel_hash(files):
     import hashlib
     h = hashlib.sha256()
@@ -235,7 +247,8 @@ def chain_roofline(precision, w, units, chain_ms, batch=None):
            "peaks_measured": peaks}
     if precision == "mixed":
         tf = gemm * units / t / 1e12
-        out["tensor"] = {"achieved_tflops": tf, "peak_tflops": 1899.4, "frac": tf / 1899.4,
+        tp, tsrc = bf16_tensor_peak()
+        out["tensor"] = {"achieved_tflops": tf, "peak_tflops": tp, "frac": tf / tp, "peak_source": tsrc,
                          "per_unit": f"{gemm:g} Gram flops per chain-iteration (D' = X'[Gt|PGt])"}
     else:
         fma = peaks.get("fma")
@@ -579,6 +592,7 @@ def run_learned(args, w, batch, rank, world, dist, dev, pkg, torch):
     H_ = 256
     fpr = 2 * (6 * H_ + H_ * H_ + H_ * w["qam"])
     mlp_tf = rows * fpr / (mlp_ms * 1e-3) / 1e12
+    tpeak, tsrc = bf16_tensor_peak()
     del Xr, logits
 
     value = B * Np * T_ref * world / (ms_l * 1e-3)
@@ -609,10 +623,10 @@ def run_learned(args, w, batch, rank, world, dist, dev, pkg, torch):
                     "speedup_vs_plain_fp32_at_equal_ber": ms_32 / ms_l,
                     "mlp_tensor_roofline": {
                         "bound": "tensor", "rows": rows, "ms": mlp_ms,
-                        "achieved": mlp_tf, "peak": 1899.4, "unit": "TFLOP/s",
-                        "frac": mlp_tf / 1899.4,
+                        "achieved": mlp_tf, "peak": tpeak, "unit": "TFLOP/s",
+                        "frac": mlp_tf / tpeak,
                         "per_unit": f"{fpr} flops per row (6x256 + 256x256 + 256x{w['qam']} MACs)",
-                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)"}},
+                        "peak_source": tsrc}},
                 "e2e": None, "cpu_baseline": cb}
         print(json.dumps(line), flush=True)
     for d in (d32, dl):
@@ -731,6 +745,63 @@ def run_convergence(args, w, batch, rank, world, dist, dev, pkg, torch):
     return 0
 
 
+def run_mlp_train(args, rank, world, dist, dev, pkg, torch):
+    """One Adam step of the learned proposal's network (forward, softmax cross-entropy, backward,
+    Adam) on ROWS synthetic feature rows of the detector's scale, timed per training engine. Its
+    products: forward 2 R (6 H + H H + H Q) flops, backward 2 R (2 H Q + 2 H H + 6 H) flops
+    (H = 256 hidden units, Q = the workload's alphabet size)."""
+    w = workload.WORKLOADS["learned_64x64_16qam"]
+    Q, R, Hh = w["qam"], args.mlp_train, 256
+    rng = np.random.default_rng(rank_seed(11, rank))
+    X = np.zeros((R, 6), np.float32)
+    X[:, :4] = rng.normal(0.0, 4.0, (R, 4))
+    X[:, 4] = rng.normal(-2.0, 0.5, R)
+    X[:, 5] = rng.uniform(-7.0, -2.0, R)
+    Xd = torch.from_numpy(X).to(dev)
+    lab = torch.from_numpy(rng.integers(0, Q, R).astype(np.int32)).to(dev)
+    flops = 2.0 * R * (12 * Hh + 3 * Hh * Hh + 3 * Hh * Q)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, tc in (("tcgen05", True), ("cuda_cores", False)):
+        m = pkg.Mlp(Q, max_rows=R, stream=stream)
+        m.set_params((0.05 * rng.standard_normal(m.param_count)).astype(np.float32))
+        m.set_train_engine(tc)
+        loss = torch.zeros(1, device=dev)
+        for _ in range(args.warmup):
+            m.train_step(Xd, lab, None, 1e-3, loss, rows=R)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                m.train_step(Xd, lab, None, 1e-3, loss, rows=R)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+        res[name] = {"ms_per_step": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                     "loss": float(loss.item()), "clocks": clk.summary()}
+        m.destroy()
+    tp, tsrc = bf16_tensor_peak()
+    if rank == 0:
+        tc = res["tcgen05"]
+        print(json.dumps({
+            "metric": "network training rows per second (one Adam step)",
+            "value": R * world / (tc["ms_per_step"] * 1e-3), "unit": "rows/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tc["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3 x bf16 split)",
+            "data": "synthetic", "config": {"workload": f"mlp_train_{R}rows_{Q}qam", "rows": R,
+                                            "hidden": Hh, "outputs": Q},
+            "flops_per_step": flops, "engines": res,
+            "tensor_roofline": {"bound": "tensor", "achieved": tc["tflops"],
+                                "peak": tp / 6.0, "unit": "TFLOP/s", "frac": tc["tflops"] / (tp / 6.0),
+                                "peak_source": tsrc + "; divided by the 6 BF16 term products each "
+                                                      "FP32 product takes"}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -760,6 +831,9 @@ def main():
     ap.add_argument("--refresh", type=int, default=None, help="FP64 energy refresh period")
     ap.add_argument("--tile", type=int, default=0,
                     help="chains per work item with an explicit --engine (0: the engine's default)")
+    ap.add_argument("--mlp-train", type=int, default=0, metavar="ROWS",
+                    help="time one Adam step of the learned proposal's network on ROWS rows with "
+                         "each training engine (tcgen05 and CUDA cores) instead of a detection run")
     args = ap.parse_args()
     rank, world, local = _env_rank()
     if args.impl == "reference":
@@ -776,6 +850,8 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    if args.mlp_train:
+        return run_mlp_train(args, rank, world, dist, dev, pkg, torch)
     batch, w = load_batch(args.scale, rank, args.workload)
     if w["kind"] == "learned":
         return run_learned(args, w, batch, rank, world, dist, dev, pkg, torch)

@@ -407,7 +407,9 @@ class Mlp:
         self._l = load()
         self.qam = int(qam)
         h = ctypes.c_void_p()
-        st = self._l.mcmc_mlp_create(self.qam, int(max_rows), stream, ctypes.byref(h))
+        sp = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else stream
+        st = self._l.mcmc_mlp_create(self.qam, int(max_rows), ctypes.c_void_p(sp) if sp else None,
+                                     ctypes.byref(h))
         if st != 0:
             raise McmcError(st, self._l.mcmc_status_string(st).decode())
         self._h = h

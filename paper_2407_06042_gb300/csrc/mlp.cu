@@ -136,10 +136,9 @@ __global__ void splitk_reduce_kernel(const float *partial, int splits, int M, in
     }
 }
 
-// out[n] = sum_r A[r lda + n]: 8 row groups per 32 columns, summed in group order.
 // Column sums out[n] = sum_r A[r lda + n] in two deterministic stages: CTA (x, y) sums rows
 // [y rpc, (y + 1) rpc) of columns 32x .. 32x + 31 into part[y N + n] (eight row groups of 32
-// lanes, added in group order), then colsum_final_kernel adds the chunks in chunk order.
+// lanes, added in group order), then colsum_final_kernel adds the chunks in a fixed order.
 __global__ void colsum_kernel(const float *A, int R, int N, long long lda, int rpc, float *part)
 {
     __shared__ float red[8][33];
@@ -164,13 +163,24 @@ __global__ void colsum_kernel(const float *A, int R, int N, long long lda, int r
     }
 }
 
-__global__ void colsum_final_kernel(const float *part, int chunks, int N, float *out)
+// Chunk partials added in a fixed order: warp w of CTA x sums chunks w, w + 8, ... of columns
+// 32x .. 32x + 31, then warp 0 adds the eight sums in warp order.
+__global__ void __launch_bounds__(256) colsum_final_kernel(const float *part, int chunks, int N, float *out)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    __shared__ float red[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int n = blockIdx.x * 32 + lane;
     float t = 0.f;
-    for (int c = 0; c < chunks; ++c) t += part[(long long)c * N + n];
-    out[n] = t;
+    if (n < N)
+        for (int c = w; c < chunks; c += 8) t += part[(long long)c * N + n];
+    red[w][lane] = t;
+    __syncthreads();
+    if (w == 0 && n < N) {
+        float s = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += red[q][lane];
+        out[n] = s;
+    }
 }
 
 // Softmax cross-entropy per row (one warp per row, Q <= 64): dlog = (softmax - onehot) * inv_r,
@@ -611,7 +621,7 @@ cudaError_t colsum(mcmc_mlp *m, const float *A, int R, int N, float *out, cudaSt
     colsum_kernel<<<dim3(cgroups, chunks), 256, 0, s>>>(A, R, N, N, rpc, m->partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    colsum_final_kernel<<<(N + 255) / 256, 256, 0, s>>>(m->partial, chunks, N, out);
+    colsum_final_kernel<<<(N + 31) / 32, 256, 0, s>>>(m->partial, chunks, N, out);
     m->launches += 2;
     return cudaGetLastError();
 }
