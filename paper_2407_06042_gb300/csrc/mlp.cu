@@ -267,20 +267,34 @@ __global__ void adam_kernel(float *p, float *m, float *v, const float *g, long l
 // ------------------------------------------------------------------------------------------
 // Tensor-core inference
 // ------------------------------------------------------------------------------------------
-constexpr uint32_t kW2Bytes = kMlpHidden * kMlpHidden * 2;   // 131072
-constexpr uint32_t kHBytes = 128 * kMlpHidden * 2;           // 65536
-constexpr uint32_t kCoreSbo = (kMlpHidden / 8) * 128;        // 8-row group stride, K = 256
+// All three layers run on the tensor cores.
+// Layer 1 (K = 6 features) is evaluated to FP32 accuracy from BF16 terms: every feature x and
+// weight w is split into three terms, x = x0 + x1 + x2 (each the round-to-nearest BF16 of what
+// the previous leave; the remainder is below 2^-26 |x|), and the six products x_i w_j with
+// i + j <= 2 are laid side by side along K (the dropped ones are below 2^-26 |x w|), followed by
+// the bias's three terms against constant 1.0 columns: K = 6 x 6 + 3, padded to 48.
+// Layers 2 and 3 contract over the 256 BF16 hidden values plus their bias, again three BF16
+// terms against 1.0 columns: K = 256 + 3, padded to 272. Every MMA adds its bias itself.
+constexpr int kMlpK = kMlpHidden + 16;                         // 272
+constexpr int kMlpK1 = 48;
+constexpr uint32_t kCoreSbo = (kMlpK / 8) * 128;              // 8-row group stride, K = 272
+constexpr uint32_t kCoreSbo1 = (kMlpK1 / 8) * 128;            // 8-row group stride, K = 48
+constexpr uint32_t kW2Bytes = kMlpHidden * kMlpK * 2;         // 139264
+constexpr uint32_t kW1Bytes = kMlpHidden * kMlpK1 * 2;        // 24576
+constexpr uint32_t kA0Bytes = 128 * kMlpK1 * 2;               // 12288, one tile's layer-1 A operand
 constexpr int kMlpTmemCols = 512;
+
+__host__ __device__ inline uint32_t mlp_w3_bytes(int Qp) { return (uint32_t)Qp * kMlpK * 2u; }
 
 __host__ __device__ inline uint32_t mlp_smem_bytes(int Qp)
 {
-    return kW2Bytes + (uint32_t)Qp * 512u + kHBytes + 64u;
+    return kW2Bytes + mlp_w3_bytes(Qp) + kW1Bytes + 2 * kA0Bytes + 256u;   // + mbarriers, TMEM slot
 }
 
-// Byte offset of element (row, k) in a K-major, no-swizzle core-matrix image with K = 256.
-__device__ __forceinline__ uint32_t core_off(int row, int k)
+// Byte offset of element (row, k) in a K-major, no-swizzle core-matrix image of stride sbo.
+__device__ __forceinline__ uint32_t core_off(int row, int k, uint32_t sbo = kCoreSbo)
 {
-    return (uint32_t)(row >> 3) * kCoreSbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u +
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u +
            (uint32_t)(k & 7) * 2u;
 }
 
@@ -290,26 +304,76 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// W2 and W3 (rows padded to Qp with zeros) as BF16 core-matrix images; one thread per 8 K values.
+// Three-term BF16 split of an FP32 value (as floats).
+__device__ __forceinline__ void split3(float v, float (&t)[3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        t[i] = __bfloat162float(__float2bfloat16_rn(v));
+        v -= t[i];
+    }
+}
+
+// Term of a layer-1 weight (B side) and of a feature (A side) at position t = 0..5 of a
+// feature's six K slots: the products x0 w0, x0 w1, x1 w0, x0 w2, x1 w1, x2 w0.
+__host__ __device__ constexpr int l1_wterm(int t) { return t == 1 || t == 4 ? 1 : (t == 3 ? 2 : 0); }
+__host__ __device__ constexpr int l1_xterm(int t) { return t == 2 || t == 4 ? 1 : (t == 5 ? 2 : 0); }
+
+// Operand images in global memory, one thread per 8 K values of a row:
+//   W2 | b2 (256 x 272), W3 | b3 (rows padded to Qp with zeros), W1 terms | b1 (256 x 48).
 __global__ void mlp_pack_kernel(const float *params, int Q, int Qp, uint8_t *ops)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (kMlpHidden + Qp) * 32) return;
-    const int n = e >> 5, c = e & 31;
-    const float *src = nullptr;
-    uint8_t *dst;
-    if (n < kMlpHidden) {
-        src = params + mlp_off_W2() + (long long)n * kMlpHidden + 8 * c;
-        dst = ops + core_off(n, 8 * c);
-    } else {
-        const int nn = n - kMlpHidden;
-        if (nn < Q) src = params + mlp_off_W3() + (long long)nn * kMlpHidden + 8 * c;
-        dst = ops + kW2Bytes + core_off(nn, 8 * c);
-    }
-    uint32_t w[4];
+    const int n23 = (kMlpHidden + Qp) * (kMlpK / 8);
+    if (e >= n23 + kMlpHidden * (kMlpK1 / 8)) return;
+    float v[8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = src ? pack_bf16(src[2 * j], src[2 * j + 1]) : 0u;
-    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    for (int j = 0; j < 8; ++j) v[j] = 0.f;
+    uint8_t *dst;
+    if (e < n23) {
+        const int n = e / (kMlpK / 8), c = e % (kMlpK / 8);
+        const float *w = nullptr;   // the row's weights
+        float bias = 0.f;
+        if (n < kMlpHidden) {
+            w = params + mlp_off_W2() + (long long)n * kMlpHidden;
+            bias = params[mlp_off_b2() + n];
+            dst = ops + core_off(n, 8 * c);
+        } else {
+            const int nn = n - kMlpHidden;
+            if (nn < Q) {
+                w = params + mlp_off_W3() + (long long)nn * kMlpHidden;
+                bias = params[mlp_off_b3(Q) + nn];
+            }
+            dst = ops + kW2Bytes + core_off(nn, 8 * c);
+        }
+        if (w && 8 * c < kMlpHidden) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = w[8 * c + j];
+        } else if (w && 8 * c == kMlpHidden) {
+            float t[3];   // k = 256, 257, 258: the bias's three terms (k = 259 .. 271 stay zero)
+            split3(bias, t);
+            v[0] = t[0]; v[1] = t[1]; v[2] = t[2];
+        }
+    } else {
+        const int f = e - n23, u = f / (kMlpK1 / 8), c = f % (kMlpK1 / 8);
+        dst = ops + kW2Bytes + mlp_w3_bytes(Qp) + core_off(u, 8 * c, kCoreSbo1);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * c + j;
+            float t[3];
+            if (k < 6 * kMlpIn) {
+                split3(params[(long long)u * kMlpIn + k / 6], t);
+                v[j] = t[l1_wterm(k % 6)];
+            } else if (k < 6 * kMlpIn + 3) {
+                split3(params[mlp_off_b1() + u], t);
+                v[j] = t[k - 6 * kMlpIn];
+            }
+        }
+    }
+    uint32_t pk[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) pk[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
@@ -329,130 +393,190 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Small weights travel in the kernel's parameter block (constant bank): the CUDA-core layers read
-// them as direct FMA operands. W2 and W3 are the BF16 operand images in global memory.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&p)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(p[0]), "r"(p[1]), "r"(p[2]), "r"(p[3]), "r"(p[4]), "r"(p[5]), "r"(p[6]),
+        "r"(p[7]), "r"(p[8]), "r"(p[9]), "r"(p[10]), "r"(p[11]), "r"(p[12]), "r"(p[13]), "r"(p[14]),
+        "r"(p[15])
+        : "memory");
+}
+
+// The bias columns of an A operand in tensor memory (k = 256 .. 271: 1, 1, 1, then zeros).
+__device__ __forceinline__ void tmem_st_bias_cols(uint32_t taddr)
+{
+    const uint32_t one2 = 0x3F803F80u, one = 0x00003F80u;   // BF16 1.0 = 0x3F80
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%3,%3,%3,%3,%3};" ::"r"(taddr), "r"(one2),
+        "r"(one), "r"(0u)
+        : "memory");
+}
+
 template <int Q>
 struct MlpTcArgs {
     long long rows;
     const float *X;
-    const uint8_t *ops;
+    const uint8_t *ops;     // W2 | b2, W3 | b3 and W1 | b1 images
     float *logits;
     unsigned *status;
-    float W1[kMlpHidden * kMlpIn];
-    float b1[kMlpHidden];
-    float b2[kMlpHidden];
-    float b3[Q];
+    int vec_out;            // logits 16-byte aligned
 };
 
-// Issue K = 256 worth of MMAs (16 x K16) from the A image at sa and the B image at sb into
-// tensor memory column tcol, then commit to the barrier (one thread).
-__device__ __forceinline__ void mlp_issue(uint32_t tmem_d, uint32_t sa, uint32_t sb, uint32_t idesc,
-                                          uint32_t bar)
+// Roles of the inference kernel's warps: four feature warps (layer 1's A operand), four layer-1
+// epilogue warps, four layer-2/3 epilogue warps (an epilogue warp w serves TMEM lane quadrant
+// w % 4, one row per thread) and one MMA warp.
+constexpr int kXWarps = 4, kE0Warps = 4, kE1Warps = 4;
+constexpr int kMmaWarpId = kXWarps + kE0Warps + kE1Warps;
+constexpr int kMlpThreads = 32 * (kMmaWarpId + 1);
+// Tensor-memory columns. Region 0: layer-1 accumulators, over whose first 136 columns the
+// epilogue writes h1 with its bias columns (layer 2's A operand) once it has read them. Region
+// 1: layer-2 accumulators, then h2 with its bias columns in the same way (layer 3's A operand),
+// and the logits' accumulators in its last 64 columns (written once h2 is there).
+constexpr uint32_t kColR0 = 0, kColR1 = 256, kColD2 = 448;
+// mbarriers: weights loaded, and the full / empty hand-overs of the pipeline
+enum : int { kBarW, kBarA0Full0, kBarA0Full1, kBarA0Empty0, kBarA0Empty1, kBarD0Full, kBarA1Full,
+             kBarA1Empty, kBarD1Full, kBarA2Full, kBarD2Full, kBarR1Free, kBarDone, kMlpBars };
+
+// max(lo, 0) and max(hi, 0) rounded to BF16, lo in the low half.
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi)
 {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-    for (int ks = 0; ks < kMlpHidden / 16; ++ks)
-        mma_bf16(tmem_d, smem_desc(sa + ks * 256u, 128u, kCoreSbo),
-                 smem_desc(sb + ks * 256u, 128u, kCoreSbo), idesc, ks ? 1u : 0u);
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// BF16 MMA whose A operand (M = 128 rows in the 128 lanes, K along the columns, two values per
+// column) is in tensor memory.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc,
+                                            uint32_t accumulate)
+{
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate));
 }
 
-// The CUDA-core parts of one 128-row tile for one half of the hidden units / logits (HALF_ID a
-// compile-time constant, so every weight is a direct constant-bank operand).
-template <int Q, int HALF_ID>
-__device__ __forceinline__ void mlp_layer1(const MlpTcArgs<Q> &a, const float (&x)[kMlpIn],
-                                           unsigned char *hrow)
+__device__ __forceinline__ void mlp_commit(uint32_t bar)
 {
-    constexpr int HALF = kMlpHidden / 2;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mlp_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Layer 1's A operand for one row: the six feature terms of each input, then 1.0 three times
+// (the bias terms), zeros to K = 48.
+__device__ __forceinline__ void mlp_features(const float (&x)[kMlpIn], unsigned char *img, int row)
+{
+    float v[kMlpK1];
 #pragma unroll
-    for (int c = 0; c < HALF / 8; ++c) {
-        uint32_t pk[4];
+    for (int k = 0; k < kMlpK1; ++k) v[k] = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float v[2];
+    for (int q = 0; q < kMlpIn; ++q) {
+        float t[3];
+        split3(x[q], t);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int u = HALF * HALF_ID + 8 * c + 2 * j + h;
-                float s = a.b1[u];
-#pragma unroll
-                for (int q = 0; q < kMlpIn; ++q) s = fmaf(a.W1[u * kMlpIn + q], x[q], s);
-                v[h] = fmaxf(s, 0.f);
-            }
-            pk[j] = pack_bf16(v[0], v[1]);
-        }
-        *reinterpret_cast<uint4 *>(hrow + c * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        for (int i = 0; i < 6; ++i) v[6 * q + i] = t[l1_xterm(i)];
     }
+    v[6 * kMlpIn] = v[6 * kMlpIn + 1] = v[6 * kMlpIn + 2] = 1.f;
+#pragma unroll
+    for (int g = 0; g < kMlpK1 / 8; ++g)
+        *reinterpret_cast<uint4 *>(img + core_off(row, 8 * g, kCoreSbo1)) =
+            make_uint4(pack_bf16(v[8 * g], v[8 * g + 1]), pack_bf16(v[8 * g + 2], v[8 * g + 3]),
+                       pack_bf16(v[8 * g + 4], v[8 * g + 5]), pack_bf16(v[8 * g + 6], v[8 * g + 7]));
 }
 
-template <int Q, int HALF_ID>
-__device__ __forceinline__ void mlp_epilogue2(const MlpTcArgs<Q> &a, uint32_t lane_base,
-                                              unsigned char *hrow)
+// ReLU and BF16 of one row's 256 accumulators (the bias is in them) at column col, written in
+// place as the next layer's A operand over the columns already read, then its bias columns.
+__device__ __forceinline__ void mlp_relu_inplace(uint32_t col)
 {
-    constexpr int HALF = kMlpHidden / 2;
-#pragma unroll
-    for (int c4 = 0; c4 < HALF / 32; ++c4) {
+#pragma unroll 1
+    for (int c = 0; c < kMlpHidden / 32; ++c) {
         float v[32];
-        tmem_ld32(lane_base + (uint32_t)(HALF * HALF_ID + 32 * c4), v);
+        tmem_ld32(col + (uint32_t)(32 * c), v);
+        uint32_t pk[16];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            uint32_t pk[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int u = HALF * HALF_ID + 32 * c4 + 8 * c + 2 * j;
-                pk[j] = pack_bf16(fmaxf(v[8 * c + 2 * j] + a.b2[u], 0.f),
-                                  fmaxf(v[8 * c + 2 * j + 1] + a.b2[u + 1], 0.f));
-            }
-            *reinterpret_cast<uint4 *>(hrow + (4 * c4 + c) * 128) =
-                make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
+        for (int j = 0; j < 16; ++j) pk[j] = pack_relu_bf16(v[2 * j], v[2 * j + 1]);
+        tmem_st16(col + (uint32_t)(16 * c), pk);
     }
+    tmem_st_bias_cols(col + kMlpHidden / 2);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-template <int Q, int HALF_ID>
-__device__ __forceinline__ void mlp_epilogue3(const MlpTcArgs<Q> &a, uint32_t lane_base,
-                                              long long r)
-{
-    constexpr int Qp = (Q + 15) / 16 * 16;
-    constexpr int base = (Qp / 2) * HALF_ID;
-#pragma unroll
-    for (int c = 0; c < Qp / 16; ++c) {
-        float v[8];
-        tmem_ld8(lane_base + (uint32_t)(kMlpHidden + base + 8 * c), v);
-        if (r < a.rows) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int n = base + 8 * c + j;
-                if (n < Q) a.logits[r * Q + n] = v[j] + a.b3[n < Q ? n : 0];
-            }
-        }
-    }
-}
-
-// 256 threads: warps w and w + 4 own the rows of TMEM lane quadrant w % 4 and split each row's
-// hidden units (and logits) in halves.
+// Layer-3 epilogue of one row: the logits (bias included) -> global memory, 16-byte stores when
+// the output is aligned.
 template <int Q>
-__global__ void __launch_bounds__(256, 1) mlp_tc_kernel(const __grid_constant__ MlpTcArgs<Q> a)
+__device__ __forceinline__ void mlp_logits(const MlpTcArgs<Q> &a, uint32_t lane_base, long long r)
 {
     constexpr int Qp = (Q + 15) / 16 * 16;
-    constexpr int HALF = kMlpHidden / 2;
+    float v[Qp];
+#pragma unroll
+    for (int c = 0; c < Qp / 8; ++c) {
+        float t[8];
+        tmem_ld8(lane_base + kColD2 + (uint32_t)(8 * c), t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[8 * c + j] = t[j];
+    }
+    if (r >= a.rows) return;
+    float *out = a.logits + r * Q;
+    if (a.vec_out) {
+#pragma unroll
+        for (int n = 0; n < Q; n += 4)
+            *reinterpret_cast<float4 *>(out + n) = make_float4(v[n], v[n + 1], v[n + 2], v[n + 3]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < Q; ++n) out[n] = v[n];
+    }
+}
+
+// Persistent, one CTA per SM, 128-row tiles through a pipeline:
+//   feature warps:  X -> layer 1's A operand (three BF16 terms per feature) in shared memory,
+//                   two buffers;
+//   MMA warp:       D0 = A0 [W1 | b1]^T (3 MMAs, N = 256), D1 = [h1 | 1] [W2 | b2]^T (17 MMAs,
+//                   N = 256, A in tensor memory), D2 = [h2 | 1] [W3 | b3]^T (17 MMAs, N = Qp,
+//                   A in tensor memory), issued in the order D1(t), D0(t + 1), D2(t);
+//   layer-1 epilogue warps: D0 -> h1 = BF16(ReLU(D0)) in place;
+//   layer-2/3 epilogue warps: D1 -> h2 = BF16(ReLU(D1)) in place, D2 -> logits.
+// So layer 1 of the next tile and its epilogue run beside this tile's layer-2 epilogue and
+// layer 3. Every hand-over is an mbarrier (MMA completion through tcgen05.commit). Every wait is
+// bounded and the warp-collective roles take each wait's verdict for the whole warp: a role that
+// gives up sets the timeout status and leaves its loop, the others run out of their own waits,
+// and the CTA waits (bounded) for its last MMAs before it frees the tensor memory.
+template <int Q>
+__global__ void __launch_bounds__(kMlpThreads, 1) mlp_tc_kernel(const __grid_constant__ MlpTcArgs<Q> a)
+{
+    constexpr int Qp = (Q + 15) / 16 * 16;
+    constexpr int kSteps = kMlpK / 16;   // 17
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, half = warp >> 2;
-    const int row_l = 32 * quad + lane;            // row of the tile (TMEM lane)
     unsigned char *sW2 = smem;
-    unsigned char *sW3 = smem + kW2Bytes;
-    unsigned char *sH = sW3 + (uint32_t)Qp * 512u;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sH + kHBytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
-    const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+    unsigned char *sW3 = sW2 + kW2Bytes;
+    unsigned char *sW1 = sW3 + mlp_w3_bytes(Qp);
+    unsigned char *sA0 = sW1 + kW1Bytes;                   // two buffers
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA0 + 2 * kA0Bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + kMlpBars);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
     if (tid == 0) {
-        mbar_init(bar_ld, 1);
-        mbar_init(bar_mma, 1);
+        mbar_init(bar(kBarW), 1);
+        mbar_init(bar(kBarA0Full0), 32 * kXWarps);
+        mbar_init(bar(kBarA0Full1), 32 * kXWarps);
+        mbar_init(bar(kBarA0Empty0), 1);
+        mbar_init(bar(kBarA0Empty1), 1);
+        mbar_init(bar(kBarD0Full), 1);
+        mbar_init(bar(kBarA1Full), 32 * kE0Warps);
+        mbar_init(bar(kBarA1Empty), 1);
+        mbar_init(bar(kBarD1Full), 1);
+        mbar_init(bar(kBarA2Full), 32 * kE1Warps);
+        mbar_init(bar(kBarD2Full), 1);
+        mbar_init(bar(kBarR1Free), 32 * kE1Warps);
+        mbar_init(bar(kBarDone), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == kMmaWarpId) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),
                      "r"(kMlpTmemCols));
@@ -463,10 +587,10 @@ __global__ void __launch_bounds__(256, 1) mlp_tc_kernel(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
 
-    // W2 and W3 images: one bulk copy per CTA
-    const uint32_t wbytes = kW2Bytes + (uint32_t)Qp * 512u;
+    // the three weight images: one bulk copy per CTA
+    const uint32_t wbytes = kW2Bytes + mlp_w3_bytes(Qp) + kW1Bytes;
     if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld),
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(kBarW)),
                      "r"(wbytes)
                      : "memory");
         const uint32_t chunk = 1u << 15;
@@ -475,74 +599,130 @@ __global__ void __launch_bounds__(256, 1) mlp_tc_kernel(const __grid_constant__ 
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
                 "%2, [%3];" ::"r"(smem_u32(sW2) + off),
-                "l"(a.ops + off), "r"(n), "r"(bar_ld)
+                "l"(a.ops + off), "r"(n), "r"(bar(kBarW))
                 : "memory");
         }
     }
-    bool alive = !__syncthreads_or(!mbar_wait(bar_ld, 0));
-    if (!alive && tid == 0) set_status(a.status, kStatusTimeout);
-
-    const uint32_t idesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMlpHidden >> 3) << 17) |
-                            ((uint32_t)(128 >> 4) << 24);
-    const uint32_t idesc3 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Qp >> 3) << 17) |
-                            ((uint32_t)(128 >> 4) << 24);
-    const uint32_t sa = smem_u32(sH), sb2 = smem_u32(sW2), sb3 = smem_u32(sW3);
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
-    unsigned char *hrow = sH + core_off(row_l, HALF * half);
-    uint32_t phase = 0;
+    bool ok = !__syncthreads_or(!mbar_wait(bar(kBarW), 0));
     const long long ntiles = (a.rows + 127) / 128;
+    const int my_tiles = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    // a wait whose verdict the whole warp takes (the tensor-memory loads and stores that follow
+    // are warp-collective)
+    auto wwait = [&](int b, uint32_t parity) {
+        return __all_sync(0xffffffffu, mbar_wait(bar(b), parity)) != 0;
+    };
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    auto row_of = [&](int j) {
+        return ((long long)blockIdx.x + (long long)j * gridDim.x) * 128 + 32 * (warp & 3) + lane;
+    };
 
-    float x[kMlpIn];
-    {
-        const long long r0 = (long long)blockIdx.x * 128 + row_l;
+    if (ok && warp < kXWarps) {
+        // features: thread = row 32 w + lane
+        const int row_l = 32 * warp + lane;
+        float x[kMlpIn];
+        auto load_x = [&](int j) {
+            const long long r = row_of(j);
 #pragma unroll
-        for (int j = 0; j < kMlpIn; ++j) x[j] = r0 < a.rows ? a.X[r0 * kMlpIn + j] : 0.f;
-    }
-    for (long long tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
-        const long long r = tile * 128 + row_l;
-        // layer 1 on the CUDA cores (this thread's half of the hidden units) -> BF16 A operand
-        if (half == 0) mlp_layer1<Q, 0>(a, x, hrow);
-        else mlp_layer1<Q, 1>(a, x, hrow);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) mlp_issue(tmem, sa, sb2, idesc2, bar_mma);
-        {   // the next tile's features, loaded while the MMAs run
-            const long long rn = (tile + gridDim.x) * 128 + row_l;
+            for (int q = 0; q < kMlpIn; ++q) x[q] = r < a.rows ? a.X[r * kMlpIn + q] : 0.f;
+        };
+        load_x(0);
+        for (int j = 0; j < my_tiles; ++j) {
+            const int b = j & 1;
+            // layer 1 of tile j - 2 read this buffer: wait for its commit
+            if (j >= 2 && !wwait(b ? kBarA0Empty1 : kBarA0Empty0, (uint32_t)((j >> 1) - 1) & 1u)) {
+                ok = false;
+                break;
+            }
+            mlp_features(x, sA0 + b * kA0Bytes, row_l);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mlp_arrive(bar(b ? kBarA0Full1 : kBarA0Full0));
+            if (j + 1 < my_tiles) load_x(j + 1);
+        }
+    } else if (ok && warp < kXWarps + kE0Warps) {
+        // layer-1 epilogue: thread = row = its TMEM lane
+        for (int j = 0; j < my_tiles; ++j) {
+            if (!wwait(kBarD0Full, (uint32_t)j & 1u)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            mlp_relu_inplace(lane_base + kColR0);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mlp_arrive(bar(kBarA1Full));
+        }
+    } else if (ok && warp < kMmaWarpId) {
+        // layer-2 and layer-3 epilogues: thread = row = its TMEM lane
+        for (int j = 0; j < my_tiles; ++j) {
+            const uint32_t ph = (uint32_t)j & 1u;
+            if (!wwait(kBarD1Full, ph)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            mlp_relu_inplace(lane_base + kColR1);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mlp_arrive(bar(kBarA2Full));
+            if (!wwait(kBarD2Full, ph)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            mlp_logits<Q>(a, lane_base, row_of(j));
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mlp_arrive(bar(kBarR1Free));
+        }
+    } else if (ok && lane == 0) {
+        // MMA warp, one lane
+        const uint32_t idesc_h = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMlpHidden >> 3) << 17) |
+                                 ((uint32_t)(128 >> 4) << 24);
+        const uint32_t idesc_q = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Qp >> 3) << 17) |
+                                 ((uint32_t)(128 >> 4) << 24);
+        const uint32_t sb1 = smem_u32(sW1), sb2 = smem_u32(sW2), sb3 = smem_u32(sW3), sa0 = smem_u32(sA0);
+        // layer 1 of tile j: its features, and region 0 free (layer 2 of tile j - 1 complete)
+        auto layer1 = [&](int j) {
+            const int b = j & 1;
+            if (!mbar_wait(bar(b ? kBarA0Full1 : kBarA0Full0), (uint32_t)(j >> 1) & 1u)) return false;
+            if (j > 0 && !mbar_wait(bar(kBarA1Empty), (uint32_t)(j - 1) & 1u)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < kMlpIn; ++j) x[j] = rn < a.rows ? a.X[rn * kMlpIn + j] : 0.f;
+            for (int ks = 0; ks < kMlpK1 / 16; ++ks)
+                mma_bf16(tmem + kColR0, smem_desc(sa0 + b * kA0Bytes + ks * 256u, 128u, kCoreSbo1),
+                         smem_desc(sb1 + ks * 256u, 128u, kCoreSbo1), idesc_h, ks ? 1u : 0u);
+            mlp_commit(bar(b ? kBarA0Empty1 : kBarA0Empty0));
+            mlp_commit(bar(kBarD0Full));
+            return true;
+        };
+        if (my_tiles > 0) ok = layer1(0);
+        for (int j = 0; j < my_tiles && ok; ++j) {
+            const uint32_t ph = (uint32_t)j & 1u, pp = (uint32_t)(j - 1) & 1u;
+            // layer 2: h1 of this tile, and region 1 free (the previous tile's logits read out)
+            if (!mbar_wait(bar(kBarA1Full), ph) || (j > 0 && !mbar_wait(bar(kBarR1Free), pp))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ks = 0; ks < kSteps; ++ks)
+                mma_bf16_ta(tmem + kColR1, tmem + kColR0 + (uint32_t)(8 * ks),
+                            smem_desc(sb2 + ks * 256u, 128u, kCoreSbo), idesc_h, ks ? 1u : 0u);
+            mlp_commit(bar(kBarA1Empty));
+            mlp_commit(bar(kBarD1Full));
+            // layer 1 of the next tile while this tile's layer-2 epilogue runs
+            if (j + 1 < my_tiles && !layer1(j + 1)) { ok = false; break; }
+            // layer 3: h2 of this tile
+            if (!mbar_wait(bar(kBarA2Full), ph)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int ks = 0; ks < kSteps; ++ks)
+                mma_bf16_ta(tmem + kColD2, tmem + kColR1 + (uint32_t)(8 * ks),
+                            smem_desc(sb3 + ks * 256u, 128u, kCoreSbo), idesc_q, ks ? 1u : 0u);
+            mlp_commit(bar(kBarD2Full));
         }
-        bool ok = mbar_wait(bar_mma, phase);
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!ok)) {
-            alive = false;
-            if (tid == 0) set_status(a.status, kStatusTimeout);
-            break;
-        }
-        // layer 2 epilogue (this thread's half of the columns): + b2, ReLU, BF16 -> A operand
-        if (half == 0) mlp_epilogue2<Q, 0>(a, lane_base, hrow);
-        else mlp_epilogue2<Q, 1>(a, lane_base, hrow);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) mlp_issue(tmem + kMlpHidden, sa, sb3, idesc3, bar_mma);
-        ok = mbar_wait(bar_mma, phase);
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!ok)) {
-            alive = false;
-            if (tid == 0) set_status(a.status, kStatusTimeout);
-            break;
-        }
-        // layer 3 epilogue: + b3 -> logits (this thread's half of the Qp columns)
-        if (half == 0) mlp_epilogue3<Q, 0>(a, lane_base, r);
-        else mlp_epilogue3<Q, 1>(a, lane_base, r);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        // completes once every MMA issued above has (at once when there were none)
+        mlp_commit(bar(kBarDone));
     }
+    if (!ok) set_status(a.status, kStatusTimeout);
+    __syncwarp();
+    // no thread frees the tensor memory while an MMA may still write it
+    if (warp == kMmaWarpId) {
+        const bool done = __shfl_sync(0xffffffffu, lane == 0 ? mbar_wait(bar(kBarDone), 0) : false, 0);
+        if (!done && lane == 0) set_status(a.status, kStatusTimeout);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0)
+    if (warp == kMmaWarpId)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kMlpTmemCols));
 }
@@ -660,12 +840,8 @@ cudaError_t launch_tc(mcmc_mlp *m, long long rows, const float *X, float *logits
     a.ops = m->tc_ops;
     a.logits = logits;
     a.status = m->status;
-    const float *h = m->small_host;   // W1, b1 | b2 | b3
-    std::memcpy(a.W1, h, sizeof a.W1);
-    std::memcpy(a.b1, h + kMlpHidden * kMlpIn, sizeof a.b1);
-    std::memcpy(a.b2, h + mlp_off_W2(), sizeof a.b2);
-    std::memcpy(a.b3, h + mlp_off_W2() + kMlpHidden, sizeof a.b3);
-    mlp_tc_kernel<Q><<<grid, 256, smem, s>>>(a);
+    a.vec_out = ((uintptr_t)logits & 15u) == 0;
+    mlp_tc_kernel<Q><<<grid, kMlpThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -687,21 +863,11 @@ cudaError_t mlp_forward_tc(mcmc_mlp *m, long long rows, const float *X, float *l
 {
     if (rows <= 0) return cudaSuccess;
     if (!m->tc_valid) {
-        const int n = (kMlpHidden + m->Qp) * 32;
+        const int n = (kMlpHidden + m->Qp) * (kMlpK / 8) + kMlpHidden * (kMlpK1 / 8);
         mlp_pack_kernel<<<(n + 255) / 256, 256, 0, s>>>(m->params, m->Q, m->Qp, m->tc_ops);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         m->launches++;
-        // the small weights travel in the launch parameters: read them back once
-        float *h = m->small_host;
-        const long long P = mlp_param_count(m->Q);
-        if ((e = cudaMemcpyAsync(h, m->params, 4 * (size_t)mlp_off_W2(), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(h + mlp_off_W2(), m->params + mlp_off_b2(), 4 * kMlpHidden,
-                                 cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(h + mlp_off_W2() + kMlpHidden, m->params + mlp_off_b3(m->Q),
-                                 4 * (size_t)(P - mlp_off_b3(m->Q)), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(s)) != cudaSuccess)
-            return e;
         m->tc_valid = true;
     }
     const long long tiles = (rows + 127) / 128;
@@ -880,8 +1046,6 @@ mcmc_status mcmc_mlp_create(int32_t qam, int32_t max_rows, void *stream, mcmc_ml
     };
     for (auto &a : allocs)
         if ((e = cudaMalloc(a.p, a.bytes)) != cudaSuccess) return bail(e);
-    if ((e = cudaMallocHost(&m->small_host, 4 * (size_t)(kMlpHidden * kMlpIn + 3 * kMlpHidden))) != cudaSuccess)
-        return bail(e);
     for (void *p : {(void *)m->params, (void *)m->adam_m, (void *)m->adam_v})
         if ((e = cudaMemsetAsync(p, 0, 4 * P, m->stream)) != cudaSuccess) return bail(e);
     if ((e = cudaMemsetAsync(m->status, 0, 256, m->stream)) != cudaSuccess) return bail(e);
@@ -899,7 +1063,6 @@ mcmc_status mcmc_mlp_destroy(mcmc_mlp *m)
                     (void *)m->dlog, (void *)m->logit, (void *)m->rowloss, (void *)m->partial,
                     (void *)m->status, (void *)m->tc_ops})
         if (p) cudaFree(p);
-    if (m->small_host) cudaFreeHost(m->small_host);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
     return MCMC_OK;

@@ -27,7 +27,6 @@ struct mcmc_mlp {
     // tensor-core operand images of W2 and W3 (BF16), rebuilt when the parameters change
     uint8_t *tc_ops = nullptr;
     bool tc_valid = false;
-    float *small_host = nullptr;   // pinned host copy of W1, b1 | b2 | b3 (launch parameters)
     // the large products of a forward or training pass (hidden layer, input and weight
     // gradients) on tcgen05 with split-BF16 operands (default on sm_103), else on CUDA cores
     bool tc_train = false;
@@ -50,8 +49,9 @@ __host__ __device__ inline long long mlp_off_b2() { return mlp_off_W2() + (long 
 __host__ __device__ inline long long mlp_off_W3() { return mlp_off_b2() + kMlpHidden; }
 __host__ __device__ inline long long mlp_off_b3(int Q) { return mlp_off_W3() + (long long)Q * kMlpHidden; }
 
-// Bytes of the tensor-core operand images: W2 (256 x 256) and W3 (Qp x 256), BF16.
-inline size_t mlp_tc_bytes(int Qp) { return (size_t)(kMlpHidden + Qp) * kMlpHidden * 2; }
+// Bytes of the tensor-core operand images, BF16: W2 | b2 (256 x 272) and W3 | b3 (Qp x 272), the
+// bias split into three terms in the extra K columns, and the layer-1 terms of W1 | b1 (256 x 48).
+inline size_t mlp_tc_bytes(int Qp) { return (size_t)(kMlpHidden + Qp) * (kMlpHidden + 16) * 2 + (size_t)kMlpHidden * 48 * 2; }
 
 // logits [rows x Q] of X [rows x 6]: FP32 CUDA-core kernels in chunks of max_rows rows.
 cudaError_t mlp_forward_simt(mcmc_mlp *m, long long rows, const float *X, float *logits,

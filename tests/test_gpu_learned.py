@@ -60,16 +60,18 @@ def test_forward_fp32_matches_oracle(qam, train_tc):
     m.destroy()
 
 
-@pytest.mark.parametrize("qam", [4, 16, 64])
-def test_forward_tensor_cores_match_quantised_oracle(qam):
+@pytest.mark.parametrize("qam,rows", [(4, 128 * 40 + 77), (16, 128 * 40 + 77), (64, 128 * 40 + 77),
+                                      (16, 128 * 152 * 3 + 77), (64, 128 * 152 * 3 + 77)])
+def test_forward_tensor_cores_match_quantised_oracle(qam, rows):
     """BF16 tcgen05 forward against the oracle's quantised network (hidden activations and
     layer-2/3 weights rounded to BF16). The two differ by FP32 vs FP64 accumulation, except
     where an activation sits within FP32 error of a BF16 rounding boundary and rounds the other
     way (~1e-5 of activations): such a row moves by about one BF16 ulp of one activation times
-    its weights."""
+    its weights. The larger row counts give every CTA of the persistent kernel several tiles,
+    so its pipeline (layer 1 of one tile beside the MMAs and epilogues of the previous one)
+    runs through every buffer's phases several times."""
     import torch
     p = _params(qam)
-    rows = 128 * 40 + 77
     X = _features(rows, seed=1)
     m = _mlp(qam, p)
     out = m.forward(torch.tensor(X, dtype=torch.float32, device="cuda"),
