@@ -169,7 +169,9 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels,
 
 /* Algorithm 1's loop: `iterations` transitions of every chain of every channel, numbered
  * t_offset+1 .. t_offset+iterations (t_offset >= 0). Resuming with t_offset = the number of
- * transitions already done continues the same random stream exactly. */
+ * transitions already done continues the same random stream exactly. The first run after
+ * preprocess (or a warm start) first evaluates the states' energies in FP64, where the chains'
+ * tracked energies and running best start. */
 mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t t_offset);
 
 /* Read-out (Sec. III-A hard decision, Algorithm 2 / Eq. (34) soft output) from the chains' final
@@ -229,6 +231,12 @@ mcmc_status mcmc_detect_set_chains(mcmc_detector *d, const int8_t *states, int32
  * CTAs per cluster for thread-block clusters). The choices of the autotuner, per shape class,
  * are what they show. 0 for NULL or before preprocess; info may be NULL. */
 int32_t mcmc_detect_launch_groups(const mcmc_detector *d, int32_t *info, int32_t cap);
+
+/* Device time (ms) of the chain kernels of the latest n runs, oldest first: from the start of
+ * the first launch group to the end of the last (CUDA events on the handle's stream), without
+ * the exact energy evaluations before and after them. 1 <= n <= min(runs so far, 64), else
+ * MCMC_EINVAL. Waits for those runs' events. */
+mcmc_status mcmc_detect_run_kernel_ms(mcmc_detector *d, int32_t n, float *ms);
 
 /* Waits for every call enqueued on the handle's stream; reports device faults. */
 mcmc_status mcmc_detect_synchronize(mcmc_detector *d);

@@ -110,7 +110,8 @@ mcmc_status mcmc_detect_set_model(mcmc_detector *d, mcmc_mlp *m, float lambda,
                                   int32_t tensor_cores);
 
 /* Warm start: redraws the states of every chain of the network's channels from the network at
- * x = 0 and recomputes their energies in FP64 (the running best restarts there). */
+ * x = 0; their energies are evaluated in FP64 when next needed (the next run, estimate or mixture
+ * move), and the running best restarts there. */
 mcmc_status mcmc_detect_init_learned(mcmc_detector *d);
 
 /* One mixture move, numbered t (1 .. 2^32 - 1), of every chain of the network's channels. */

@@ -42,7 +42,7 @@ ABI_FUNCTIONS = [
     "mcmc_detect_set_chains", "mcmc_detect_synchronize", "mcmc_detect_destroy",
     "mcmc_status_string", "mcmc_detect_last_error", "mcmc_detect_kernel_launches",
     "mcmc_detect_noalloc", "mcmc_detect_llr_list", "mcmc_detect_get_tracked",
-    "mcmc_detect_get_trace", "mcmc_detect_launch_groups",
+    "mcmc_detect_get_trace", "mcmc_detect_launch_groups", "mcmc_detect_run_kernel_ms",
 ]
 
 # Every entry point of include/mcmcdet_learned.h.
@@ -114,6 +114,8 @@ def load(path: Optional[str] = None):
     l.mcmc_detect_get_tracked.restype = ctypes.c_int
     l.mcmc_detect_launch_groups.argtypes = [vp, vp, i32]
     l.mcmc_detect_launch_groups.restype = ctypes.c_int32
+    l.mcmc_detect_run_kernel_ms.argtypes = [vp, i32, vp]
+    l.mcmc_detect_run_kernel_ms.restype = ctypes.c_int
     l.mcmc_detect_get_trace.argtypes = [vp, vp, i32]
     l.mcmc_detect_get_trace.restype = ctypes.c_int
     l.mcmc_detect_set_chains.argtypes = [vp, vp, i32]
@@ -332,6 +334,13 @@ class Detector:
         self._l.mcmc_detect_launch_groups(self._h, buf, n)
         keys = ("engine", "tile", "packed", "max_n", "items", "ctas_per_sm")
         return [dict(zip(keys, buf[6 * i:6 * i + 6])) for i in range(n)]
+
+    def run_kernel_ms(self, n: int = 1):
+        """Device time (ms) of the chain kernels of the latest n runs, oldest first, without the
+        exact energy evaluations around them (waits for those runs)."""
+        buf = (ctypes.c_float * max(int(n), 1))()
+        self._check(self._l.mcmc_detect_run_kernel_ms(self._h, int(n), buf))
+        return [float(v) for v in buf[:int(n)]]
 
     def set_chains(self, states, *, host_io: Optional[bool] = None):
         if host_io is None:

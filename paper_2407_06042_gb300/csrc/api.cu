@@ -64,6 +64,10 @@ struct mcmc_detector {
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> ev_join;
     cudaEvent_t ev_fork = nullptr;
+    // start / end of the chain kernels of the latest runs (the refreshes around them excluded)
+    static constexpr int kRunSlots = 64;
+    cudaEvent_t ev_run[kRunSlots][2] = {};
+    long long runs = 0;
     int device = 0;
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
@@ -754,6 +758,9 @@ mcmc_status mcmc_detect_destroy(mcmc_detector *d)
     for (cudaStream_t a : d->aux) cudaStreamDestroy(a);
     for (cudaEvent_t e : d->ev_join) cudaEventDestroy(e);
     if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+    for (auto &pr : d->ev_run)
+        for (cudaEvent_t e : pr)
+            if (e) cudaEventDestroy(e);
     if (d->own_stream && d->stream) cudaStreamDestroy(d->stream);
     cudaGetLastError();
     delete d;
@@ -985,13 +992,12 @@ mcmc_status mcmc_detect_preprocess(mcmc_detector *d, int32_t n_channels, const i
         if (gs != MCMC_OK) return gs;
     }
 
-    // exact energies of the initial states (every precision); the running best starts there
-    {
-        mcmc_status es = refresh_energies(d, P<double>(d->d_f), true, false);
-        if (es != MCMC_OK) return es;
-    }
-    d->f_valid = true;
-    d->f_exact = true;
+    // the exact energies of the initial states (every precision), where the running best
+    // starts, are evaluated when first needed: by the next run, estimate or mixture move (the
+    // read-outs hand out FP64 evaluations meanwhile); a warm start that replaces the states
+    // first does not pay for them twice
+    d->f_valid = false;
+    d->f_exact = false;
     d->d_valid = false;
     d->transitions = 0;
     d->prepared = true;
@@ -1007,6 +1013,11 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         return fail(d, MCMC_EINVAL, "iterations/t_offset out of range");
     if (iterations == 0) return MCMC_OK;
     const bool fp64 = d->cfg.precision == MCMC_PREC_FP64;
+    // the chains start from exact energies of their states (after preprocess or a warm start)
+    {
+        mcmc_status es = ensure_energies(d);
+        if (es != MCMC_OK) return es;
+    }
     const ChainArgs ca = chain_args(d, iterations, t_offset);
     // FP32 / MIXED: the energies the chains tracked in FP32 steps are replaced by exact
     // evaluations when the run ends (refresh_period >= 0), and the correction is recorded
@@ -1042,9 +1053,12 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         }
         for (size_t gi = 1; gi < ng && e == cudaSuccess; ++gi)
             e = cudaStreamWaitEvent(d->stream, d->ev_join[gi - 1], 0);
-        if (e == cudaSuccess && final_refresh) e = launch_refresh(fr, d->stream);
         return e;
     };
+    const int slot = (int)(d->runs % mcmc_detector::kRunSlots);
+    for (int k = 0; k < 2; ++k)
+        if (!d->ev_run[slot][k]) CK(cudaEventCreate(&d->ev_run[slot][k]), "event");
+    CK(cudaEventRecord(d->ev_run[slot][0], d->stream), "record run start");
     // one CUDA graph per run (replayed; updated in place when only the arguments changed) when
     // asked for, and by default for a batch of several launch groups
     const bool graph = (d->cfg.engine & MCMC_ENGINE_GRAPH) ||
@@ -1075,6 +1089,9 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
     } else {
         CK(enqueue(), "chain kernel");
     }
+    CK(cudaEventRecord(d->ev_run[slot][1], d->stream), "record run end");
+    d->runs++;
+    if (final_refresh) CK(launch_refresh(fr, d->stream), "energies");
     d->launches += (long long)d->groups.size() + (final_refresh ? 1 : 0);
     d->f_valid = true;
     d->f_exact = fp64 || final_refresh;
@@ -1292,6 +1309,20 @@ int32_t mcmc_detect_launch_groups(const mcmc_detector *d, int32_t *info, int32_t
     return n;
 }
 
+mcmc_status mcmc_detect_run_kernel_ms(mcmc_detector *d, int32_t n, float *ms)
+{
+    if (!d) return MCMC_EINVAL;
+    d->err.clear();
+    if (!ms || n < 1 || n > mcmc_detector::kRunSlots || n > d->runs)
+        return fail(d, MCMC_EINVAL, "n must lie in 1 .. min(runs so far, %d)", mcmc_detector::kRunSlots);
+    for (int32_t i = 0; i < n; ++i) {
+        const int slot = (int)((d->runs - n + i) % mcmc_detector::kRunSlots);
+        CK(cudaEventSynchronize(d->ev_run[slot][1]), "event synchronize");
+        CK(cudaEventElapsedTime(&ms[i], d->ev_run[slot][0], d->ev_run[slot][1]), "event time");
+    }
+    return MCMC_OK;
+}
+
 mcmc_status mcmc_detect_synchronize(mcmc_detector *d)
 {
     if (!d) return MCMC_EINVAL;
@@ -1431,11 +1462,10 @@ mcmc_status mcmc_detect_init_learned(mcmc_detector *d)
     CK(net_forward(d, rows, P<float>(d->d_mx_X), P<float>(d->d_mx_logits)), "network forward");
     CK(launch_mix(2, step_args(d), d->n_channels, d->max_nt, d->stream), "warm start kernel");
     d->launches++;
-    // exact energies of the warm-start states; the running best restarts there
-    st = refresh_energies(d, P<double>(d->d_f), true, false);
-    if (st != MCMC_OK) return st;
-    d->f_valid = true;
-    d->f_exact = true;
+    // exact energies of the warm-start states, where the running best restarts: evaluated when
+    // first needed, as after preprocess
+    d->f_valid = false;
+    d->f_exact = false;
     d->d_valid = false;
     return MCMC_OK;
 }

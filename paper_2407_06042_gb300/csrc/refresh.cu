@@ -17,7 +17,10 @@
 //
 // One CTA per (channel, block of chains): the channel's digits are generated 32 rows at a time
 // into shared memory; each warp takes four chains at a time and each lane one row of the block,
-// so every digit word loaded serves four chains' DP4A products.
+// so every digit word loaded serves four chains' DP4A products. Gt is symmetric, so a block of
+// rows needs only its own 32 x 32 diagonal block (each ordered pair once) and the columns to its
+// right (counted twice, for the mirrored pairs below the diagonal): about (N + 32) / 2N of the
+// digits and products of the full form, with the same integer sums.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -104,9 +107,10 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a,
     const int sh = sflag[0];
 
     for (int r0 = 0; r0 < N; r0 += kRowBlock) {
-        // digit planes of rows r0 .. r0 + 31
-        for (int u = tid; u < kRowBlock * nw; u += blockDim.x) {
-            const int i = u / nw, w = u - i * nw, n = r0 + i;
+        // digit planes of rows r0 .. r0 + 31, columns r0 .. N - 1 (word w0 onwards)
+        const int w0 = r0 / 4, nwb = nw - w0, wd = min(nwb, kRowBlock / 4);
+        for (int u = tid; u < kRowBlock * nwb; u += blockDim.x) {
+            const int i = u / nwb, wr = u - i * nwb, w = w0 + wr, n = r0 + i;
             uint32_t dw[kDigits] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
             if (n < N) {
 #pragma unroll
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a,
                 }
             }
 #pragma unroll
-            for (int k = 0; k < kDigits; ++k) sD[(k * kRowBlock + i) * rs + w] = dw[k];
+            for (int k = 0; k < kDigits; ++k) sD[(k * kRowBlock + i) * rs + wr] = dw[k];
         }
         __syncthreads();
         // lane = row r0 + lane; a warp takes four chains at a time
@@ -134,17 +138,26 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a,
 #pragma unroll
                 for (int k = 0; k < kDigits; ++k) t[j][k] = 0;
             const uint32_t *x0 = sX + (size_t)(4 * cq) * nw;
-            for (int w = 0; w < nw; ++w) {
-                uint32_t dv[kDigits];
+            auto dp_words = [&](int wa, int wb) {
+                for (int wr = wa; wr < wb; ++wr) {
+                    uint32_t dv[kDigits];
 #pragma unroll
-                for (int k = 0; k < kDigits; ++k) dv[k] = sD[(k * kRowBlock + lane) * rs + w];
+                    for (int k = 0; k < kDigits; ++k) dv[k] = sD[(k * kRowBlock + lane) * rs + wr];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int xw = (int)x0[(size_t)j * nw + w];   // rows past nc hold zeros
+                    for (int j = 0; j < 4; ++j) {
+                        const int xw = (int)x0[(size_t)j * nw + w0 + wr];   // rows past nc hold zeros
 #pragma unroll
-                    for (int k = 0; k < kDigits; ++k) t[j][k] = __dp4a((int)dv[k], xw, t[j][k]);
+                        for (int k = 0; k < kDigits; ++k) t[j][k] = __dp4a((int)dv[k], xw, t[j][k]);
+                    }
                 }
-            }
+            };
+            // the columns right of the diagonal block, doubled, then the diagonal block
+            dp_words(wd, nwb);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int k = 0; k < kDigits; ++k) t[j][k] *= 2;
+            dp_words(0, wd);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int c = 4 * cq + j;

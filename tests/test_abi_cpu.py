@@ -65,6 +65,7 @@ def test_host_only_entry_points():
     assert lib.mcmc_detect_get_tracked(None, None, None, 0) == 1
     assert lib.mcmc_detect_get_trace(None, None, 0) == 1
     assert lib.mcmc_detect_launch_groups(None, None, 0) == 0
+    assert lib.mcmc_detect_run_kernel_ms(None, 1, None) == 1
 
 
 def test_config_struct_matches_header():
