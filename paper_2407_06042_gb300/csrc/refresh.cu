@@ -13,7 +13,9 @@
 // One FP64 Horner pass gives xt^T Gt xt = 2^-sh sum_k 256^k Q_k. Each entry of Gt is off by at
 // most half a unit of 2^-sh <= 2^-52 max Gt_nn, so the quadratic form is off by at most
 // 2^-53 max Gt_nn (sum_n |xt_n|)^2, comparable to the rounding of an FP64 sum. The linear term
-// xt^T zt is an FP64 sum of N products.
+// xt^T zt is formed the same way: zt at the fixed point 2^-sz, sz = 53 - exponent(max_m |zt_m|),
+// in seven int8 digits, exact DP4A sums, one Horner pass (off by at most
+// 2^-53 max_m |zt_m| sum_m |xt_m|).
 //
 // One CTA per (channel, block of chains): the channel's digits are generated 32 rows at a time
 // into shared memory; each warp takes four chains at a time and each lane one row of the block,
@@ -50,7 +52,8 @@ __host__ __device__ inline size_t refresh_smem_bytes(int chains, int N)
     return (size_t)cpb * nw * 4                                   // states (odd integers, int8)
            + (size_t)kDigits * kRowBlock * refresh_row_stride(N) * 4   // digit planes of one block
            + (size_t)cpb * kDigits * 4                            // Q_k per chain
-           + 16;                                                  // shift, flags
+           + (size_t)kDigits * nw * 4                             // digit planes of zt
+           + 16;                                                  // shifts, flags
 }
 
 __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a, int cpb)
@@ -66,7 +69,9 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a,
     uint32_t *sX = reinterpret_cast<uint32_t *>(smem);                       // [cpb][nw]
     uint32_t *sD = sX + (size_t)cpb * nw;                                    // [7][32][rs]
     int *sQ = reinterpret_cast<int *>(sD + (size_t)kDigits * kRowBlock * rs);  // [cpb][7]
-    int *sflag = sQ + (size_t)cpb * kDigits;                                 // [0] shift, [1] bad
+    uint32_t *sZ = reinterpret_cast<uint32_t *>(sQ + (size_t)cpb * kDigits); // [7][nw]
+    int *sflag = reinterpret_cast<int *>(sZ + (size_t)kDigits * nw);        // [0] shift, [1] bad,
+                                                                             // [2] shift of zt
     const double *G = a.G64 + d.mat_off;
     const double *z = a.z64 + d.vec_off;
     const int8_t *states = a.states + d.state_off + (long long)c0 * N;
@@ -101,10 +106,38 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a,
             sflag[0] = 53 - ex;               // |Gt_nm| 2^sh < 2^53
             sflag[1] = 0;
         }
+    } else if (warp == 1) {
+        double mx = 0.0;
+        for (int n = lane; n < N; n += 32) mx = fmax(mx, fabs(z[n]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            int ex = 0;
+            frexp(mx, &ex);
+            sflag[2] = 53 - ex;               // |zt_m| 2^sz < 2^53
+        }
     }
     __syncthreads();
     if (bad) atomicOr(&sflag[1], 1);
-    const int sh = sflag[0];
+    const int sh = sflag[0], sz = sflag[2];
+    // zt at the fixed point 2^-sz in seven balanced int8 digits, four values per word (the
+    // linear term x^T zt then is an exact int32 sum per digit, like the quadratic form)
+    for (int w = tid; w < nw; w += blockDim.x) {
+        uint32_t dw[kDigits] = {0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = 4 * w + j;
+            long long v = m < N ? fixed_of(z[m], sz) : 0;
+#pragma unroll
+            for (int k = 0; k < kDigits; ++k) {
+                const int lo = (int)(v & 255), dk = lo >= 128 ? lo - 256 : lo;
+                v = (v - dk) >> 8;
+                dw[k] |= (uint32_t)(dk & 255) << (8 * j);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kDigits; ++k) sZ[k * nw + w] = dw[k];
+    }
 
     for (int r0 = 0; r0 < N; r0 += kRowBlock) {
         // digit planes of rows r0 .. r0 + 31, columns r0 .. N - 1 (word w0 onwards)
@@ -138,26 +171,20 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a,
 #pragma unroll
                 for (int k = 0; k < kDigits; ++k) t[j][k] = 0;
             const uint32_t *x0 = sX + (size_t)(4 * cq) * nw;
-            auto dp_words = [&](int wa, int wb) {
-                for (int wr = wa; wr < wb; ++wr) {
-                    uint32_t dv[kDigits];
+            // the diagonal block's words once, the words to its right with x doubled (each byte
+            // 2 x, |2 x| <= 14: the shift's carries into the next byte are masked off)
+            for (int wr = 0; wr < nwb; ++wr) {
+                uint32_t dv[kDigits];
 #pragma unroll
-                    for (int k = 0; k < kDigits; ++k) dv[k] = sD[(k * kRowBlock + lane) * rs + wr];
+                for (int k = 0; k < kDigits; ++k) dv[k] = sD[(k * kRowBlock + lane) * rs + wr];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int xw = (int)x0[(size_t)j * nw + w0 + wr];   // rows past nc hold zeros
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t xw = x0[(size_t)j * nw + w0 + wr];   // rows past nc hold zeros
+                    const int xs = (int)(wr < wd ? xw : (xw << 1) & 0xFEFEFEFEu);
 #pragma unroll
-                        for (int k = 0; k < kDigits; ++k) t[j][k] = __dp4a((int)dv[k], xw, t[j][k]);
-                    }
+                    for (int k = 0; k < kDigits; ++k) t[j][k] = __dp4a((int)dv[k], xs, t[j][k]);
                 }
-            };
-            // the columns right of the diagonal block, doubled, then the diagonal block
-            dp_words(wd, nwb);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int k = 0; k < kDigits; ++k) t[j][k] *= 2;
-            dp_words(0, wd);
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int c = 4 * cq + j;
@@ -176,37 +203,44 @@ __global__ void __launch_bounds__(kRefreshThreads) refresh_kernel(RefreshArgs a,
         __syncthreads();
     }
 
-    // f per chain: the integer sums recombined once in FP64, the linear term in FP64
+    // f per chain: the integer sums recombined once in FP64, the linear term in FP64; the
+    // largest corrections (non-negative doubles, ordered as their bit patterns) per warp
+    unsigned long long mdr = 0ull, mdr_rel = 0ull;
     for (int c = tid; c < nc; c += blockDim.x) {
         double q = 0.0;
 #pragma unroll
         for (int k = kDigits - 1; k >= 0; --k) q = fma(q, 256.0, (double)sQ[c * kDigits + k]);
         q = ldexp(q, -sh);
-        double l0 = 0.0, l1 = 0.0;
+        int lk[kDigits] = {0, 0, 0, 0, 0, 0, 0};
         const uint32_t *xc = sX + (size_t)c * nw;
         for (int w = 0; w < nw; ++w) {
-            const uint32_t word = xc[w];
+            const int xw = (int)xc[w];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int m = 4 * w + j;
-                if (m >= N) break;
-                const double xv = (double)(int8_t)((word >> (8 * j)) & 255u);
-                if (j & 1) l1 = fma(xv, z[m], l1);
-                else l0 = fma(xv, z[m], l0);
-            }
+            for (int k = 0; k < kDigits; ++k) lk[k] = __dp4a((int)sZ[k * nw + w], xw, lk[k]);
         }
-        const double f = -(a.yy[b] - 2.0 * (l0 + l1) + q) * d.inv_s2;
+        double l = 0.0;
+#pragma unroll
+        for (int k = kDigits - 1; k >= 0; --k) l = fma(l, 256.0, (double)lk[k]);
+        l = ldexp(l, -sz);
+        const double f = -(a.yy[b] - 2.0 * l + q) * d.inv_s2;
         if (!isfinite(f)) set_status(a.status, kStatusNumeric);
         const long long ci = (long long)b * a.chains + c0 + c;
         if (a.drift_bits) {
             const double dr = fabs(a.f[ci] - f);
-            atomicMax(a.drift_bits, (unsigned long long)__double_as_longlong(dr));
-            if (a.drift_rel_bits)
-                atomicMax(a.drift_rel_bits,
-                          (unsigned long long)__double_as_longlong(dr / fmax(fabs(f), 1e-300)));
+            mdr = max(mdr, (unsigned long long)__double_as_longlong(dr));
+            mdr_rel = max(mdr_rel, (unsigned long long)__double_as_longlong(dr / fmax(fabs(f), 1e-300)));
         }
         a.f[ci] = f;
         if (a.reset_best) a.best_f[ci] = f;
+    }
+    if (a.drift_bits) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            mdr = max(mdr, __shfl_xor_sync(0xffffffffu, mdr, o));
+            mdr_rel = max(mdr_rel, __shfl_xor_sync(0xffffffffu, mdr_rel, o));
+        }
+        if (lane == 0 && mdr) atomicMax(a.drift_bits, mdr);
+        if (lane == 0 && mdr_rel && a.drift_rel_bits) atomicMax(a.drift_rel_bits, mdr_rel);
     }
     if (sflag[1]) {
         if (tid == 0) set_status(a.status, kStatusBadState);
