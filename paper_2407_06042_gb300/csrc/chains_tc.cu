@@ -269,20 +269,27 @@ __device__ __forceinline__ void cl_send_b(const TcCtx &x)
 }
 
 // Threads 0 .. C-1 (chain c): publish 16 bytes into slot [buffer][this rank][c] of every CTA of
-// the cluster and wait (bounded) until every CTA has published. The caller reads the CL slots of
-// chain c with cl_slot() and then calls cl_next() (all threads).
+// the cluster and wait (bounded) until every CTA has published. The C threads store into every
+// CTA's slots, meet (a warp or named barrier), and then thread r alone releases them to CTA r
+// with one cluster-scope fence and one remote arrival: CL arrivals per CTA and exchange instead
+// of CL x C release-arrivals. The caller reads the CL slots of chain c with cl_slot() and then
+// calls cl_next() (all threads).
 template <int CL>
 __device__ __forceinline__ bool cl_exchange(const TcCtx &x, int c, uint4 v)
 {
     const uint32_t slot =
         smem_u32(x.sx) + (uint32_t)(((x.x_buf * CL + x.rank) * x.C + c) * 16);
 #pragma unroll
-    for (int r = 0; r < CL; ++r) {
+    for (int r = 0; r < CL; ++r)
         asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(cl_map(slot, r)),
                      "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                      : "memory");
-        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
-                         cl_map(x.bar_x, r))
+    // every exchanging thread's stores happen before the releases below
+    if (x.C <= 32) __syncwarp(x.C == 32 ? 0xffffffffu : (1u << x.C) - 1u);
+    else asm volatile("bar.sync 1, %0;" ::"r"(x.C) : "memory");
+    if (c < CL) {
+        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_map(x.bar_x, c))
                      : "memory");
     }
     return mbar_wait_cl(x.bar_x, x.x_phase);
@@ -419,24 +426,40 @@ __device__ __forceinline__ void tc_gemm_issue(TcCtx &x)
         }
         return;
     }
-    if (x.tid == 0) {
+    if (x.tid == 0 || (CL > 1 && x.tid == 32)) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         bool go = true;
         if constexpr (CL > 1) {
             // the other CTAs' slices of x' complete on the B-slice barrier
-            cl_send_b<CL>(x);
+            if (x.tid == 0) cl_send_b<CL>(x);
             if (!mbar_wait(x.bar_b, x.b_phase)) { x.fail = true; go = false; }
         }
         // the descriptors were laid out for this work item by tc_mma_descs: only the issue is left
-        const int per_tile = x.S * (x.Kp / 16);
+        const int nk = x.Kp / 16, per_tile = x.S * nk;
         const uint32_t idesc = x.idesc;
-        for (int t = 0; t < MT && go; ++t) {
-            const uint32_t d = x.tmem + (uint32_t)(t * x.C);
-            const uint4 *dl = x.sdsc + t * per_tile;
+        if constexpr (CL > 1) {
+            // a cluster CTA's K = N > 128 is long: two issuers take the first and the second half
+            // of the K steps into two accumulator blocks (the second 7 C columns further, past
+            // the carried tables), which the reads add, so the two dependent MMA chains run side
+            // by side in the tensor pipe
+            const int h = (nk + 1) / 2, k0 = x.tid == 0 ? 0 : h, k1 = x.tid == 0 ? h : nk;
+            const uint32_t d = x.tmem + (x.tid == 0 ? 0u : 7u * (uint32_t)x.C);
+            bool first = true;
+            for (int sterm = 0; sterm < x.S && go; ++sterm)
+                for (int ks = k0; ks < k1; ++ks) {
+                    const uint4 v = x.sdsc[sterm * nk + ks];
+                    mma_bf16(d, ((uint64_t)v.y << 32) | v.x, ((uint64_t)v.w << 32) | v.z, idesc, first ? 0u : 1u);
+                    first = false;
+                }
+        } else {
+            for (int t = 0; t < MT && go; ++t) {
+                const uint32_t d = x.tmem + (uint32_t)(t * x.C);
+                const uint4 *dl = x.sdsc + t * per_tile;
 #pragma unroll 4
-            for (int e = 0; e < per_tile; ++e) {
-                const uint4 v = dl[e];
-                mma_bf16(d, ((uint64_t)v.y << 32) | v.x, ((uint64_t)v.w << 32) | v.z, idesc, e ? 1u : 0u);
+                for (int e = 0; e < per_tile; ++e) {
+                    const uint4 v = dl[e];
+                    mma_bf16(d, ((uint64_t)v.y << 32) | v.x, ((uint64_t)v.w << 32) | v.z, idesc, e ? 1u : 0u);
+                }
             }
         }
         asm volatile(
@@ -455,7 +478,7 @@ __device__ __forceinline__ bool tc_gemm_wait(TcCtx &x, bool prefetch_next)
     const bool ok = mbar_wait(x.bar_mma, x.mma_phase);
     x.mma_phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if constexpr (CL > 1) return ok && !(x.tid == 0 && x.fail);
+    if constexpr (CL > 1) return ok && !((x.tid == 0 || x.tid == 32) && x.fail);
     if constexpr (tc_streamed(MT)) {
         if (x.tid == 0) {
             if (ok && prefetch_next) tc_stream_prefetch<MT>(x);
@@ -465,14 +488,22 @@ __device__ __forceinline__ bool tc_gemm_wait(TcCtx &x, bool prefetch_next)
     return ok;
 }
 
-// TMEM -> registers: Gt x (g) and P~ Gt x (m) of this thread's dimension for its 8 chains.
-template <int MT>
+// TMEM -> registers: Gt x (g) and P~ Gt x (m) of this thread's dimension for its 8 chains
+// (a cluster CTA adds its second accumulator block, 7 C columns further).
+template <int MT, int CL = 1>
 __device__ __forceinline__ void tc_read(const TcCtx &x, float (&g)[MT][4], float (&m)[MT][4])
 {
 #pragma unroll
     for (int t = 0; t < MT; ++t) {
         float v[8];
-        tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + x.gofs + 8 * x.cgi), v);
+        const uint32_t ta = x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + x.gofs + 8 * x.cgi);
+        tmem_ld8(ta, v);
+        if constexpr (CL > 1) {
+            float v1[8];
+            tmem_ld8(ta + 7u * (uint32_t)x.C, v1);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] += v1[j];
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const float send = x.h ? v[j] : v[4 + j];
@@ -486,10 +517,18 @@ __device__ __forceinline__ void tc_read(const TcCtx &x, float (&g)[MT][4], float
 
 // TMEM -> registers for one 128-row tile t: Gt x (g) and P~ Gt x (m) of this thread's dimension
 // for its 4 chains (the streamed kernels read tile by tile to bound register pressure).
+template <int CL = 1>
 __device__ __forceinline__ void tc_read_tile(const TcCtx &x, int t, float (&g)[4], float (&m)[4])
 {
     float v[8];
-    tmem_ld8(x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + x.gofs + 8 * x.cgi), v);
+    const uint32_t ta = x.tmem + ((uint32_t)(32 * x.q) << 16) + (uint32_t)(t * x.C + x.gofs + 8 * x.cgi);
+    tmem_ld8(ta, v);
+    if constexpr (CL > 1) {
+        float v1[8];
+        tmem_ld8(ta + 7u * (uint32_t)x.C, v1);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += v1[j];
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const float send = x.h ? v[j] : v[4 + j];
@@ -700,7 +739,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
     }
     {
         float g[MT][4], m[MT][4];
-        if (alive) tc_read<MT>(x, g, m);
+        if (alive) tc_read<MT, CL>(x, g, m);
 #pragma unroll
         for (int t = 0; t < MT; ++t)
 #pragma unroll
@@ -851,7 +890,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
         for (int t = 0; t < MT; ++t) {
             const uint64_t z2 = f2_splat(2.f * zt[t]);
             float gpt[4], mpt[4];
-            tc_read_tile(x, t, gpt, mpt);
+            tc_read_tile<CL>(x, t, gpt, mpt);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 const uint64_t gg = f2_pack(gpt[2 * p], gpt[2 * p + 1]);
@@ -995,7 +1034,7 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
 #pragma unroll
                 for (int t = 0; t < MT; ++t) {
                     float g[4], m[4];
-                    tc_read_tile(x, t, g, m);
+                    tc_read_tile<CL>(x, t, g, m);
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
                         float ka[2], da[2], sa[2], sb[2];
@@ -1287,13 +1326,13 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
 
     if (x.tid == 0) {
         mbar_init(x.bar_tma, 1);
-        mbar_init(x.bar_mma, 1);
+        mbar_init(x.bar_mma, CL > 1 ? 2 : 1);   // clusters: two issuers commit
         for (int b = 0; b < 2; ++b) {
             mbar_init(x.bar_full[b], 1);
             mbar_init(x.bar_empty[b], 1);
         }
         mbar_init(x.bar_b, 1);
-        mbar_init(x.bar_x, (uint32_t)(CL * C));   // every CTA's C exchanging threads
+        mbar_init(x.bar_x, (uint32_t)CL);         // one release-arrival from every CTA
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (x.warp == 0) {
