@@ -44,6 +44,7 @@ def test_learned_host_only_entry_points():
     assert lib.mcmc_mlp_create(16, 16, None, None) == 1
     assert lib.mcmc_mlp_destroy(None) == 1
     assert lib.mcmc_mlp_last_error(None) == b"null handle"
+    assert lib.mcmc_mlp_set_train_engine(None, 1) == 1
     assert lib.mcmc_detect_mix_step(None, 1) == 1
     assert lib.mcmc_detect_set_model(None, None, 0.5, 0) == 1
 
