@@ -61,7 +61,8 @@ def test_forward_fp32_matches_oracle(qam, train_tc):
 
 
 @pytest.mark.parametrize("qam,rows", [(4, 128 * 40 + 77), (16, 128 * 40 + 77), (64, 128 * 40 + 77),
-                                      (16, 128 * 152 * 3 + 77), (64, 128 * 152 * 3 + 77)])
+                                      (16, 128 * 152 * 3 + 77), (64, 128 * 152 * 3 + 77),
+                                      (16, 1), (4, 129)])
 def test_forward_tensor_cores_match_quantised_oracle(qam, rows):
     """BF16 tcgen05 forward against the oracle's quantised network (hidden activations and
     layer-2/3 weights rounded to BF16). The two differ by FP32 vs FP64 accumulation, except
