@@ -24,9 +24,11 @@
  *   wt = (Gt + (sigma^2 / 2) I)^{-1} zt               (Remark 1's preconditioned matched filter)
  *   F_i = [r_i, r_{Nt+i}, wt_i, wt_{Nt+i}, log Gt_ii, log sigma^2]   (6 FP32 values per row)
  * Training: softmax cross-entropy of the logits against symbol labels, Adam (Kingma & Ba) with
- * beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected, FP32 throughout, on CUDA cores.
- * Inference: FP32 on CUDA cores, or on tcgen05 tensor cores with the hidden activations and the
- * weights of layers 2 and 3 rounded to BF16 (round to nearest even) and FP32 accumulation.
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected, FP32-accurate throughout (the matrix
+ * products on tcgen05 from three-term BF16 splits, or on CUDA cores: mcmc_mlp_set_train_engine).
+ * Inference: FP32-accurate through the training products, or the BF16 network on tcgen05 tensor
+ * cores: the hidden activations and the weights of layers 2 and 3 rounded to BF16 (round to
+ * nearest even), layer 1 and every bias FP32-accurate, FP32 accumulation.
  *
  * Random numbers (Philox4x32-10 as in mcmcdet.h): a mixture move numbered t uses transition t's
  * proposal uniforms (dimension n: counter (t, n, channel, chain / 4)) and acceptance uniform;
@@ -65,13 +67,13 @@ mcmc_status mcmc_mlp_create(int32_t qam, int32_t max_rows, void *stream, mcmc_ml
 mcmc_status mcmc_mlp_destroy(mcmc_mlp *m);
 const char *mcmc_mlp_last_error(const mcmc_mlp *m);
 
-/* Engine of the matrix products of training (loss_grad, train_step) and of the CUDA-core
- * forward: the three layers' products, the input gradients and the weight gradients summed over
- * the rows. tensor_cores = 1 (the default on sm_103): tcgen05 tiles of 128 x 64, 128 or 256 with
- * each FP32 operand split into two BF16 terms (hi + lo, about 2^-17 relative) and the products
- * hi*hi + hi*lo + lo*hi accumulated in FP32; 0: the FP32 CUDA-core kernel. The bias gradients
- * (column sums) run on CUDA cores either way. Both engines are deterministic.
- * MCMC_EUNSUPPORTED for 1 without sm_103. */
+/* Engine of the matrix products of training (loss_grad, train_step) and of the forward that
+ * mcmc_mlp_forward runs with tensor_cores = 0: the three layers' products, the input gradients
+ * and the weight gradients summed over the rows. tensor_cores = 1 (the default on sm_103):
+ * tcgen05 tiles of 128 x 64 or 128 x 128, each FP32 operand split into three BF16 terms (to 2^-26
+ * of itself) and the six leading term products accumulated in FP32, as accurate as an FP32
+ * product; 0: the FP32 CUDA-core kernel. The bias gradients (column sums) run on CUDA cores
+ * either way. Both engines are deterministic. MCMC_EUNSUPPORTED for 1 without sm_103. */
 mcmc_status mcmc_mlp_set_train_engine(mcmc_mlp *m, int32_t tensor_cores);
 
 /* Copies the flat parameter vector in or out (host_io = 1: host pointer, synchronous). Setting
@@ -80,7 +82,8 @@ mcmc_status mcmc_mlp_set_params(mcmc_mlp *m, const float *params, int32_t host_i
 mcmc_status mcmc_mlp_get_params(mcmc_mlp *m, float *params, int32_t host_io);
 
 /* logits [rows x Qc] of features X [rows x 6] (row-major FP32). tensor_cores = 1 runs the
- * tcgen05 kernel (BF16 as above), 0 the FP32 CUDA-core kernels. */
+ * BF16 network kernel on tcgen05 (as above), 0 the FP32-accurate products of training (on the
+ * engine mcmc_mlp_set_train_engine selects). */
 mcmc_status mcmc_mlp_forward(mcmc_mlp *m, int64_t rows, const float *X, float *logits,
                              int32_t tensor_cores);
 
