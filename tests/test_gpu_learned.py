@@ -1,6 +1,7 @@
 """GPU parity of the learned proposal's kernels against the FP64 oracle (oracle/mlp.py and the
-oracle's mixture move): network forward (FP32 CUDA cores and BF16 tcgen05), loss gradient and
-Adam, features, warm start and the mixture move."""
+oracle's mixture move): network forward (the FP32-accurate training products on either engine,
+and the BF16 tcgen05 network kernel), loss gradient and Adam on either engine, features, warm
+start and the mixture move."""
 import numpy as np
 import pytest
 
