@@ -824,6 +824,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workload.WORKLOADS),
                     help="bench a parity-test configuration instead of the headline one")
     ap.add_argument("--graph", action="store_true", help="replay run_chains from a CUDA graph")
+    ap.add_argument("--no-cluster", action="store_true",
+                    help="N > 128 on the single-CTA kernel that streams the operand (no clusters)")
     ap.add_argument("--no-pack", action="store_true",
                     help="one launch per shape class, enqueued directly (no packed launch, no graph)")
     ap.add_argument("--engine", default="auto", choices=["auto", "tc", "simt"],
@@ -895,7 +897,8 @@ def main():
                                      "simt": pkg.MCMC_ENGINE_SIMT}[args.engine] if prec == precision
                                     else pkg.MCMC_ENGINE_AUTO)
                             | (pkg.MCMC_ENGINE_GRAPH if args.graph else 0)
-                            | ((pkg.MCMC_ENGINE_NO_PACK | pkg.MCMC_ENGINE_NO_GRAPH) if args.no_pack else 0),
+                            | ((pkg.MCMC_ENGINE_NO_PACK | pkg.MCMC_ENGINE_NO_GRAPH) if args.no_pack else 0)
+                            | (pkg.MCMC_ENGINE_NO_CLUSTER if args.no_cluster else 0),
                             tile=args.tile if (prec == precision and args.engine != "auto") else 0)
 
     def step(det):
