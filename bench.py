@@ -181,7 +181,47 @@ def profiled_traffic(precision):
     return traffic
 
 
-def chain_roofline(precision, w, units, chain_ms, batch=None):
+def profiled_issue(precision, workload):
+    """Warp instructions per (chain, dimension, transition) of the chain kernel from the committed
+    ncu summary of this workload, or None (another workload, or sources changed since)."""
+    f = PROFILE_FILES.get(precision)
+    if not f or not os.path.exists(os.path.join(ROOT, f)):
+        return None
+    got = {}
+    for line in open(os.path.join(ROOT, f)):
+        for key in ("source_hash", "profile_workload", "warp_instructions_per_chain_dim_transition"):
+            if line.startswith(key + ":"):
+                got[key] = line.split(":", 1)[1].strip()
+    if got.get("source_hash") != _kernel_hash(CHAIN_SOURCES[precision]):
+        return None
+    if got.get("profile_workload") != workload or "warp_instructions_per_chain_dim_transition" not in got:
+        return None
+    return float(got["warp_instructions_per_chain_dim_transition"])
+
+
+def issue_roofline(precision, workload, n_dims, units, chain_ms, clocks):
+    """Instruction issue of the chain kernel: the implementation's warp instructions (ncu's count
+    in the committed capture of this workload, per chain x dimension x transition) over one issue
+    slot per scheduler and clock (4 per SM, at the median SM clock sampled in the timed region).
+    This counts the kernel's own instructions, not the method's work, so it is reported beside
+    the roofline rather than as its bound."""
+    per = profiled_issue(precision, workload)
+    mhz = (clocks or {}).get("sm_mhz")
+    if per is None or not mhz:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    achieved = per * n_dims * units / (chain_ms * 1e-3)
+    peak = 4.0 * sms * mhz * 1e6
+    return {"achieved_warp_inst_per_s": achieved, "peak_warp_inst_per_s": peak,
+            "frac": achieved / peak,
+            "per_unit": f"{per * n_dims:.1f} warp instructions per chain-iteration "
+                        f"({per:g} per chain x dimension x transition, ncu count of the committed "
+                        f"capture; N={n_dims})",
+            "peak_basis": f"4 issue slots per SM per clock x {sms} SMs x {mhz:g} MHz (median sampled)"}
+
+
+def chain_roofline(precision, w, units, chain_ms, batch=None, workload=None, clocks=None):
     """Roofline of the chain loop (the dominant kernel), from the method's algorithmic work per
     chain-iteration (one MH transition of one chain; Algorithm 1 with the proposal of the
     current state carried over, N real dimensions, L levels):
@@ -245,6 +285,8 @@ def chain_roofline(precision, w, units, chain_ms, batch=None):
                                "frac": v["frac"], "per_unit": v["per_unit"]}
                            for k, v in pipes.items() if k != bind},
            "peaks_measured": peaks}
+    if workload is not None:
+        out["issue"] = issue_roofline(precision, workload, N, units, chain_ms, clocks)
     if precision == "mixed":
         tf = gemm * units / t / 1e12
         tp, tsrc = bf16_tensor_peak()
@@ -1024,14 +1066,15 @@ def main():
                      "chain_kernel_ms": kms32, "detections_per_s": B * world / (ms32 * 1e-3),
                      "ber": ber32, "clocks": clk32,
                      "equal_ber": equal_ber(ber, ber32),
-                     "roofline": chain_roofline("fp32", w, units_rank, kms32, batch)}
+                     "roofline": chain_roofline("fp32", w, units_rank, kms32, batch,
+                                                  args.workload, clk32)}
         d32.destroy()
 
     sweep = None
     if compare and not args.no_ber_sweep and precision == "mixed":
         sweep = ber_sweep(args, batch, w, pkg, torch, dev, stream, make)
 
-    roofline = chain_roofline(precision, w, units_rank, chain_ms, batch)
+    roofline = chain_roofline(precision, w, units_rank, chain_ms, batch, args.workload, clocks)
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
