@@ -868,6 +868,9 @@ def main():
     ap.add_argument("--graph", action="store_true", help="replay run_chains from a CUDA graph")
     ap.add_argument("--no-cluster", action="store_true",
                     help="N > 128 on the single-CTA kernel that streams the operand (no clusters)")
+    ap.add_argument("--kernel-refresh", action="store_true",
+                    help="in-run energy refreshes inside the chain kernels (one launch per run) "
+                         "instead of the refresh kernel between launches")
     ap.add_argument("--no-pack", action="store_true",
                     help="one launch per shape class, enqueued directly (no packed launch, no graph)")
     ap.add_argument("--engine", default="auto", choices=["auto", "tc", "simt"],
@@ -940,7 +943,8 @@ def main():
                                     else pkg.MCMC_ENGINE_AUTO)
                             | (pkg.MCMC_ENGINE_GRAPH if args.graph else 0)
                             | ((pkg.MCMC_ENGINE_NO_PACK | pkg.MCMC_ENGINE_NO_GRAPH) if args.no_pack else 0)
-                            | (pkg.MCMC_ENGINE_NO_CLUSTER if args.no_cluster else 0),
+                            | (pkg.MCMC_ENGINE_NO_CLUSTER if args.no_cluster else 0)
+                            | (pkg.MCMC_ENGINE_KERNEL_REFRESH if args.kernel_refresh else 0),
                             tile=args.tile if (prec == precision and args.engine != "auto") else 0)
 
     def step(det):

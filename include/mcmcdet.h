@@ -83,12 +83,15 @@ typedef struct {
                                add FP32 energy differences to the last exact value. R >= 0: every
                                run_chains ends with an exact evaluation of the energies (so the
                                read-outs see exact values); R > 0 also refreshes them every R
-                               transitions inside the run; R = -1: never (the tracked values
+                               transitions inside the run (after each transition t with
+                               t % R == 0: the run is cut into chain-kernel launches there, with
+                               the exact evaluation between them, unless
+                               MCMC_ENGINE_KERNEL_REFRESH); R = -1: never (the tracked values
                                drift; for measuring that drift) */
     int32_t split_terms;    /* MIXED: BF16 terms G is split into (2 = hi+lo, 3 = hi+lo+lo2) */
     int32_t engine;         /* MCMC_ENGINE_AUTO (autotuned per shape class), _SIMT or _TC, optionally
                                OR-ed with the flags MCMC_ENGINE_GRAPH, _NO_CLUSTER, _TRACE,
-                               _NO_PACK and _NO_GRAPH */
+                               _NO_PACK, _NO_GRAPH and _KERNEL_REFRESH */
     int32_t tile;           /* with an explicit engine: chains per work item (TC: 16 or 32, and 64
                                for channels with N = 2 Nt > 128, which run on thread-block
                                clusters; SIMT: a multiple of 8, at most 64); 0: the engine's
@@ -120,6 +123,10 @@ typedef struct {
                                    first, from a device queue) */
 #define MCMC_ENGINE_NO_GRAPH 64 /* flag: a batch of several launch groups is enqueued directly
                                    instead of being replayed from a CUDA graph */
+#define MCMC_ENGINE_KERNEL_REFRESH 128 /* flag: the in-run refreshes of refresh_period > 0 run
+                                          inside the chain kernels (one launch per run) instead
+                                          of between launches; the states, decisions and draws are
+                                          the same either way */
 #define MCMC_ENGINE_TRACE 16    /* flag: every chain records the log acceptance ratio and the log
                                    uniform of its latest transition (Eq. (18)), read back with
                                    mcmc_detect_get_trace (parity diagnostics; one extra store per
@@ -234,7 +241,9 @@ int32_t mcmc_detect_launch_groups(const mcmc_detector *d, int32_t *info, int32_t
 
 /* Device time (ms) of the chain kernels of the latest n runs, oldest first: from the start of
  * the first launch group to the end of the last (CUDA events on the handle's stream), without
- * the exact energy evaluations before and after them. 1 <= n <= min(runs so far, 64), else
+ * the exact energy evaluations before and after them (the in-run refreshes of refresh_period > 0
+ * are inside that span, between the launches or inside the kernels). 1 <= n <= min(runs so far,
+ * 64), else
  * MCMC_EINVAL. Waits for those runs' events. */
 mcmc_status mcmc_detect_run_kernel_ms(mcmc_detector *d, int32_t n, float *ms);
 

@@ -21,7 +21,7 @@ __all__ = [
     "Detector", "Config", "Stats", "lib", "load", "MCMC_PREC_FP64", "MCMC_PREC_FP32",
     "MCMC_PREC_MIXED", "MCMC_ENGINE_AUTO", "MCMC_ENGINE_SIMT", "MCMC_ENGINE_TC",
     "MCMC_ENGINE_GRAPH", "MCMC_ENGINE_NO_CLUSTER", "MCMC_ENGINE_TRACE", "MCMC_ENGINE_NO_PACK",
-    "MCMC_ENGINE_NO_GRAPH", "McmcError", "Mlp",
+    "MCMC_ENGINE_NO_GRAPH", "MCMC_ENGINE_KERNEL_REFRESH", "McmcError", "Mlp",
     "ABI_FUNCTIONS", "ABI_FUNCTIONS_LEARNED", "ABI_FUNCTIONS_DIAG", "transition_diagnostics",
 ]
 
@@ -31,6 +31,7 @@ MCMC_ENGINE_NO_CLUSTER = 8
 MCMC_ENGINE_TRACE = 16
 MCMC_ENGINE_NO_PACK = 32
 MCMC_ENGINE_NO_GRAPH = 64
+MCMC_ENGINE_KERNEL_REFRESH = 128
 _PREC = {"fp64": MCMC_PREC_FP64, "fp32": MCMC_PREC_FP32, "mixed": MCMC_PREC_MIXED}
 STATUS = {0: "MCMC_OK", 1: "MCMC_EINVAL", 2: "MCMC_ENOMEM", 3: "MCMC_ECUDA", 4: "MCMC_ETIMEOUT",
           5: "MCMC_ENUMERIC", 6: "MCMC_ESTATE", 7: "MCMC_EUNSUPPORTED"}

@@ -14,6 +14,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -688,7 +689,7 @@ mcmc_status mcmc_detect_create(const mcmc_config *cfg, mcmc_detector **out)
         (cfg->preconditioned != 0 && cfg->preconditioned != 1) || cfg->refresh_period < -1 ||
         cfg->split_terms < 1 || cfg->split_terms > 3 || cfg->engine < 0 ||
         (cfg->engine & ~(3 | MCMC_ENGINE_GRAPH | MCMC_ENGINE_NO_CLUSTER | MCMC_ENGINE_TRACE |
-                         MCMC_ENGINE_NO_PACK | MCMC_ENGINE_NO_GRAPH)) != 0 ||
+                         MCMC_ENGINE_NO_PACK | MCMC_ENGINE_NO_GRAPH | MCMC_ENGINE_KERNEL_REFRESH)) != 0 ||
         (cfg->engine & 3) == 3 ||
         cfg->tile < 0 || (cfg->tile != 0 && (cfg->engine & 3) == MCMC_ENGINE_AUTO) ||
         ((cfg->engine & 3) == MCMC_ENGINE_TC && cfg->tile != 0 && cfg->tile != 16 && cfg->tile != 32 &&
@@ -1018,10 +1019,28 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         mcmc_status es = ensure_energies(d);
         if (es != MCMC_OK) return es;
     }
-    const ChainArgs ca = chain_args(d, iterations, t_offset);
+    ChainArgs ca = chain_args(d, iterations, t_offset);
     // FP32 / MIXED: the energies the chains tracked in FP32 steps are replaced by exact
     // evaluations when the run ends (refresh_period >= 0), and the correction is recorded
     const bool final_refresh = !fp64 && d->cfg.refresh_period >= 0;
+    // In-run refreshes (refresh_period R > 0) after every transition t with t % R == 0: by
+    // default the run is cut into launches at those transitions and the exact refresh kernel runs
+    // between them. The draws follow the transition number, so the states and decisions are those
+    // of one launch; MCMC_ENGINE_KERNEL_REFRESH keeps the refreshes inside the chain kernels.
+    const int R = d->cfg.refresh_period;
+    const bool cut = !fp64 && R > 0 && !(d->cfg.engine & MCMC_ENGINE_KERNEL_REFRESH);
+    std::vector<std::pair<int64_t, int32_t>> segs;   // (t_offset, iterations) of each launch
+    if (cut) {
+        ca.refresh_period = 0;
+        const int64_t end = t_offset + iterations;
+        for (int64_t s0 = t_offset; s0 < end;) {
+            const int64_t e = std::min<int64_t>((s0 / R + 1) * R, end);
+            segs.emplace_back(s0, (int32_t)(e - s0));
+            s0 = e;
+        }
+    } else {
+        segs.emplace_back(t_offset, iterations);
+    }
     RefreshArgs fr{};
     if (final_refresh) {
         fr.desc = P<ChannelDesc>(d->d_desc);
@@ -1044,15 +1063,22 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
         cudaError_t e = cudaSuccess;
         const size_t ng = d->groups.size();
         int *queues = P<int>(d->d_queue);
-        if (ng > 1) e = cudaEventRecord(d->ev_fork, d->stream);
-        for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) {
-            cudaStream_t s = gi == 0 ? d->stream : d->aux[gi - 1];
-            if (gi > 0) e = cudaStreamWaitEvent(s, d->ev_fork, 0);
-            if (e == cudaSuccess) e = launch_group(d, d->groups[gi], ca, s, queues + gi);
-            if (e == cudaSuccess && gi > 0) e = cudaEventRecord(d->ev_join[gi - 1], s);
+        for (size_t si = 0; si < segs.size() && e == cudaSuccess; ++si) {
+            ChainArgs cs = ca;
+            cs.t_offset = segs[si].first;
+            cs.iterations = segs[si].second;
+            if (ng > 1) e = cudaEventRecord(d->ev_fork, d->stream);
+            for (size_t gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+                cudaStream_t s = gi == 0 ? d->stream : d->aux[gi - 1];
+                if (gi > 0) e = cudaStreamWaitEvent(s, d->ev_fork, 0);
+                if (e == cudaSuccess) e = launch_group(d, d->groups[gi], cs, s, queues + gi);
+                if (e == cudaSuccess && gi > 0) e = cudaEventRecord(d->ev_join[gi - 1], s);
+            }
+            for (size_t gi = 1; gi < ng && e == cudaSuccess; ++gi)
+                e = cudaStreamWaitEvent(d->stream, d->ev_join[gi - 1], 0);
+            // an in-run refresh (the last cut is the run's end: the final refresh follows it)
+            if (e == cudaSuccess && si + 1 < segs.size()) e = launch_refresh(fr, d->stream);
         }
-        for (size_t gi = 1; gi < ng && e == cudaSuccess; ++gi)
-            e = cudaStreamWaitEvent(d->stream, d->ev_join[gi - 1], 0);
         return e;
     };
     const int slot = (int)(d->runs % mcmc_detector::kRunSlots);
@@ -1092,7 +1118,7 @@ mcmc_status mcmc_detect_run_chains(mcmc_detector *d, int32_t iterations, int64_t
     CK(cudaEventRecord(d->ev_run[slot][1], d->stream), "record run end");
     d->runs++;
     if (final_refresh) CK(launch_refresh(fr, d->stream), "energies");
-    d->launches += (long long)d->groups.size() + (final_refresh ? 1 : 0);
+    d->launches += (long long)(d->groups.size() + 1) * segs.size() - 1 + (final_refresh ? 1 : 0);
     d->f_valid = true;
     d->f_exact = fp64 || final_refresh;
     d->d_valid = !fp64;

@@ -125,9 +125,10 @@ def test_config_validation_on_the_host():
                dict(precision=MIXED, engine=TC | NOCL, tile=32),
                dict(precision=MIXED, engine=TC | GRAPH | NOCL),
                dict(precision=MIXED, engine=AUTO | NOCL),
-               dict(precision=FP32, engine=pkg.MCMC_ENGINE_SIMT, tile=64)]:
+               dict(precision=FP32, engine=pkg.MCMC_ENGINE_SIMT, tile=64),
+               dict(precision=MIXED, engine=AUTO | pkg.MCMC_ENGINE_KERNEL_REFRESH, refresh_period=10)]:
         assert create(**kw) in (0, 7), kw
-    for kw in [dict(engine=128), dict(engine=3), dict(precision=MIXED, engine=TC, tile=48),
+    for kw in [dict(engine=256), dict(engine=3), dict(precision=MIXED, engine=TC, tile=48),
                dict(precision=MIXED, engine=AUTO, tile=64), dict(precision=FP32, engine=TC),
                dict(max_nt=129), dict(chains=6), dict(split_terms=4),
                dict(refresh_period=-2)]:

@@ -268,3 +268,46 @@ def test_deferred_initial_energies_and_kernel_timing():
     assert len(det2.run_kernel_ms(1)) == 1
     det.destroy()
     det2.destroy()
+
+
+KERNEL_REFRESH = 128   # MCMC_ENGINE_KERNEL_REFRESH: in-run refreshes inside the chain kernels
+
+
+@pytest.mark.parametrize("case", ["cluster", "streamed", "one_tile", "simt_fp32"])
+def test_in_run_refresh_between_launches(case):
+    """A run with in-run refreshes is cut into launches at the refresh points, with the exact
+    refresh kernel between them; the in-kernel refreshes (MCMC_ENGINE_KERNEL_REFRESH) give the
+    same chains: equal states, acceptances, near-tie counts, best samples and LLRs, and energies
+    equal to within the two exact evaluations' rounding. The second run starts between refresh
+    points."""
+    if case in ("cluster", "streamed"):
+        b = workload.kronecker_batch(128, 128, 64, [30.0], 2, 0.5, 78)
+        kw = dict(chains=64, precision="mixed", split_terms=2,
+                  engine=TC | (NO_CLUSTER if case == "streamed" else 0))
+    elif case == "one_tile":
+        b = workload.rayleigh_batch(32, 32, 64, [26.0], 8, 79)
+        kw = dict(chains=32, precision="mixed", split_terms=2, engine=TC)
+    else:
+        b = workload.rayleigh_batch(32, 32, 64, [26.0], 8, 79)
+        kw = dict(chains=32, precision="fp32", engine=1)   # MCMC_ENGINE_SIMT
+    outs = []
+    for extra in (0, KERNEL_REFRESH):
+        kx = dict(kw)
+        kx["engine"] = kw["engine"] | extra
+        det = H.make_detector(b, seed=11, refresh_period=7, **kx)
+        det.run_chains(17)
+        det.run_chains(9, 17)
+        flat, _ = det.get_chains()
+        ftr, fbest = det.get_tracked()
+        est = det.estimate(stats=True)
+        outs.append((flat.copy(), ftr.copy(), fbest.copy(), est))
+        det.destroy()
+    (s0, f0, b0, e0), (s1, f1, b1, e1) = outs
+    np.testing.assert_array_equal(s0, s1)
+    assert e0["stats"]["accepts"] == e1["stats"]["accepts"]
+    assert e0["stats"]["near_ties"] == e1["stats"]["near_ties"]
+    assert e0["stats"]["accepts"] > 0
+    np.testing.assert_allclose(f0, f1, rtol=1e-10, atol=0)
+    np.testing.assert_allclose(b0, b1, rtol=1e-10, atol=0)
+    np.testing.assert_array_equal(e0["best_idx"], e1["best_idx"])
+    np.testing.assert_allclose(e0["llr"], e1["llr"], rtol=1e-5, atol=1e-5)
