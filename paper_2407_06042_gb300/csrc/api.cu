@@ -528,7 +528,7 @@ cudaError_t launch_group(mcmc_detector *d, const Group &g, ChainArgs ca, cudaStr
             if (e != cudaSuccess) return e;
             ca.queue = queue;
         }
-        return tc_launch_chains(ca, g.plan, s);
+        return ca.refresh_period > 0 ? tc_launch_chains_kr(ca, g.plan, s) : tc_launch_chains(ca, g.plan, s);
     }
     return launch_chains_simt(ca, fp64, g.smem, s);
 }
@@ -595,6 +595,8 @@ mcmc_status autotune(mcmc_detector *d, bool *probed)
                                cudaMemcpyHostToDevice, d->stream), "copy probe items");
             ChainArgs ca = chain_args(d, 2, 0);
             ca.init_f = 1;
+            // the kernels the run will launch: without the in-run refresh unless it stays inside
+            if (!(d->cfg.engine & MCMC_ENGINE_KERNEL_REFRESH)) ca.refresh_period = 0;
             ca.near_ties = nullptr;   // probe transitions are not the batch's
             ca.trace = nullptr;
             cudaError_t e = launch_group(d, g, ca, d->stream, nullptr);   // warm-up

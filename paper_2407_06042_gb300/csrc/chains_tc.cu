@@ -32,6 +32,11 @@
 // Every wait is bounded: a wait that runs out sets the timeout status bit, the CTA stops issuing
 // work, waits (bounded) for its copies in flight, frees its TMEM and returns (in a cluster, after
 // the exit barrier that keeps every CTA's shared memory alive for the others' stores).
+//
+// The in-run FP64 refreshes (refresh_period > 0) normally run between launches (the refresh
+// kernel); the kernels here carry none of that code. chains_tc_kr.cu compiles this file a second
+// time with MCMC_TC_IN_KERNEL_REFRESH = 1: the same kernels with the refresh inside, launched by
+// tc_launch_chains_kr (MCMC_ENGINE_KERNEL_REFRESH), and none of the host-side planning.
 #include "tc_plan.h"
 
 #include <cuda_bf16.h>
@@ -39,9 +44,15 @@
 #include "proposal.cuh"
 #include "tc_ptx.cuh"
 
+#ifndef MCMC_TC_IN_KERNEL_REFRESH
+#define MCMC_TC_IN_KERNEL_REFRESH 0
+#endif
+
 namespace mcmcdet {
 
 namespace {
+
+constexpr bool kInKernelRefresh = MCMC_TC_IN_KERNEL_REFRESH != 0;
 
 // Launch bounds of the one-tile kernel: at most TC_MAX_THREADS threads per CTA (16 per chain),
 // registers sized for TC_MIN_BLOCKS such CTAs per SM.
@@ -1062,8 +1073,10 @@ __device__ void tc_item(const ChainArgs &A, TcCtx &x, const WorkItem &it, const 
                 }
             }
         }
-        // periodic FP64 refresh of the tracked energies (decisions never read them)
-        if constexpr (CL > 1) {
+        // periodic FP64 refresh of the tracked energies (decisions never read them); compiled
+        // into the kernels of the second translation unit only
+        if constexpr (!kInKernelRefresh) {
+        } else if constexpr (CL > 1) {
             if (A.refresh_period > 0 && (t_it % (uint32_t)A.refresh_period) == 0u) {
                 // every CTA needs the whole state: x goes through the B operand's slice transfer.
                 // Then x^T G x over this CTA's rows n (all columns m) is evaluated exactly for
@@ -1456,6 +1469,7 @@ __global__ void __launch_bounds__(CL > 1 ? 1024 : TC_MAX_THREADS, MT == 1 && CL 
                      "r"(ncols_alloc));
 }
 
+#if !MCMC_TC_IN_KERNEL_REFRESH
 // ------------------------------------------------------------------------------------------
 // Operand packing: [Gt | P~Gt] (FP32) -> `S` BF16 split terms in the core-matrix image. One
 // thread builds one 16-byte core-matrix row (8 consecutive K values of one A row) per term.
@@ -1508,6 +1522,7 @@ int pow2_at_least(int v)
     while (p < v) p <<= 1;
     return p;
 }
+#endif  // !MCMC_TC_IN_KERNEL_REFRESH
 
 }  // namespace
 
@@ -1517,6 +1532,7 @@ using TcKernel = void (*)(const ChainArgs, const int, const int, const int);
 
 TcKernel cluster_kernel(int CL) { return CL == 3 ? chains_tc_kernel<1, 1, 3> : chains_tc_kernel<1, 1, 4>; }
 
+#if !MCMC_TC_IN_KERNEL_REFRESH
 // Clusters of CL CTAs (smem bytes, threads each) that can be resident at once; 0 if none.
 int cluster_capacity(int CL, size_t smem, int threads)
 {
@@ -1543,9 +1559,11 @@ int cluster_capacity(int CL, size_t smem, int threads)
     }
     return n;
 }
+#endif  // !MCMC_TC_IN_KERNEL_REFRESH
 
 }  // namespace
 
+#if !MCMC_TC_IN_KERNEL_REFRESH
 bool tc_make_plan(int max_n, int chains_per_cta, int split_terms, size_t smem_optin, bool allow_cluster,
                   TcPlan *plan)
 {
@@ -1653,7 +1671,15 @@ cudaError_t tc_launch_pack(int split_terms, const ChannelDesc *desc, int n_chann
     return cudaGetLastError();
 }
 
+#endif  // !MCMC_TC_IN_KERNEL_REFRESH
+
+// The launch of a group's work items: tc_launch_chains runs the kernels without the in-run
+// refresh (refresh_period must be 0 in a_in), tc_launch_chains_kr those with it.
+#if MCMC_TC_IN_KERNEL_REFRESH
+cudaError_t tc_launch_chains_kr(const ChainArgs &a_in, const TcPlan &plan, cudaStream_t s)
+#else
 cudaError_t tc_launch_chains(const ChainArgs &a_in, const TcPlan &plan, cudaStream_t s)
+#endif
 {
     if (a_in.n_items <= 0) return cudaSuccess;
     ChainArgs a = a_in;

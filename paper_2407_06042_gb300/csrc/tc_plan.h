@@ -50,6 +50,11 @@ long long tc_operand_bytes(int N, int split_terms);
 cudaError_t tc_launch_pack(int split_terms, const ChannelDesc *desc, int n_channels,
                            const float *bt32, uint8_t *tc_ops, cudaStream_t s);
 
+// Launches the chain kernels of a plan for a.n_items work items. tc_launch_chains: kernels
+// without the in-run FP64 refresh (a.refresh_period must be 0: the caller refreshes between
+// launches); tc_launch_chains_kr: the same kernels with the refresh every a.refresh_period
+// transitions inside them.
 cudaError_t tc_launch_chains(const ChainArgs &a, const TcPlan &plan, cudaStream_t s);
+cudaError_t tc_launch_chains_kr(const ChainArgs &a, const TcPlan &plan, cudaStream_t s);
 
 }  // namespace mcmcdet
