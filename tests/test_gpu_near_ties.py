@@ -10,7 +10,7 @@ unambiguous, and the energies the chains track are compared with the oracle's f 
 after every step. The kernels also count their own near-ties (mcmc_stats.near_ties). Each case
 appends its figures to $MCMC_PARITY_REPORT when that variable names a file.
 
-Windows: FP64 1e-6 (the benchmark spec's); FP32 and MIXED with three split terms 2e-4 (CDF) and 2e-3
+Windows: FP64 1e-6 (the bar stated for FP64 accept decisions); FP32 and MIXED with three split terms 2e-4 (CDF) and 2e-3
 (accept), the FP32 rounding of Gt x' amplified by 1/(tau sigma^2); MIXED with two terms 32x
 those (the split error 2^-17 per product instead of 2^-24)."""
 import numpy as np
