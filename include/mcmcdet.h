@@ -144,7 +144,9 @@ typedef struct {
                                |log A - log u|, as the chain kernel evaluated it in its own
                                precision, was below 1e-6, 1e-4 and 1e-2 (natural log): the
                                decisions a rounding difference of that size could flip */
-    double refresh_drift_rel; /* max |f_tracked - f_exact| / |f_exact| seen at refreshes */
+    double refresh_drift_rel; /* max |f_tracked - f_exact| / |f_exact| seen at the refreshes
+                                 between and after launches (the in-kernel refreshes of
+                                 MCMC_ENGINE_KERNEL_REFRESH record refresh_drift only) */
 } mcmc_stats;
 
 /* Fills *cfg with defaults: 1 channel, Nt = Nr = 4, 32 chains, FP32, preconditioned, R = 0,
