@@ -126,7 +126,9 @@ typedef struct {
 #define MCMC_ENGINE_KERNEL_REFRESH 128 /* flag: the in-run refreshes of refresh_period > 0 run
                                           inside the chain kernels (one launch per run) instead
                                           of between launches; the states, decisions and draws are
-                                          the same either way */
+                                          the same either way. Without it a run makes one launch
+                                          per R transitions, so for very short periods (a few
+                                          transitions) this form can be the faster one */
 #define MCMC_ENGINE_TRACE 16    /* flag: every chain records the log acceptance ratio and the log
                                    uniform of its latest transition (Eq. (18)), read back with
                                    mcmc_detect_get_trace (parity diagnostics; one extra store per
