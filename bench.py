@@ -162,6 +162,10 @@ CHAIN_SOURCES = {
 }
 PROFILE_FILES = {"mixed": "profiles/chains_tc_rayleigh_32x32_64qam.md",
                  "fp32": "profiles/chains_simt_rayleigh_32x32_64qam.md"}
+# summaries that give the chain kernel's instruction count, per (precision, workload)
+ISSUE_PROFILES = {("mixed", "rayleigh_32x32_64qam"): PROFILE_FILES["mixed"],
+                  ("fp32", "rayleigh_32x32_64qam"): PROFILE_FILES["fp32"],
+                  ("mixed", "kronecker_128x128_64qam"): "profiles/chains_tc_kronecker_128x128_64qam.md"}
 
 
 def profiled_traffic(precision):
@@ -184,7 +188,7 @@ def profiled_traffic(precision):
 def profiled_issue(precision, workload):
     """Warp instructions per (chain, dimension, transition) of the chain kernel from the committed
     ncu summary of this workload, or None (another workload, or sources changed since)."""
-    f = PROFILE_FILES.get(precision)
+    f = ISSUE_PROFILES.get((precision, workload))
     if not f or not os.path.exists(os.path.join(ROOT, f)):
         return None
     got = {}

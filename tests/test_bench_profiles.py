@@ -20,6 +20,9 @@ def _patch(monkeypatch, tmp_path, src, prof):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "CHAIN_SOURCES", {"mixed": [os.path.basename(src)]})
     monkeypatch.setattr(bench, "PROFILE_FILES", {"mixed": os.path.basename(prof)})
+    monkeypatch.setattr(bench, "ISSUE_PROFILES",
+                        {("mixed", "rayleigh_32x32_64qam"): os.path.basename(prof),
+                         ("mixed", "kronecker_128x128_64qam"): os.path.basename(prof)})
 
 
 def test_current_summary_is_quoted(monkeypatch, tmp_path):
@@ -41,6 +44,14 @@ def test_stale_summary_is_not_quoted(monkeypatch, tmp_path):
     src.write_text("// kernel source, changed since the capture\n")
     assert bench.profiled_traffic("mixed") is None
     assert bench.profiled_issue("mixed", "rayleigh_32x32_64qam") is None
+
+
+def test_committed_summaries_name_their_workload():
+    for (precision, workload), f in bench.ISSUE_PROFILES.items():
+        text = open(os.path.join(bench.ROOT, f)).read()
+        assert f"profile_workload: {workload}" in text, f
+        assert "warp_instructions_per_chain_dim_transition:" in text, f
+        assert "source_hash:" in text, f
 
 
 def test_missing_summary(monkeypatch, tmp_path):
