@@ -168,19 +168,21 @@ ISSUE_PROFILES = {("mixed", "rayleigh_32x32_64qam"): PROFILE_FILES["mixed"],
                   ("mixed", "kronecker_128x128_64qam"): "profiles/chains_tc_kronecker_128x128_64qam.md"}
 
 
-def profiled_traffic(precision):
-    """DRAM bytes per full-size launch of the chain kernel from the committed ncu summary, or
-    None when the kernel sources changed since that capture."""
+def profiled_traffic(precision, workload):
+    """DRAM bytes per full-size launch of the chain kernel from the committed ncu summary of this
+    workload, or None (no such summary, another workload, or sources changed since)."""
     f = PROFILE_FILES.get(precision)
     if not f or not os.path.exists(os.path.join(ROOT, f)):
         return None
-    want, traffic = None, None
+    want, traffic, wl = None, None, None
     for line in open(os.path.join(ROOT, f)):
         if line.startswith("source_hash:"):
             want = line.split(":", 1)[1].strip()
         if line.startswith("dram_bytes_per_full_launch:"):
             traffic = float(line.split(":", 1)[1].strip())
-    if want != _kernel_hash(CHAIN_SOURCES[precision]):
+        if line.startswith("profile_workload:"):
+            wl = line.split(":", 1)[1].strip()
+    if want != _kernel_hash(CHAIN_SOURCES[precision]) or wl != workload:
         return None
     return traffic
 
@@ -282,7 +284,7 @@ def chain_roofline(precision, w, units, chain_ms, batch=None, workload=None, clo
     pb = pipes[bind]
     out = {"bound": "alu", "achieved": pb["achieved"] / 1e9,
            "peak": (pb["peak"] / 1e9) if pb["peak"] else None, "unit": "Gop/s",
-           "frac": pb["frac"], "traffic": profiled_traffic(precision),
+           "frac": pb["frac"], "traffic": profiled_traffic(precision, workload),
            "pipe": pb["pipe"], "per_unit": pb["per_unit"], "launch_ms": chain_ms,
            "other_pipes": {k: {"achieved_gops": v["achieved"] / 1e9,
                                "peak_gops": (v["peak"] / 1e9) if v["peak"] else None,

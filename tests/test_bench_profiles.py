@@ -1,7 +1,7 @@
 """bench.py's use of the committed ncu summaries (host logic, no GPU): the DRAM traffic and the
 instruction count per chain x dimension x transition are quoted only while the summary's source
-hash equals the hash of the kernel sources it was captured from, and the instruction count only
-for the workload it was captured on."""
+hash equals the hash of the kernel sources it was captured from, and only for the workload it
+was captured on."""
 import os
 
 import bench
@@ -30,7 +30,8 @@ def test_current_summary_is_quoted(monkeypatch, tmp_path):
     _patch(monkeypatch, tmp_path, src, prof)
     h = bench._kernel_hash(bench.CHAIN_SOURCES["mixed"])
     prof.write_text(prof.read_text().replace("0" * 16, h))
-    assert bench.profiled_traffic("mixed") == 1.5e9
+    assert bench.profiled_traffic("mixed", "rayleigh_32x32_64qam") == 1.5e9
+    assert bench.profiled_traffic("mixed", "kronecker_128x128_64qam") is None
     assert bench.profiled_issue("mixed", "rayleigh_32x32_64qam") == 4.25
     # another workload's instruction count is not this one's
     assert bench.profiled_issue("mixed", "kronecker_128x128_64qam") is None
@@ -42,7 +43,7 @@ def test_stale_summary_is_not_quoted(monkeypatch, tmp_path):
     h = bench._kernel_hash(bench.CHAIN_SOURCES["mixed"])
     prof.write_text(prof.read_text().replace("0" * 16, h))
     src.write_text("// kernel source, changed since the capture\n")
-    assert bench.profiled_traffic("mixed") is None
+    assert bench.profiled_traffic("mixed", "rayleigh_32x32_64qam") is None
     assert bench.profiled_issue("mixed", "rayleigh_32x32_64qam") is None
 
 
@@ -56,6 +57,6 @@ def test_committed_summaries_name_their_workload():
 
 def test_missing_summary(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.profiled_traffic("mixed") is None
+    assert bench.profiled_traffic("mixed", "rayleigh_32x32_64qam") is None
     assert bench.profiled_issue("mixed", "rayleigh_32x32_64qam") is None
     assert bench.profiled_issue("fp64", "rayleigh_32x32_64qam") is None
